@@ -1,0 +1,201 @@
+/*
+ * ftgemm.h -- C ABI of libftgemm, a fault-tolerant FP64 GEMM for one NVIDIA
+ * GB300 (sm_103a).
+ *
+ * The operation is the BLAS DGEMM of FT-GEMM (Wu et al., HPDC'23, abstract
+ * and §2.1):
+ *
+ *     C <- alpha * op(A) * op(B) + beta * C,   op(X) = X or X^T,
+ *
+ * protected by algorithm-based fault tolerance (§2.2, after Huang and Abraham
+ * 1984): for every BM x BN output tile the library predicts the column and
+ * row checksums of the result from checksums of the operands and of beta*C,
+ * sums the reference checksums from the computed tile before it leaves the
+ * chip, and on a mismatch locates the wrong elements and rewrites them with a
+ * recomputed value.  Faults are injected at source level (§3.2) by flipping
+ * seeded bits of accumulator values.
+ *
+ * Conventions (all entry points):
+ *  - Column-major storage.  trans is 'N'/'n' (op(X) = X) or 'T'/'t'/'C'/'c'
+ *    (op(X) = X^T; real data, so 'C' equals 'T').  op(A) is M x K, op(B) is
+ *    K x N, C is M x N.
+ *  - Matrix pointers of ftgemm_d* are DEVICE pointers owned by the caller;
+ *    they must stay valid until the stream reaches the end of the call.
+ *    ftgemm_d_host takes HOST pointers instead.  Report and injection structs
+ *    are HOST memory owned by the caller.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is stream-ordered.  A call with rep == NULL returns after
+ *    enqueueing (no host synchronisation); a call with rep != NULL waits for
+ *    its own stream so that the report is complete on return.
+ *  - Return value: 0 on success; -i when argument i is invalid (BLAS xerbla
+ *    numbering: 1 transA, 2 transB, 3 M, 4 N, 5 K, 8 lda, 10 ldb, 13 ldc);
+ *    a positive FTGEMM_ERR_* code otherwise.  A detected and corrected fault
+ *    is not an error: the call returns 0 and the report counts it.
+ *  - BLAS quick returns: M == 0 or N == 0 does nothing; K == 0 or alpha == 0
+ *    gives C = beta*C; beta == 0 never reads C (NaN in C does not propagate).
+ *  - The library owns a lazily grown per-device workspace (operand checksum
+ *    vectors, the device report, the injection table, staging for unaligned
+ *    operands and for ftgemm_d_host), released by ftgemm_finalize().  Calls
+ *    share it, so calls must not run concurrently on different streams or
+ *    host threads.
+ *  - Operands whose base address is not 16-byte aligned or whose leading
+ *    dimension is odd are first copied into aligned workspace (the tensor
+ *    memory accelerator needs 16-byte aligned rows); results are the same.
+ */
+#ifndef FTGEMM_H
+#define FTGEMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Output tile of the checksum scheme, and the k-step (products accumulated
+ * between two points where a fault may be injected). */
+#define FTGEMM_BM 128
+#define FTGEMM_BN 128
+#define FTGEMM_KSTEP 16
+
+/* Positive error codes. */
+#define FTGEMM_ERR_CUDA 1       /* a CUDA runtime call or kernel launch failed */
+#define FTGEMM_ERR_TIMEOUT 2    /* a bounded pipeline wait expired on the device */
+#define FTGEMM_ERR_NODEVICE 4   /* no usable CUDA device */
+#define FTGEMM_ERR_NOMEM 5      /* workspace allocation failed */
+#define FTGEMM_ERR_INJECT 6     /* an explicit fault lies outside the problem */
+#define FTGEMM_ERR_TENSORMAP 7  /* a TMA descriptor could not be encoded */
+
+/* One located fault: element (row, col) of C, 0-based. */
+typedef struct {
+  int64_t row, col;
+  int32_t tile;  /* tile id: I + J * ceil(M / FTGEMM_BM) */
+  int32_t kind;  /* 0: found at a flagged row x flagged column intersection;
+                    1: found by the fallback that recomputes whole row/column
+                       segments of a tile */
+  double delta;  /* stored value minus recomputed value (may be Inf/NaN) */
+} ftgemm_loc;
+
+/* Fault report of one call.  The caller sets cap and loc (loc may be NULL
+ * with cap 0); the library fills the rest.  Every count is exact even when
+ * n_loc > cap (then only the first cap records, in no particular order, are
+ * written). */
+typedef struct {
+  int64_t detected;      /* elements whose recomputed value differed from the
+                            computed one by more than the element bound */
+  int64_t corrected;     /* of those, rewritten with the recomputed value */
+  int64_t checksum_only; /* rows + columns whose mismatch survived every
+                            recomputation: a fault in a checksum, data intact */
+  int64_t unverifiable;  /* rows + columns (per tile) whose predicted checksum
+                            was not finite because the inputs are not */
+  int64_t flagged_rows;  /* row mismatches raised by the first verification */
+  int64_t flagged_cols;  /* column mismatches raised by the first verification */
+  int64_t recomputed;    /* elements recomputed, wrong or not */
+  int64_t n_loc;         /* location records produced */
+  int64_t cap;           /* capacity of loc (input) */
+  ftgemm_loc *loc;       /* caller-owned host array of cap records (input) */
+} ftgemm_report;
+
+/* One fault to inject: flip bit `bit` (0..62; the sign bit is excluded) of
+ * the accumulator of C(row, col) right after its k-step `kstep`, i.e. after
+ * its first min(K, FTGEMM_KSTEP * (kstep + 1)) products (source-level
+ * injection, §3.2). */
+typedef struct {
+  int64_t row, col, kstep;
+  int32_t bit, pad;
+} ftgemm_flip;
+
+/* Injection setting, process-global, applied to every later ftgemm_d call
+ * (not to ftgemm_d_noft).  mode 0: off.  mode 1: `count` faults per call at
+ * positions drawn from splitmix64(seed): fault f takes outputs 4f..4f+3 of the
+ * generator, n-th output = mix(seed + (n+1) * 0x9E3779B97F4A7C15), as
+ * (row mod M, col mod N, kstep mod ceil(K/16), bit mod 63).  mode 2: the
+ * explicit `list` of n_list faults (copied at the call). */
+typedef struct {
+  int32_t mode, pad;
+  uint64_t seed;
+  int64_t count;
+  const ftgemm_flip *list;
+  int64_t n_list;
+} ftgemm_inject;
+
+/* What happened to one injected fault of the last injected call. */
+typedef struct {
+  int64_t row, col, kstep;
+  int32_t bit;
+  int32_t applied;  /* 1 when the flip was made */
+  double before;    /* accumulator value before the flip */
+  double after;     /* accumulator value after the flip */
+} ftgemm_flip_log;
+
+/* Fault-tolerant DGEMM (abstract; §2.2).  Encodes, verifies, locates and
+ * corrects per FTGEMM_BM x FTGEMM_BN tile; rep may be NULL. */
+int ftgemm_d(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+             const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+             double *C, int64_t ldc, ftgemm_report *rep, void *stream);
+
+/* The same DGEMM with the fault tolerance compiled out: the same tiles,
+ * pipeline and epilogue without checksums, verification or injection (the
+ * baseline the ABFT overhead is measured against, §3.1 "FT-GEMM: Ori"). */
+int ftgemm_d_noft(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                  double *C, int64_t ldc, void *stream);
+
+/* ftgemm_d on HOST matrices: copies A, B (and C unless beta == 0) to device
+ * workspace, runs ftgemm_d, copies C back, and waits for the stream.  Pinned
+ * host memory makes the copies fastest; pageable memory also works. */
+int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                  double *C, int64_t ldc, ftgemm_report *rep, void *stream);
+
+/* The operand checksum pass on its own (the A and B checksum vectors of
+ * §2.2/§2.3 per FTGEMM_BM-row / FTGEMM_BN-column tile, and the absolute sums
+ * the detection threshold uses).  All outputs are device arrays owned by the
+ * caller: acs (ceil(M/BM) x K, row stride K), aabsmax (ceil(M/BM)), arowabs
+ * (M), bcs (ceil(N/BN) x K, row stride K), babsmax (ceil(N/BN)), bcolabs (N):
+ *   acs[I*K+k] = sum_{i in I} op(A)(i,k),   aabsmax[I] = max_k sum_{i in I} |op(A)(i,k)|,
+ *   arowabs[i] = sum_k |op(A)(i,k)|,        and symmetrically for op(B). */
+int ftgemm_encode_operands(char transA, char transB, int64_t M, int64_t N, int64_t K,
+                           const double *A, int64_t lda, const double *B, int64_t ldb,
+                           double *acs, double *aabsmax, double *arowabs, double *bcs,
+                           double *babsmax, double *bcolabs, void *stream);
+
+/* Set (cfg != NULL) or clear (cfg == NULL or mode 0) fault injection. */
+int ftgemm_set_injection(const ftgemm_inject *cfg);
+
+/* Copy up to cap records of the last injected call's faults, in the order
+ * they were drawn or listed, into out; returns the number of faults of that
+ * call (or a negative value if out is NULL while cap > 0).  Waits for the
+ * device. */
+int64_t ftgemm_injection_log(ftgemm_flip_log *out, int64_t cap);
+
+/* Test hook for the bounded waits: launches one block that waits on an
+ * mbarrier nothing ever completes, with a limit of limit_ns nanoseconds.
+ * Returns FTGEMM_ERR_TIMEOUT when the wait gave up and the context is still
+ * usable (the expected result), another code otherwise. */
+int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
+
+/* Number of kernels this library has launched in this process. */
+int64_t ftgemm_launch_count(void);
+
+/* Event timing of the library's own kernels, for benchmarks: enable != 0
+ * starts recording CUDA events on the launching stream around every later
+ * main GEMM kernel and around the work before it (operand checksum pass,
+ * report reset, injection upload); any call clears what was recorded. */
+int ftgemm_timing(int enable);
+
+/* Wait for the recorded events and return the summed main-kernel time, the
+ * number of main-kernel launches timed, and the summed time of the work
+ * before each launch (milliseconds; any pointer may be NULL). */
+int ftgemm_timing_read(double *main_ms, int64_t *main_launches, double *aux_ms);
+
+/* Static description of an error code. */
+const char *ftgemm_strerror(int code);
+
+/* Release the workspace of the current device. */
+int ftgemm_finalize(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTGEMM_H */

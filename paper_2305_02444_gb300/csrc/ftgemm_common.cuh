@@ -1,0 +1,177 @@
+// Shared device definitions of libftgemm: tile shape, parameter block,
+// device report layout, and inline-PTX helpers for mbarriers and the tensor
+// memory accelerator (TMA) on sm_103a.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ftg {
+
+// Output tile BM x BN per CTA, k-slab BK (the injection k-step), ring depth.
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 16;
+constexpr int STAGES = 4;
+constexpr int NCOMPUTE = 256;  // 8 compute warps, 8x8 accumulators each
+constexpr int NTHREADS = 256;  // thread 0 also issues the TMA loads
+constexpr int A_BYTES = BM * BK * 8;  // 16 KiB
+constexpr int B_BYTES = BN * BK * 8;  // 16 KiB
+constexpr int CS_BYTES = BK * 8;      // one k-slab of a checksum vector
+constexpr int STAGE_BYTES = 33 * 1024;  // A | B | acs | bcs, 1 KiB aligned
+constexpr int RING_BYTES = STAGES * STAGE_BYTES;
+constexpr int CTILE_BYTES = BM * BN * 8;  // output tile staged for verify/store
+constexpr int TILE_REGION = RING_BYTES > CTILE_BYTES ? RING_BYTES : CTILE_BYTES;
+// epilogue arrays: 10 x 128 doubles + 4 x 128 ints + counters
+constexpr int EPI_BYTES = 10 * 128 * 8 + 4 * 128 * 4 + 256;
+constexpr int BAR_BYTES = 2 * STAGES * 8 + 8 + 8;
+constexpr int SMEM_BYTES = TILE_REGION + EPI_BYTES + BAR_BYTES + 1024;
+constexpr int MAX_INTERSECT = 64;  // flagged row x column intersections per tile
+
+// Device copy of the fault report (zeroed by the host before each call).
+struct DevReport {
+  unsigned long long detected, corrected, checksum_only, unverifiable;
+  unsigned long long flagged_rows, flagged_cols, recomputed, n_loc;
+  int err;  // FTGEMM_ERR_TIMEOUT when a bounded wait expired
+  int pad;
+};
+
+struct DevLoc {
+  long long row, col;
+  int tile, kind;
+  double delta;
+};
+
+// One injected fault, sorted by (tile, kstep); before/after written by the kernel.
+struct DevFlip {
+  long long row, col, kstep;
+  int bit, applied;
+  double before, after;
+};
+
+struct Params {
+  long long M, N, K;
+  double alpha, beta;
+  const double *A, *B;
+  double *C;
+  long long lda, ldb, ldc;
+  int nI, nJ, nks;
+  long long Kp;                  // row stride of acs / bcs (K rounded up to BK)
+  const double *acs, *bcs;       // (nI x Kp), (nJ x Kp) operand checksum vectors
+  const double *arowabs, *aabsmax, *bcolabs, *babsmax;
+  DevReport *rep;
+  DevLoc *loc;
+  long long loc_cap;
+  DevFlip *flips;                // injection table (INJ kernels only)
+  const int *tile_off;           // ntiles + 1 offsets into flips
+  unsigned long long wait_limit_ns;
+};
+
+constexpr int ERR_TIMEOUT = 2;
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of an mbarrier.  Gives up after limit_ns
+// nanoseconds of %globaltimer (or 2^28 polls, whichever comes first), records
+// ERR_TIMEOUT in the device report and returns false; never traps.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_ns, int *err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = globaltimer_ns();
+  for (uint32_t it = 1; it < (1u << 28); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) break;
+  }
+  atomicExch(err, ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size % 16 == 0).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Named barrier over the 256 compute threads (barrier 0 is __syncthreads).
+__device__ __forceinline__ void compute_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double flip_bit(double x, int bit) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (1ll << bit));
+}
+
+}  // namespace ftg

@@ -1,0 +1,159 @@
+// Operand checksum pass: per-tile checksum vectors of op(A) and op(B) and the
+// absolute sums the detection threshold uses (the A and B checksums of
+// FT-GEMM §2.2/§2.3).  One read of each operand; deterministic (fixed
+// reduction order, partials combined in a second small kernel).
+//
+// Both operands reduce to the same two shapes on a column-major X (R x S):
+//  SEG: groups of 128 consecutive rows; gsum[G][s] = sum_{r in G} X[r,s],
+//       gmax[G] = max_s sum_{r in G} |X[r,s]|, rabs[r] = sum_s |X[r,s]|.
+//       (op(A) with 'N': rows i, columns k.  op(B) with 'T': rows j, columns k.)
+//  STR: groups of 128 consecutive columns; gsum[G][r] = sum_{s in G} X[r,s],
+//       gmax[G] = max_r sum_{s in G} |X[r,s]|, cabs[s] = sum_r |X[r,s]|.
+//       (op(A) with 'T': rows k, columns i.  op(B) with 'N': rows k, columns j.)
+#pragma once
+
+#include "ftgemm_common.cuh"
+
+namespace ftg {
+
+constexpr int ENC_CW = 256;  // SEG: columns per block
+constexpr int ENC_RW = 256;  // STR: rows per block
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// grid (nG, ceil(S / ENC_CW)), 256 threads
+__global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__ X, long long R, long long S,
+                                                      long long ld, double *__restrict__ gsum, long long gstride,
+                                                      double *__restrict__ part_rabs, double *__restrict__ part_max) {
+  __shared__ double sh[8][128];
+  __shared__ double smx[8];
+  const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)G * 128;
+  double rabs[4] = {0.0, 0.0, 0.0, 0.0};
+  double mx = 0.0;
+  const long long s1 = min(S, (long long)(c + 1) * ENC_CW);
+  for (long long s = (long long)c * ENC_CW + w; s < s1; s += 8) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long r = r0 + lane + 32 * q;
+      v[q] = (r < R) ? X[r + s * ld] : 0.0;
+      rabs[q] += fabs(v[q]);
+    }
+    const double sum = warp_sum((v[0] + v[1]) + (v[2] + v[3]));
+    const double ab = warp_sum((fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3])));
+    if (lane == 0) {
+      gsum[(long long)G * gstride + s] = sum;
+      mx = fmax(mx, ab);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh[w][lane + 32 * q] = rabs[q];
+  if (lane == 0) smx[w] = mx;
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+    const long long r = r0 + threadIdx.x;
+    if (r < R) part_rabs[(long long)c * R + r] = t;
+  }
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int q = 0; q < 8; ++q) m = fmax(m, smx[q]);
+    part_max[(long long)c * nG + G] = m;
+  }
+}
+
+// grid (nG, ceil(R / ENC_RW)), 256 threads
+__global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__ X, long long R, long long S,
+                                                      long long ld, double *__restrict__ gsum, long long gstride,
+                                                      double *__restrict__ part_cabs, double *__restrict__ part_max) {
+  __shared__ double sh[8][128];
+  __shared__ double smx[8];
+  const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r = (long long)c * ENC_RW + threadIdx.x;
+  const long long s0 = (long long)G * 128;
+  const int ns = (int)min(128LL, S - s0);
+  double sum = 0.0, ab = 0.0;
+  for (int s = 0; s < ns; ++s) {
+    const double v = (r < R) ? X[r + (s0 + s) * ld] : 0.0;
+    sum += v;
+    ab += fabs(v);
+    const double wa = warp_sum(fabs(v));
+    if (lane == 0) sh[w][s] = wa;
+  }
+  if (r < R) gsum[(long long)G * gstride + r] = sum;
+  const double m = warp_max(ab);
+  if (lane == 0) smx[w] = m;
+  __syncthreads();
+  if (threadIdx.x < ns) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+    part_cabs[(long long)c * S + s0 + threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int q = 0; q < 8; ++q) mm = fmax(mm, smx[q]);
+    part_max[(long long)c * nG + G] = mm;
+  }
+}
+
+// abs[x] = sum_c part_abs[c][x] (x < L), gmax[G] = max_c part_max[c][G] (G < nG)
+__global__ void enc_finish_kernel(const double *__restrict__ part_abs, int nchunk, long long L,
+                                  double *__restrict__ abs_out, const double *__restrict__ part_max, int nG,
+                                  double *__restrict__ gmax) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < L) {
+    double t = 0.0;
+    for (int c = 0; c < nchunk; ++c) t += part_abs[(long long)c * L + x];
+    abs_out[x] = t;
+  }
+  if (x < nG) {
+    double m = 0.0;
+    for (int c = 0; c < nchunk; ++c) m = fmax(m, part_max[(long long)c * nG + x]);
+    gmax[x] = m;
+  }
+}
+
+// C <- beta*C (beta == 0 writes zeros without reading C)
+__global__ void scale_kernel(double *C, long long M, long long N, long long ldc, double beta) {
+  const long long total = M * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e % M, j = e / M;
+    double *c = C + i + j * ldc;
+    *c = (beta == 0.0) ? 0.0 : beta * *c;
+  }
+}
+
+// dst[r + c*ldd] = src[r + c*lds] for r < rows, c < cols
+__global__ void copy2d_kernel(const double *__restrict__ src, long long lds, double *__restrict__ dst, long long ldd,
+                              long long rows, long long cols) {
+  const long long total = rows * cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % rows, c = e / rows;
+    dst[r + c * ldd] = src[r + c * lds];
+  }
+}
+
+// One block waits on an mbarrier that nothing completes (test of the bounded wait).
+__global__ void wait_timeout_kernel(DevReport *rep, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_bounded(smem_u32(&bar), 0, limit_ns, &rep->err);
+}
+
+}  // namespace ftg

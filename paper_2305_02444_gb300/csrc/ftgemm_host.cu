@@ -1,0 +1,654 @@
+// Host side of libftgemm: the C ABI declared in include/ftgemm.h, argument
+// checks, workspace, TMA descriptors, the operand checksum pass, the fault
+// injection table and the report.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ftgemm.h"
+#include "ftgemm_common.cuh"
+#include "ftgemm_encode.cuh"
+
+namespace ftg {
+// main-kernel launchers, one translation unit per operand layout
+cudaError_t launch_main_nn(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                           const Params &, cudaStream_t);
+cudaError_t launch_main_nt(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                           const Params &, cudaStream_t);
+cudaError_t launch_main_tn(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                           const Params &, cudaStream_t);
+cudaError_t launch_main_tt(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
+                           const Params &, cudaStream_t);
+}  // namespace ftg
+
+using namespace ftg;
+
+namespace {
+
+constexpr long long LOC_CAP_DEV = 65536;
+constexpr int MAX_DEV = 64;
+
+std::atomic<long long> g_launches{0};
+std::mutex g_mu;
+
+struct Buf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+struct Workspace {
+  bool init = false;
+  Buf acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max;
+  Buf rep, loc, flips, tile_off;
+  Buf stA, stB, stC;        // aligned copies of unaligned operands
+  Buf hA, hB, hC;           // device copies for ftgemm_d_host
+  Buf pin;                  // pinned host staging (report, loc, injection upload)
+  // the last injected call, for ftgemm_injection_log
+  long long last_nflips = 0;
+  std::vector<long long> last_perm;  // sorted position -> original index
+};
+Workspace g_ws[MAX_DEV];
+
+// Optional CUDA-event timing of the library's own kernels (ftgemm_timing).
+struct TimingState {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> main_ev, aux_ev;
+} g_tim;
+
+void timing_record(std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, cudaEvent_t *a, cudaEvent_t *b) {
+  cudaEventCreate(a);
+  cudaEventCreate(b);
+  v.emplace_back(*a, *b);
+}
+
+struct InjState {
+  int mode = 0;
+  unsigned long long seed = 0;
+  long long count = 0;
+  std::vector<ftgemm_flip> list;
+} g_inj;
+
+bool is_n(char t) { return t == 'N' || t == 'n'; }
+bool is_t(char t) { return t == 'T' || t == 't' || t == 'C' || t == 'c'; }
+
+int check_args(char ta, char tb, long long M, long long N, long long K, long long lda, long long ldb,
+               long long ldc) {
+  if (!is_n(ta) && !is_t(ta)) return -1;
+  if (!is_n(tb) && !is_t(tb)) return -2;
+  if (M < 0) return -3;
+  if (N < 0) return -4;
+  if (K < 0) return -5;
+  const long long arows = is_n(ta) ? M : K, brows = is_n(tb) ? K : N;
+  if (lda < std::max(1LL, arows)) return -8;
+  if (ldb < std::max(1LL, brows)) return -10;
+  if (ldc < std::max(1LL, M)) return -13;
+  return 0;
+}
+
+int ensure(Buf &b, size_t bytes) {
+  if (b.cap >= bytes && b.p) return 0;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t n = std::max<size_t>(bytes, 256);
+  if (cudaMalloc(&b.p, n) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_NOMEM;
+  }
+  b.cap = n;
+  return 0;
+}
+
+int ensure_pinned(Buf &b, size_t bytes) {
+  if (b.cap >= bytes && b.p) return 0;
+  if (b.p) cudaFreeHost(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t n = std::max<size_t>(bytes, 4096);
+  if (cudaMallocHost(&b.p, n) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_NOMEM;
+  }
+  b.cap = n;
+  return 0;
+}
+
+Workspace *workspace(int *dev_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *dev_out = dev;
+  Workspace &w = g_ws[dev];
+  if (!w.init) {
+    if (ensure(w.rep, sizeof(DevReport)) || ensure(w.loc, sizeof(DevLoc) * LOC_CAP_DEV)) return nullptr;
+    w.init = true;
+  }
+  return &w;
+}
+
+unsigned long long wait_limit_ns() {
+  static unsigned long long v = [] {
+    const char *e = getenv("FTGEMM_WAIT_LIMIT_NS");
+    unsigned long long x = e ? strtoull(e, nullptr, 10) : 0;
+    return x ? x : 2000000000ull;  // 2 s: a slab normally lands within microseconds
+  }();
+  return v;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// 2-D fp64 tensor map of a column-major matrix with `rows` x `cols` and leading dimension ld.
+int make_map(CUtensorMap *m, const double *ptr, long long rows, long long cols, long long ld, int box0, int box1,
+             bool swizzle128) {
+  auto fn = encode_fn();
+  if (!fn) return FTGEMM_ERR_TENSORMAP;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+  cuuint32_t box[2] = {(cuuint32_t)box0, (cuuint32_t)box1};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : FTGEMM_ERR_TENSORMAP;
+}
+
+bool tma_ok(const void *p, long long ld) {
+  return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && (ld % 2 == 0) && (ld * 8 < (1LL << 40));
+}
+
+int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
+
+cudaError_t launch_copy(const double *src, long long lds, double *dst, long long ldd, long long rows,
+                        long long cols, cudaStream_t s) {
+  copy2d_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+  g_launches++;
+  return cudaGetLastError();
+}
+
+uint64_t splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Encode the operand checksum vectors (see ftgemm_encode.cuh).  Writes
+// acs (nI x Kp), aabsmax, arowabs, bcs (nJ x Kp), babsmax, bcolabs.
+int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, const double *A, long long lda,
+               const double *B, long long ldb, long long Kp, double *acs, double *aabsmax, double *arowabs,
+               double *bcs, double *babsmax, double *bcolabs, Workspace &w, cudaStream_t s) {
+  const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN;
+  // partial buffers: worst case over the two operands
+  auto part_need = [&](long long R, long long S, bool seg) -> long long {
+    const long long nch = seg ? (S + ENC_CW - 1) / ENC_CW : (R + ENC_RW - 1) / ENC_RW;
+    return nch * (seg ? R : S);
+  };
+  auto max_need = [&](long long R, long long S, bool seg) -> long long {
+    const long long nch = seg ? (S + ENC_CW - 1) / ENC_CW : (R + ENC_RW - 1) / ENC_RW;
+    return nch * (seg ? (R + 127) / 128 : (S + 127) / 128);
+  };
+  const long long pa = std::max(ta_t ? part_need(K, M, false) : part_need(M, K, true),
+                                tb_t ? part_need(N, K, true) : part_need(K, N, false));
+  const long long pm = std::max(ta_t ? max_need(K, M, false) : max_need(M, K, true),
+                                tb_t ? max_need(N, K, true) : max_need(K, N, false));
+  if (ensure(w.part_abs, sizeof(double) * pa) || ensure(w.part_max, sizeof(double) * pm)) return FTGEMM_ERR_NOMEM;
+  double *part_abs = (double *)w.part_abs.p, *part_max = (double *)w.part_max.p;
+  if (Kp != K) {
+    cudaMemsetAsync(acs, 0, sizeof(double) * nI * Kp, s);
+    cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
+  }
+  // op(A): SEG over stored A (M x K) for 'N', STR over stored A (K x M) for 'T'
+  if (!ta_t) {
+    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
+    enc_seg_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, M, K, lda, acs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
+                                                                 aabsmax);
+  } else {
+    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
+    enc_str_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, K, M, lda, acs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
+                                                                 aabsmax);
+  }
+  // op(B): STR over stored B (K x N) for 'N', SEG over stored B (N x K) for 'T'
+  if (!tb_t) {
+    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
+    enc_str_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, K, N, ldb, bcs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
+                                                                 babsmax);
+  } else {
+    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
+    enc_seg_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, N, K, ldb, bcs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
+                                                                 babsmax);
+  }
+  g_launches += 4;
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+}
+
+void zero_report(ftgemm_report *rep) {
+  if (!rep) return;
+  rep->detected = rep->corrected = rep->checksum_only = rep->unverifiable = 0;
+  rep->flagged_rows = rep->flagged_cols = rep->recomputed = rep->n_loc = 0;
+}
+
+// Build and upload the injection table for this call (FT path only).
+int upload_injection(long long M, long long N, long long nks, long long nI, long long ntiles, Workspace &w,
+                     cudaStream_t s, Params &p, bool *inj) {
+  *inj = false;
+  if (g_inj.mode == 0) return 0;
+  std::vector<ftgemm_flip> L;
+  if (g_inj.mode == 1) {
+    L.resize((size_t)std::max(0LL, g_inj.count));
+    for (long long f = 0; f < (long long)L.size(); ++f) {
+      L[f].row = (long long)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 0) % (uint64_t)M);
+      L[f].col = (long long)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 1) % (uint64_t)N);
+      L[f].kstep = (long long)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 2) % (uint64_t)nks);
+      L[f].bit = (int)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 3) % 63u);
+      L[f].pad = 0;
+    }
+  } else {
+    L = g_inj.list;
+  }
+  for (const auto &f : L)
+    if (f.row < 0 || f.row >= M || f.col < 0 || f.col >= N || f.kstep < 0 || f.kstep >= nks || f.bit < 0 ||
+        f.bit > 62)
+      return FTGEMM_ERR_INJECT;
+  const long long nf = (long long)L.size();
+  std::vector<long long> perm(nf);
+  for (long long q = 0; q < nf; ++q) perm[q] = q;
+  auto tile_of = [&](const ftgemm_flip &f) { return (f.row / BM) + (f.col / BN) * nI; };
+  std::stable_sort(perm.begin(), perm.end(), [&](long long a, long long b) {
+    const long long ta = tile_of(L[a]), tb = tile_of(L[b]);
+    return ta != tb ? ta < tb : L[a].kstep < L[b].kstep;
+  });
+  const size_t fbytes = sizeof(DevFlip) * (size_t)std::max(1LL, nf);
+  const size_t obytes = sizeof(int) * (size_t)(ntiles + 1);
+  if (ensure(w.flips, fbytes) || ensure(w.tile_off, obytes) || ensure_pinned(w.pin, fbytes + obytes + 4096))
+    return FTGEMM_ERR_NOMEM;
+  // the pinned buffer may still be read by an earlier async copy: wait for the stream
+  cudaStreamSynchronize(s);
+  DevFlip *hf = (DevFlip *)w.pin.p;
+  int *ho = (int *)((char *)w.pin.p + fbytes);
+  std::fill(ho, ho + ntiles + 1, 0);
+  for (long long q = 0; q < nf; ++q) {
+    const ftgemm_flip &f = L[perm[q]];
+    hf[q].row = f.row; hf[q].col = f.col; hf[q].kstep = f.kstep; hf[q].bit = f.bit;
+    hf[q].applied = 0; hf[q].before = 0.0; hf[q].after = 0.0;
+    ho[tile_of(f) + 1]++;
+  }
+  for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
+  cudaMemcpyAsync(w.flips.p, hf, sizeof(DevFlip) * nf, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w.tile_off.p, ho, obytes, cudaMemcpyHostToDevice, s);
+  w.last_nflips = nf;
+  w.last_perm = perm;
+  p.flips = (DevFlip *)w.flips.p;
+  p.tile_off = (const int *)w.tile_off.p;
+  *inj = true;
+  return 0;
+}
+
+int gemm_impl(char transA, char transB, long long M, long long N, long long K, double alpha, const double *A,
+              long long lda, const double *B, long long ldb, double beta, double *C, long long ldc,
+              ftgemm_report *rep, cudaStream_t s, bool ft) {
+  int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
+  if (rc) return rc;
+  zero_report(rep);
+  if (M == 0 || N == 0) return 0;
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return FTGEMM_ERR_NODEVICE;
+  Workspace &w = *wp;
+  if (K == 0 || alpha == 0.0) {
+    if (beta != 1.0) {
+      scale_kernel<<<grid_for(M * N), 256, 0, s>>>(C, M, N, ldc, beta);
+      g_launches++;
+    }
+    if (rep && cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+  }
+  const bool ta_t = is_t(transA), tb_t = is_t(transB);
+  const long long arows = ta_t ? K : M, acols = ta_t ? M : K;
+  const long long brows = tb_t ? N : K, bcols = tb_t ? K : N;
+
+  // operands the TMA cannot address directly are copied to aligned workspace
+  const double *Ause = A, *Buse = B;
+  double *Cuse = C;
+  long long ldaU = lda, ldbU = ldb, ldcU = ldc;
+  bool c_staged = false;
+  if (!tma_ok(A, lda)) {
+    ldaU = (arows + 1) & ~1LL;
+    if (ensure(w.stA, sizeof(double) * ldaU * acols)) return FTGEMM_ERR_NOMEM;
+    launch_copy(A, lda, (double *)w.stA.p, ldaU, arows, acols, s);
+    Ause = (const double *)w.stA.p;
+  }
+  if (!tma_ok(B, ldb)) {
+    ldbU = (brows + 1) & ~1LL;
+    if (ensure(w.stB, sizeof(double) * ldbU * bcols)) return FTGEMM_ERR_NOMEM;
+    launch_copy(B, ldb, (double *)w.stB.p, ldbU, brows, bcols, s);
+    Buse = (const double *)w.stB.p;
+  }
+  if (!tma_ok(C, ldc)) {
+    ldcU = (M + 1) & ~1LL;
+    if (ensure(w.stC, sizeof(double) * ldcU * N)) return FTGEMM_ERR_NOMEM;
+    if (beta != 0.0) launch_copy(C, ldc, (double *)w.stC.p, ldcU, M, N, s);
+    Cuse = (double *)w.stC.p;
+    c_staged = true;
+  }
+
+  CUtensorMap mA, mB, mC;
+  if (ta_t) rc = make_map(&mA, Ause, K, M, ldaU, BK, BM, true);
+  else rc = make_map(&mA, Ause, M, K, ldaU, BM, BK, false);
+  if (!rc) {
+    if (tb_t) rc = make_map(&mB, Buse, N, K, ldbU, BN, BK, false);
+    else rc = make_map(&mB, Buse, K, N, ldbU, BK, BN, true);
+  }
+  if (!rc) rc = make_map(&mC, Cuse, M, N, ldcU, BM, BN, false);
+  if (rc) return rc;
+
+  const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN, ntiles = nI * nJ;
+  const long long nks = (K + BK - 1) / BK, Kp = nks * BK;
+  Params p;
+  memset(&p, 0, sizeof(p));
+  p.M = M; p.N = N; p.K = K; p.alpha = alpha; p.beta = beta;
+  p.A = Ause; p.B = Buse; p.C = Cuse; p.lda = ldaU; p.ldb = ldbU; p.ldc = ldcU;
+  p.nI = (int)nI; p.nJ = (int)nJ; p.nks = (int)nks; p.Kp = Kp;
+  p.rep = (DevReport *)w.rep.p;
+  p.loc = (DevLoc *)w.loc.p;
+  p.loc_cap = LOC_CAP_DEV;
+  p.wait_limit_ns = wait_limit_ns();
+  cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
+
+  cudaEvent_t ea0 = nullptr, ea1 = nullptr, em0 = nullptr, em1 = nullptr;
+  if (g_tim.on) {
+    timing_record(g_tim.aux_ev, &ea0, &ea1);
+    timing_record(g_tim.main_ev, &em0, &em1);
+    cudaEventRecord(ea0, s);
+  }
+  bool inj = false;
+  if (ft) {
+    if (ensure(w.acs, sizeof(double) * nI * Kp) || ensure(w.bcs, sizeof(double) * nJ * Kp) ||
+        ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
+        ensure(w.bcolabs, sizeof(double) * N) || ensure(w.babsmax, sizeof(double) * nJ))
+      return FTGEMM_ERR_NOMEM;
+    rc = run_encode(ta_t, tb_t, M, N, K, Ause, ldaU, Buse, ldbU, Kp, (double *)w.acs.p, (double *)w.aabsmax.p,
+                    (double *)w.arowabs.p, (double *)w.bcs.p, (double *)w.babsmax.p, (double *)w.bcolabs.p, w, s);
+    if (rc) return rc;
+    p.acs = (const double *)w.acs.p; p.bcs = (const double *)w.bcs.p;
+    p.arowabs = (const double *)w.arowabs.p; p.aabsmax = (const double *)w.aabsmax.p;
+    p.bcolabs = (const double *)w.bcolabs.p; p.babsmax = (const double *)w.babsmax.p;
+    rc = upload_injection(M, N, nks, nI, ntiles, w, s, p, &inj);
+    if (rc) return rc;
+  }
+
+  if (g_tim.on) {
+    cudaEventRecord(ea1, s);
+    cudaEventRecord(em0, s);
+  }
+  cudaError_t e;
+  if (!ta_t && !tb_t) e = launch_main_nn(ft, inj, mA, mB, mC, p, s);
+  else if (!ta_t && tb_t) e = launch_main_nt(ft, inj, mA, mB, mC, p, s);
+  else if (ta_t && !tb_t) e = launch_main_tn(ft, inj, mA, mB, mC, p, s);
+  else e = launch_main_tt(ft, inj, mA, mB, mC, p, s);
+  g_launches++;
+  if (g_tim.on) cudaEventRecord(em1, s);
+  if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
+  if (c_staged) launch_copy(Cuse, ldcU, C, ldc, M, N, s);
+
+  if (rep) {
+    const long long ncopy = std::min<long long>(std::max<long long>(rep->cap, 0), LOC_CAP_DEV);
+    const size_t need = sizeof(DevReport) + sizeof(DevLoc) * (size_t)ncopy;
+    if (inj) cudaStreamSynchronize(s);  // the pinned buffer held the injection upload
+    if (ensure_pinned(w.pin, need + 4096)) return FTGEMM_ERR_NOMEM;
+    DevReport *hr = (DevReport *)w.pin.p;
+    DevLoc *hl = (DevLoc *)((char *)w.pin.p + sizeof(DevReport));
+    cudaMemcpyAsync(hr, w.rep.p, sizeof(DevReport), cudaMemcpyDeviceToHost, s);
+    if (ncopy > 0 && rep->loc) cudaMemcpyAsync(hl, w.loc.p, sizeof(DevLoc) * ncopy, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+    rep->detected = (long long)hr->detected;
+    rep->corrected = (long long)hr->corrected;
+    rep->checksum_only = (long long)hr->checksum_only;
+    rep->unverifiable = (long long)hr->unverifiable;
+    rep->flagged_rows = (long long)hr->flagged_rows;
+    rep->flagged_cols = (long long)hr->flagged_cols;
+    rep->recomputed = (long long)hr->recomputed;
+    rep->n_loc = (long long)hr->n_loc;
+    if (rep->loc)
+      for (long long q = 0; q < std::min<long long>(ncopy, rep->n_loc); ++q) {
+        rep->loc[q].row = hl[q].row;
+        rep->loc[q].col = hl[q].col;
+        rep->loc[q].tile = hl[q].tile;
+        rep->loc[q].kind = hl[q].kind;
+        rep->loc[q].delta = hl[q].delta;
+      }
+    if (hr->err) return FTGEMM_ERR_TIMEOUT;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ftgemm_d(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+             int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, ftgemm_report *rep,
+             void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return gemm_impl(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rep, (cudaStream_t)stream, true);
+}
+
+int ftgemm_d_noft(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                  int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return gemm_impl(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, (cudaStream_t)stream,
+                   false);
+}
+
+int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                  int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, ftgemm_report *rep,
+                  void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
+  if (rc) return rc;
+  zero_report(rep);
+  if (M == 0 || N == 0) return 0;
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return FTGEMM_ERR_NODEVICE;
+  Workspace &w = *wp;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long acols = is_n(transA) ? K : M, bcols = is_n(transB) ? N : K;
+  const size_t abytes = sizeof(double) * (size_t)(lda * acols), bbytes = sizeof(double) * (size_t)(ldb * bcols);
+  const size_t cbytes = sizeof(double) * (size_t)(ldc * N);
+  if (ensure(w.hA, abytes) || ensure(w.hB, bbytes) || ensure(w.hC, cbytes)) return FTGEMM_ERR_NOMEM;
+  if (K > 0 && alpha != 0.0) {
+    if (abytes) cudaMemcpyAsync(w.hA.p, A, abytes, cudaMemcpyHostToDevice, s);
+    if (bbytes) cudaMemcpyAsync(w.hB.p, B, bbytes, cudaMemcpyHostToDevice, s);
+  }
+  if (beta != 0.0) cudaMemcpyAsync(w.hC.p, C, cbytes, cudaMemcpyHostToDevice, s);
+  ftgemm_report local;
+  memset(&local, 0, sizeof(local));
+  ftgemm_report *r = rep ? rep : &local;
+  rc = gemm_impl(transA, transB, M, N, K, alpha, (const double *)w.hA.p, lda, (const double *)w.hB.p, ldb, beta,
+                 (double *)w.hC.p, ldc, r, s, true);
+  if (rc && rc != FTGEMM_ERR_TIMEOUT) return rc;
+  cudaMemcpyAsync(C, w.hC.p, cbytes, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  return rc;
+}
+
+int ftgemm_encode_operands(char transA, char transB, int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                           const double *B, int64_t ldb, double *acs, double *aabsmax, double *arowabs, double *bcs,
+                           double *babsmax, double *bcolabs, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int rc = check_args(transA, transB, M, N, K, lda, ldb, std::max<int64_t>(1, M));
+  if (rc) return rc;
+  if (M == 0 || N == 0 || K == 0) return 0;
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return FTGEMM_ERR_NODEVICE;
+  return run_encode(is_t(transA), is_t(transB), M, N, K, A, lda, B, ldb, K, acs, aabsmax, arowabs, bcs, babsmax,
+                    bcolabs, *wp, (cudaStream_t)stream);
+}
+
+int ftgemm_set_injection(const ftgemm_inject *cfg) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!cfg || cfg->mode == 0) {
+    g_inj.mode = 0;
+    g_inj.list.clear();
+    return 0;
+  }
+  if (cfg->mode == 1) {
+    if (cfg->count < 0) return -1;
+    g_inj.mode = 1;
+    g_inj.seed = cfg->seed;
+    g_inj.count = cfg->count;
+    g_inj.list.clear();
+    return 0;
+  }
+  if (cfg->mode == 2) {
+    if (cfg->n_list < 0 || (cfg->n_list > 0 && !cfg->list)) return -1;
+    g_inj.mode = 2;
+    g_inj.list.assign(cfg->list, cfg->list + cfg->n_list);
+    return 0;
+  }
+  return -1;
+}
+
+int64_t ftgemm_injection_log(ftgemm_flip_log *out, int64_t cap) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (cap > 0 && !out) return -1;
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return -FTGEMM_ERR_NODEVICE;
+  Workspace &w = *wp;
+  const long long nf = w.last_nflips;
+  if (nf == 0 || cap <= 0) return nf;
+  std::vector<DevFlip> h((size_t)nf);
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(h.data(), w.flips.p, sizeof(DevFlip) * nf, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -FTGEMM_ERR_CUDA;
+  for (long long q = 0; q < nf; ++q) {
+    const long long o = w.last_perm[q];
+    if (o >= cap) continue;
+    out[o].row = h[q].row;
+    out[o].col = h[q].col;
+    out[o].kstep = h[q].kstep;
+    out[o].bit = h[q].bit;
+    out[o].applied = h[q].applied;
+    out[o].before = h[q].before;
+    out[o].after = h[q].after;
+  }
+  return nf;
+}
+
+int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return FTGEMM_ERR_NODEVICE;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevReport *r = (DevReport *)wp->rep.p;
+  cudaMemsetAsync(r, 0, sizeof(DevReport), s);
+  wait_timeout_kernel<<<1, 32, 0, s>>>(r, (unsigned long long)std::max<int64_t>(limit_ns, 1));
+  g_launches++;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, &r->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FTGEMM_ERR_CUDA;
+  return err == ERR_TIMEOUT ? FTGEMM_ERR_TIMEOUT : (err ? err : 0);
+}
+
+int64_t ftgemm_launch_count(void) { return g_launches.load(); }
+
+int ftgemm_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto *v : {&g_tim.main_ev, &g_tim.aux_ev}) {
+    for (auto &pr : *v) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    v->clear();
+  }
+  g_tim.on = enable != 0;
+  return 0;
+}
+
+int ftgemm_timing_read(double *main_ms, int64_t *main_launches, double *aux_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  double tm = 0.0, ta = 0.0;
+  for (auto &pr : g_tim.main_ev) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+      return FTGEMM_ERR_CUDA;
+    tm += ms;
+  }
+  for (auto &pr : g_tim.aux_ev) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+      return FTGEMM_ERR_CUDA;
+    ta += ms;
+  }
+  if (main_ms) *main_ms = tm;
+  if (aux_ms) *aux_ms = ta;
+  if (main_launches) *main_launches = (int64_t)g_tim.main_ev.size();
+  return 0;
+}
+
+const char *ftgemm_strerror(int code) {
+  if (code == 0) return "success";
+  if (code < 0) return "invalid argument (see the BLAS argument number)";
+  switch (code) {
+    case FTGEMM_ERR_CUDA: return "CUDA runtime call or kernel launch failed";
+    case FTGEMM_ERR_TIMEOUT: return "bounded device pipeline wait expired";
+    case FTGEMM_ERR_NODEVICE: return "no usable CUDA device";
+    case FTGEMM_ERR_NOMEM: return "workspace allocation failed";
+    case FTGEMM_ERR_INJECT: return "injected fault outside the problem";
+    case FTGEMM_ERR_TENSORMAP: return "TMA descriptor encoding failed";
+    default: return "unknown error";
+  }
+}
+
+int ftgemm_finalize(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return FTGEMM_ERR_NODEVICE;
+  Workspace &w = g_ws[dev];
+  cudaDeviceSynchronize();
+  Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
+                  &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC};
+  for (Buf *b : dbufs) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->cap = 0;
+  }
+  if (w.pin.p) cudaFreeHost(w.pin.p);
+  w.pin.p = nullptr;
+  w.pin.cap = 0;
+  w.init = false;
+  w.last_nflips = 0;
+  w.last_perm.clear();
+  return 0;
+}
+
+}  // extern "C"

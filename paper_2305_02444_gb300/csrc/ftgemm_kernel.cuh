@@ -1,0 +1,423 @@
+// The FT-DGEMM kernel for sm_103a.
+//
+// One CTA computes one BM x BN tile of C = alpha*op(A)*op(B) + beta*C:
+//  - thread 0 streams BK-deep slabs of op(A) and op(B) into a ring of
+//    shared-memory stages with TMA (cp.async.bulk.tensor), together with the
+//    matching BK-slabs of the operand checksum vectors (bulk copies); a
+//    separate producer warp would cap the 9-warp CTA at 168 registers/thread;
+//  - 8 compute warps accumulate an 8x8 register tile per thread with DFMA
+//    (on GB300, DFMA is the fastest FP64 path: FP64 mma.sync shares its pipe
+//    and issues fewer flops) and, while the slab is staged, fold it into the
+//    predicted checksums: column j gets sum_k acs_I[k] * B(k,j), row i gets
+//    sum_k A(i,k) * bcs_J[k] (the reuse of each staged operand load for the
+//    checksum updates of FT-GEMM §2.2);
+//  - the epilogue reads beta*C once (TMA), forms out = alpha*acc + beta*C,
+//    adds beta * (row/column sums of C) to the predicted checksums (the
+//    encoding of C^c and C^r fused with C = beta*C, §2.2), sums the reference
+//    checksums of out before it leaves the chip (§2.2), compares, and on a
+//    mismatch recomputes the flagged elements (readings: per-tile
+//    verification, a-priori rounding threshold, intersection recompute with
+//    a segment fallback), then stores the tile with one TMA store.
+// FT = false compiles the same kernel without any checksum work (the
+// unprotected baseline); INJ adds the source-level fault injector (§3.2).
+#pragma once
+
+#include "ftgemm_common.cuh"
+
+namespace ftg {
+
+// Byte offset of element (row, k) of a [rows][16] fp64 tile written by TMA with
+// 128-byte swizzle: the 16-byte chunk index is XORed with row % 8.
+__device__ __forceinline__ int swz_off(int row, int k) {
+  return row * 128 + ((((k >> 1) ^ (row & 7)) << 4) | ((k & 1) << 3));
+}
+
+// op(A)(i,k) of the staged slab: 'N' slabs are [BK][BM] (i contiguous),
+// 'T' slabs are [BM][BK] swizzled.
+template <bool TA>
+__device__ __forceinline__ double stage_a(const unsigned char *sA, int i, int k) {
+  if (TA) return *reinterpret_cast<const double *>(sA + swz_off(i, k));
+  return reinterpret_cast<const double *>(sA)[k * BM + i];
+}
+// op(B)(k,j): 'N' slabs are [BN][BK] swizzled, 'T' slabs are [BK][BN].
+template <bool TB>
+__device__ __forceinline__ double stage_b(const unsigned char *sB, int k, int j) {
+  if (TB) return reinterpret_cast<const double *>(sB)[k * BN + j];
+  return *reinterpret_cast<const double *>(sB + swz_off(j, k));
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ double glob_a(const Params &p, long long i, long long k) {
+  return TA ? p.A[k + i * p.lda] : p.A[i + k * p.lda];
+}
+template <bool TA, bool TB>
+__device__ __forceinline__ double glob_b(const Params &p, long long k, long long j) {
+  return TB ? p.B[j + k * p.ldb] : p.B[k + j * p.ldb];
+}
+
+// counters in shared memory
+enum { C_NR = 0, C_NC, C_DET, C_CSONLY, C_UNVER, C_RECOMP, C_ABORT, C_FAIL, C_NCNT };
+
+// Recompute element (il, jl) of the tile from the original operands with one
+// warp (lanes split k), compare with the staged value and rewrite it.
+template <bool TA, bool TB>
+__device__ __forceinline__ void recompute_elem(const Params &p, double *sC, int *cnt, int tile,
+                                               long long i0, long long j0, int il, int jl,
+                                               int kind, bool use_c, int lane) {
+  const long long gi = i0 + il, gj = j0 + jl;
+  double dot = 0.0, ab = 0.0;
+  for (long long k = lane; k < p.K; k += 32) {
+    const double a = glob_a<TA, TB>(p, gi, k), b = glob_b<TA, TB>(p, k, gj);
+    dot = fma(a, b, dot);
+    ab = fma(fabs(a), fabs(b), ab);
+  }
+  dot = warp_sum(dot);
+  ab = warp_sum(ab);
+  if (lane == 0) {
+    const double c = use_c ? p.C[gi + gj * p.ldc] : 0.0;
+    const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
+    const double E = fabs(p.alpha) * ab + (use_c ? fabs(p.beta) * fabs(c) : 0.0);
+    const double n = (double)(p.K + 3);
+    const double te = 2.01 * n * 0x1p-53 * E + n * 0x1p-1021;
+    const double old = sC[jl * BM + il];
+    const bool wrong = (!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te;
+    atomicAdd(&cnt[C_RECOMP], 1);
+    if (wrong) {
+      atomicAdd(&cnt[C_DET], 1);
+      const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
+      if ((long long)q < p.loc_cap) {
+        DevLoc L;
+        L.row = gi; L.col = gj; L.tile = tile; L.kind = kind; L.delta = old - nv;
+        p.loc[q] = L;
+      }
+    }
+    sC[jl * BM + il] = nv;
+  }
+}
+
+template <bool TA, bool TB, bool FT, bool INJ>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ftdgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, const Params p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  double *epi = reinterpret_cast<double *>(smem + TILE_REGION);
+  double *s_rc = epi, *s_rca = epi + 128, *s_cc = epi + 256, *s_cca = epi + 384;
+  double *s_ro = epi + 512, *s_co = epi + 640, *s_pr = epi + 768, *s_pc = epi + 896;
+  double *s_tr = epi + 1024, *s_tc = epi + 1152;
+  int *s_fr = reinterpret_cast<int *>(epi + 1280);
+  int *s_fc = s_fr + 128, *s_rfail = s_fc + 128, *s_cfail = s_rfail + 128;
+  int *cnt = s_cfail + 128;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + TILE_REGION + EPI_BYTES);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), cbar = smem_u32(bars + 2 * STAGES);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x;
+  const int I = tile % p.nI, J = tile / p.nI;
+  const int i0 = I * BM, j0 = J * BN;
+  const int mI = (int)min((long long)BM, p.M - i0), nJt = (int)min((long long)BN, p.N - j0);
+  const int nks = p.nks;
+  const unsigned long long limit = p.wait_limit_ns;
+  int *err = &p.rep->err;
+  double *sC = reinterpret_cast<double *>(smem);  // output tile, column-major [BN][BM]
+
+  if (tid == 0) {
+    for (int c = 0; c < C_NCNT; ++c) cnt[c] = 0;
+    cnt[C_ABORT] = (*reinterpret_cast<volatile int *>(err) != 0);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, NCOMPUTE / 32);
+    }
+    mbar_init(cbar, 1);
+    fence_mbar_init();
+  }
+  if (tid == 32) {
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    prefetch_tmap(&tmC);
+  }
+  if (tid < 128) { s_rfail[tid] = 0; s_cfail[tid] = 0; }
+  __syncthreads();
+  if (cnt[C_ABORT]) return;  // an earlier CTA hit a timeout: skip the work
+
+  // ------------------------------------------------------------------ compute
+  // Thread 0 is also the producer: it fills the first STAGES slabs, then after
+  // each slab refills the stage that the previous slab freed.
+  const uint32_t tx_bytes = FT ? A_BYTES + B_BYTES + 2 * CS_BYTES : A_BYTES + B_BYTES;
+  auto issue = [&](int s) {
+    const int st = s % STAGES;
+    const uint32_t sb = smem_u32(smem + st * STAGE_BYTES);
+    const uint32_t fb = full0 + 8 * st;
+    mbar_arrive_expect_tx(fb, tx_bytes);
+    const int k0 = s * BK;
+    if (TA) tma_load_2d(sb, &tmA, fb, k0, i0); else tma_load_2d(sb, &tmA, fb, i0, k0);
+    if (TB) tma_load_2d(sb + A_BYTES, &tmB, fb, j0, k0); else tma_load_2d(sb + A_BYTES, &tmB, fb, k0, j0);
+    if (FT) {
+      bulk_load(sb + A_BYTES + B_BYTES, p.acs + (long long)I * p.Kp + k0, CS_BYTES, fb);
+      bulk_load(sb + A_BYTES + B_BYTES + CS_BYTES, p.bcs + (long long)J * p.Kp + k0, CS_BYTES, fb);
+    }
+  };
+  int issued = 0;
+  if (tid == 0) {
+    for (; issued < STAGES && issued < nks; ++issued) issue(issued);
+  }
+
+  const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16*pp, columns ty + 16*qq
+  double acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+  double csacc = 0.0;  // FT: predicted column (tid < 128) or row (tid >= 128) checksum
+  int fptr = 0, fend = 0;
+  if (INJ) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+
+  bool ok = true;
+  for (int s = 0; s < nks; ++s) {
+    const int st = s % STAGES;
+    if (!mbar_wait_bounded(full0 + 8 * st, (s / STAGES) & 1, limit, err)) { ok = false; break; }
+    const unsigned char *sA = smem + st * STAGE_BYTES;
+    const unsigned char *sB = sA + A_BYTES;
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      double a[8], b[8];
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp) a[pp] = stage_a<TA>(sA, tx + 16 * pp, k);
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) b[qq] = stage_b<TB>(sB, k, ty + 16 * qq);
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) acc[pp][qq] = fma(a[pp], b[qq], acc[pp][qq]);
+    }
+    if (FT) {
+      const double *scs = reinterpret_cast<const double *>(sA + A_BYTES + B_BYTES);
+      if (tid < 128) {
+#pragma unroll
+        for (int k = 0; k < BK; ++k) csacc = fma(scs[k], stage_b<TB>(sB, k, tid), csacc);
+      } else {
+#pragma unroll
+        for (int k = 0; k < BK; ++k) csacc = fma(stage_a<TA>(sA, tid - 128, k), scs[BK + k], csacc);
+      }
+    }
+    if (INJ) {
+      while (fptr < fend) {
+        DevFlip *f = p.flips + fptr;
+        if (f->kstep != s) break;
+        const int il = (int)(f->row - i0), jl = (int)(f->col - j0);
+        if ((il & 15) == tx && (jl & 15) == ty) {
+          const int pq = (il >> 4) * 8 + (jl >> 4);
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+              if (a * 8 + b == pq) {
+                const double before = acc[a][b];
+                acc[a][b] = flip_bit(before, f->bit);
+                f->before = before;
+                f->after = acc[a][b];
+                f->applied = 1;
+              }
+        }
+        ++fptr;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty0 + 8 * st);
+    if (tid == 0 && s >= 1 && issued < nks) {
+      // refill the stage of slab s-1 once every warp has released it
+      const int sp = s - 1;
+      if (!mbar_wait_bounded(empty0 + 8 * (sp % STAGES), (sp / STAGES) & 1, limit, err)) { ok = false; break; }
+      issue(issued++);
+    }
+  }
+  if (!ok) {
+    atomicExch(&cnt[C_ABORT], 1);
+    if (tid == 0)  // give the copies already in flight a bounded chance to land
+      for (int s = issued > STAGES ? issued - STAGES : 0; s < issued; ++s)
+        mbar_wait_bounded(full0 + 8 * (s % STAGES), (s / STAGES) & 1, limit, err);
+  }
+  fence_proxy_async_smem();  // generic reads of the ring precede the async C load
+  compute_sync();
+  if (*reinterpret_cast<volatile int *>(&cnt[C_ABORT])) return;
+
+  // ----------------------------------------------------------------- epilogue
+  const bool use_c = (p.beta != 0.0);
+  if (use_c) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(cbar, CTILE_BYTES);
+      tma_load_2d(smem_u32(sC), &tmC, cbar, i0, j0);
+    }
+    if (!mbar_wait_bounded(cbar, 0, limit, err)) atomicExch(&cnt[C_ABORT], 1);
+    compute_sync();  // every thread leaves together if the C tile never landed
+    if (*reinterpret_cast<volatile int *>(&cnt[C_ABORT])) return;
+  }
+
+  // beta-side sums of C for the predicted checksums and the thresholds
+  if (FT && use_c) {
+    if (tid < 128) {
+      double s = 0.0, a = 0.0;
+      for (int j = 0; j < BN; ++j) {
+        const double c = sC[j * BM + tid];
+        s += c;
+        a += fabs(c);
+      }
+      s_rc[tid] = s;
+      s_rca[tid] = a;
+    } else {
+      const int w = warp - 4;
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = w * 32 + jj;
+        const double v0 = sC[j * BM + lane], v1 = sC[j * BM + lane + 32];
+        const double v2 = sC[j * BM + lane + 64], v3 = sC[j * BM + lane + 96];
+        const double s = warp_sum((v0 + v1) + (v2 + v3));
+        const double a = warp_sum((fabs(v0) + fabs(v1)) + (fabs(v2) + fabs(v3)));
+        if (lane == 0) { s_cc[j] = s; s_cca[j] = a; }
+      }
+    }
+  }
+  if (FT) compute_sync();
+
+  // out = alpha*acc + beta*C, written over the staged C tile
+#pragma unroll
+  for (int pp = 0; pp < 8; ++pp)
+#pragma unroll
+    for (int qq = 0; qq < 8; ++qq) {
+      const int idx = (ty + 16 * qq) * BM + tx + 16 * pp;
+      sC[idx] = use_c ? fma(p.alpha, acc[pp][qq], p.beta * sC[idx]) : p.alpha * acc[pp][qq];
+    }
+  compute_sync();
+
+  if (FT) {
+    // reference checksums of the computed tile
+    if (tid < 128) {
+      double s = 0.0;
+      for (int j = 0; j < BN; ++j) s += sC[j * BM + tid];
+      s_ro[tid] = s;
+    } else {
+      const int w = warp - 4;
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = w * 32 + jj;
+        const double s = warp_sum((sC[j * BM + lane] + sC[j * BM + lane + 32]) +
+                                  (sC[j * BM + lane + 64] + sC[j * BM + lane + 96]));
+        if (lane == 0) s_co[j] = s;
+      }
+    }
+    compute_sync();
+    // verify: predicted vs reference, per column (tid < 128) and per row
+    {
+      const double u = 0x1p-53;
+      if (tid < 128) {
+        const int j = tid;
+        if (j < nJt) {
+          const double pc = use_c ? fma(p.alpha, csacc, p.beta * s_cc[j]) : p.alpha * csacc;
+          const double S = fabs(p.alpha) * p.bcolabs[j0 + j] * p.aabsmax[I] + (use_c ? fabs(p.beta) * s_cca[j] : 0.0);
+          const double n = (double)(p.K + mI + 3);
+          const double tau = 2.01 * n * u * S + n * 0x1p-1021;
+          s_pc[j] = pc;
+          s_tc[j] = tau;
+          if (!isfinite(pc)) atomicAdd(&cnt[C_UNVER], 1);
+          else if (!(fabs(s_co[j] - pc) <= tau)) s_fc[atomicAdd(&cnt[C_NC], 1)] = j;
+        }
+      } else {
+        const int i = tid - 128;
+        if (i < mI) {
+          const double pr = use_c ? fma(p.alpha, csacc, p.beta * s_rc[i]) : p.alpha * csacc;
+          const double S = fabs(p.alpha) * p.arowabs[i0 + i] * p.babsmax[J] + (use_c ? fabs(p.beta) * s_rca[i] : 0.0);
+          const double n = (double)(p.K + nJt + 3);
+          const double tau = 2.01 * n * u * S + n * 0x1p-1021;
+          s_pr[i] = pr;
+          s_tr[i] = tau;
+          if (!isfinite(pr)) atomicAdd(&cnt[C_UNVER], 1);
+          else if (!(fabs(s_ro[i] - pr) <= tau)) s_fr[atomicAdd(&cnt[C_NR], 1)] = i;
+        }
+      }
+    }
+    compute_sync();
+    const int nr = cnt[C_NR], nc = cnt[C_NC];
+    if (nr + nc > 0) {
+      // locate and correct: flagged row x flagged column intersections
+      if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT)
+        for (int e = warp; e < nr * nc; e += NCOMPUTE / 32)
+          recompute_elem<TA, TB>(p, sC, cnt, tile, i0, j0, s_fr[e / nc], s_fc[e % nc], 0, use_c, lane);
+      compute_sync();
+      // re-verify the flagged rows and columns
+      for (int e = warp; e < nr + nc; e += NCOMPUTE / 32) {
+        double s = 0.0;
+        if (e < nr) {
+          const int i = s_fr[e];
+          for (int j = lane; j < BN; j += 32) s += sC[j * BM + i];
+          s = warp_sum(s);
+          if (lane == 0 && !(fabs(s - s_pr[i]) <= s_tr[i])) { s_rfail[i] = 1; atomicAdd(&cnt[C_FAIL], 1); }
+        } else {
+          const int j = s_fc[e - nr];
+          for (int i = lane; i < BM; i += 32) s += sC[j * BM + i];
+          s = warp_sum(s);
+          if (lane == 0 && !(fabs(s - s_pc[j]) <= s_tc[j])) { s_cfail[j] = 1; atomicAdd(&cnt[C_FAIL], 1); }
+        }
+      }
+      compute_sync();
+      if (cnt[C_FAIL] > 0) {
+        // fallback: recompute the whole tile segments of rows/columns still failing
+        for (int e = warp; e < mI * nJt; e += NCOMPUTE / 32) {
+          const int il = e % mI, jl = e / mI;
+          if (s_rfail[il] || s_cfail[jl]) recompute_elem<TA, TB>(p, sC, cnt, tile, i0, j0, il, jl, 1, use_c, lane);
+        }
+        compute_sync();
+        for (int e = warp; e < BM + BN; e += NCOMPUTE / 32) {
+          double s = 0.0;
+          if (e < BM) {
+            if (!s_rfail[e]) continue;
+            for (int j = lane; j < BN; j += 32) s += sC[j * BM + e];
+            s = warp_sum(s);
+            if (lane == 0 && !(fabs(s - s_pr[e]) <= s_tr[e])) atomicAdd(&cnt[C_CSONLY], 1);
+          } else {
+            const int j = e - BM;
+            if (!s_cfail[j]) continue;
+            for (int i = lane; i < BM; i += 32) s += sC[j * BM + i];
+            s = warp_sum(s);
+            if (lane == 0 && !(fabs(s - s_pc[j]) <= s_tc[j])) atomicAdd(&cnt[C_CSONLY], 1);
+          }
+        }
+        compute_sync();
+      }
+    }
+  }
+
+  // Store the tile.  TMA clips the tile at the edges of C, but in the inner
+  // (row) dimension it writes whole 16-byte chunks, so a tile ending on an odd
+  // row would also write the first padding row: such tiles use plain stores.
+  const bool tma_store = !((p.M & 1) && (i0 + BM > p.M));
+  if (tma_store) {
+    fence_proxy_async_smem();
+    compute_sync();
+  } else {
+    compute_sync();
+    for (int e = tid; e < mI * nJt; e += NCOMPUTE) {
+      const int il = e % mI, jl = e / mI;
+      p.C[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldc] = sC[jl * BM + il];
+    }
+  }
+  if (tid == 0) {
+    if (tma_store) {
+      tma_store_2d(&tmC, smem_u32(sC), i0, j0);
+      bulk_commit();
+    }
+    if (FT) {
+      DevReport *r = p.rep;
+      if (cnt[C_NR]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[C_NR]);
+      if (cnt[C_NC]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[C_NC]);
+      if (cnt[C_DET]) {
+        atomicAdd(&r->detected, (unsigned long long)cnt[C_DET]);
+        atomicAdd(&r->corrected, (unsigned long long)cnt[C_DET]);
+      }
+      if (cnt[C_CSONLY]) atomicAdd(&r->checksum_only, (unsigned long long)cnt[C_CSONLY]);
+      if (cnt[C_UNVER]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[C_UNVER]);
+      if (cnt[C_RECOMP]) atomicAdd(&r->recomputed, (unsigned long long)cnt[C_RECOMP]);
+    }
+    if (tma_store) bulk_wait_all();
+  }
+}
+
+}  // namespace ftg

@@ -1,0 +1,217 @@
+"""Python binding of libftgemm (argument marshalling only).
+
+Every function calls the C entry point of the same name declared in
+include/ftgemm.h; all arithmetic runs in the CUDA kernels of the library.
+Matrix arguments are device pointers given as torch CUDA tensors (their
+data_ptr) or plain integers; the `_host` variant takes CPU tensors or numpy
+arrays.  Streams are torch.cuda.Stream objects, raw cudaStream_t integers, or
+None for torch's current stream.  There is no fallback: a missing library
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libftgemm.so")
+
+BM = BN = 128
+KSTEP = 16
+ERR_CUDA, ERR_TIMEOUT, ERR_NODEVICE, ERR_NOMEM, ERR_INJECT, ERR_TENSORMAP = 1, 2, 4, 5, 6, 7
+
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_vp = ctypes.c_void_p
+
+
+class Loc(ctypes.Structure):
+    _fields_ = [("row", _i64), ("col", _i64), ("tile", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("delta", _dbl)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("detected", _i64), ("corrected", _i64), ("checksum_only", _i64),
+                ("unverifiable", _i64), ("flagged_rows", _i64), ("flagged_cols", _i64),
+                ("recomputed", _i64), ("n_loc", _i64), ("cap", _i64), ("loc", ctypes.POINTER(Loc))]
+
+
+class Flip(ctypes.Structure):
+    _fields_ = [("row", _i64), ("col", _i64), ("kstep", _i64), ("bit", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class Inject(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("count", _i64), ("list", ctypes.POINTER(Flip)), ("n_list", _i64)]
+
+
+class FlipLog(ctypes.Structure):
+    _fields_ = [("row", _i64), ("col", _i64), ("kstep", _i64), ("bit", ctypes.c_int32),
+                ("applied", ctypes.c_int32), ("before", _dbl), ("after", _dbl)]
+
+
+_lib = None
+
+_GEMM_ARGS = [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64]
+
+
+def lib():
+    """Load libftgemm.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first")
+        L = ctypes.CDLL(LIB_PATH)
+        L.ftgemm_d.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
+        L.ftgemm_d_noft.argtypes = _GEMM_ARGS + [_vp]
+        L.ftgemm_d_host.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
+        L.ftgemm_encode_operands.argtypes = [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _vp, _i64,
+                                             _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.ftgemm_set_injection.argtypes = [ctypes.POINTER(Inject)]
+        L.ftgemm_injection_log.argtypes = [ctypes.POINTER(FlipLog), _i64]
+        L.ftgemm_injection_log.restype = _i64
+        L.ftgemm_selftest_wait_timeout.argtypes = [_i64, _vp]
+        L.ftgemm_launch_count.restype = _i64
+        L.ftgemm_timing.argtypes = [ctypes.c_int]
+        L.ftgemm_timing.restype = ctypes.c_int
+        L.ftgemm_timing_read.argtypes = [ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
+        L.ftgemm_timing_read.restype = ctypes.c_int
+        L.ftgemm_strerror.argtypes = [ctypes.c_int]
+        L.ftgemm_strerror.restype = ctypes.c_char_p
+        for f in ("ftgemm_d", "ftgemm_d_noft", "ftgemm_d_host", "ftgemm_encode_operands",
+                  "ftgemm_set_injection", "ftgemm_selftest_wait_timeout", "ftgemm_finalize"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _report(cap: int):
+    locs = (Loc * max(1, cap))()
+    r = Report()
+    r.cap = cap
+    r.loc = ctypes.cast(locs, ctypes.POINTER(Loc))
+    return r, locs
+
+
+def _report_dict(r: Report, locs, cap: int) -> dict:
+    d = {f: getattr(r, f) for f, _ in Report._fields_ if f not in ("cap", "loc")}
+    d["locs"] = [(locs[q].row, locs[q].col, locs[q].tile, locs[q].kind, locs[q].delta)
+                 for q in range(min(cap, r.n_loc))]
+    return d
+
+
+def _c(t: str) -> bytes:
+    return t.encode() if isinstance(t, str) else t
+
+
+def ftgemm_d(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, report=True,
+             loc_cap=4096, stream=None):
+    """Fault-tolerant DGEMM on device buffers; returns (rc, report dict or None)."""
+    if report:
+        r, locs = _report(loc_cap)
+        rc = lib().ftgemm_d(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                            _ptr(C), ldc, ctypes.byref(r), _stream(stream))
+        return rc, _report_dict(r, locs, loc_cap)
+    rc = lib().ftgemm_d(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                        _ptr(C), ldc, None, _stream(stream))
+    return rc, None
+
+
+def ftgemm_d_noft(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    """The same DGEMM without fault tolerance (overhead baseline); returns rc."""
+    return lib().ftgemm_d_noft(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb,
+                               beta, _ptr(C), ldc, _stream(stream))
+
+
+def ftgemm_d_host(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, loc_cap=4096,
+                  stream=None):
+    """ftgemm_d on host buffers (copies in and out); returns (rc, report dict)."""
+    r, locs = _report(loc_cap)
+    rc = lib().ftgemm_d_host(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                             _ptr(C), ldc, ctypes.byref(r), _stream(stream))
+    return rc, _report_dict(r, locs, loc_cap)
+
+
+def ftgemm_encode_operands(transA, transB, M, N, K, A, lda, B, ldb, acs, aabsmax, arowabs, bcs,
+                           babsmax, bcolabs, stream=None):
+    return lib().ftgemm_encode_operands(_c(transA), _c(transB), M, N, K, _ptr(A), lda, _ptr(B), ldb,
+                                        _ptr(acs), _ptr(aabsmax), _ptr(arowabs), _ptr(bcs),
+                                        _ptr(babsmax), _ptr(bcolabs), _stream(stream))
+
+
+def ftgemm_set_injection(mode=0, seed=0, count=0, flips=None):
+    """mode 0 off, 1 seeded random (count per call), 2 explicit list of (row, col, kstep, bit)."""
+    cfg = Inject()
+    cfg.mode = mode
+    cfg.seed = seed & (2 ** 64 - 1)
+    cfg.count = count
+    keep = None
+    if mode == 2:
+        fl = list(flips or [])
+        keep = (Flip * max(1, len(fl)))()
+        for q, (r, c, s, b) in enumerate(fl):
+            keep[q].row, keep[q].col, keep[q].kstep, keep[q].bit = int(r), int(c), int(s), int(b)
+        cfg.list = ctypes.cast(keep, ctypes.POINTER(Flip))
+        cfg.n_list = len(fl)
+    return lib().ftgemm_set_injection(ctypes.byref(cfg))
+
+
+def ftgemm_injection_log():
+    """Faults of the last injected call, in list/draw order, as dicts."""
+    n = lib().ftgemm_injection_log(None, 0)
+    if n <= 0:
+        return []
+    buf = (FlipLog * n)()
+    lib().ftgemm_injection_log(buf, n)
+    return [{f: getattr(buf[q], f) for f, _ in FlipLog._fields_} for q in range(n)]
+
+
+def ftgemm_selftest_wait_timeout(limit_ns: int, stream=None) -> int:
+    return lib().ftgemm_selftest_wait_timeout(limit_ns, _stream(stream))
+
+
+def ftgemm_launch_count() -> int:
+    return lib().ftgemm_launch_count()
+
+
+def ftgemm_timing(enable: bool) -> int:
+    return lib().ftgemm_timing(1 if enable else 0)
+
+
+def ftgemm_timing_read():
+    """(main-kernel ms summed, main launches, pre-launch work ms summed)."""
+    m, a, n = _dbl(), _dbl(), _i64()
+    rc = lib().ftgemm_timing_read(ctypes.byref(m), ctypes.byref(n), ctypes.byref(a))
+    if rc:
+        raise RuntimeError(ftgemm_strerror(rc))
+    return m.value, n.value, a.value
+
+
+def ftgemm_strerror(code: int) -> str:
+    return lib().ftgemm_strerror(code).decode()
+
+
+def ftgemm_finalize() -> int:
+    return lib().ftgemm_finalize()

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads and exports every symbol of include/ftgemm.h;
+host-only logic (argument codes, injection settings, error strings) works
+without a GPU.  No compute call is made here."""
+from __future__ import annotations
+
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ft():
+    from paper_2305_02444_gb300 import build
+    build.build()
+    from paper_2305_02444_gb300 import ftgemm
+    ftgemm.lib()
+    return ftgemm
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?[\s\*]+(ftgemm_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ftgemm_d", "ftgemm_d_noft", "ftgemm_d_host", "ftgemm_encode_operands",
+                 "ftgemm_set_injection", "ftgemm_injection_log", "ftgemm_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(ft):
+    out = subprocess.run(["nm", "-D", "--defined-only", ft.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(ft.lib(), name) is not None
+
+
+def test_build_targets_sm103a_only():
+    from paper_2305_02444_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("args,code", [
+    (("X", "N", 2, 2, 2, 2, 2, 2), -1), (("N", "Q", 2, 2, 2, 2, 2, 2), -2),
+    (("N", "N", -1, 2, 2, 2, 2, 2), -3), (("N", "N", 2, -1, 2, 2, 2, 2), -4),
+    (("N", "N", 2, 2, -1, 2, 2, 2), -5), (("N", "N", 3, 2, 2, 2, 2, 3), -8),
+    (("T", "N", 2, 2, 3, 2, 3, 2), -8), (("N", "N", 2, 2, 3, 2, 2, 2), -10),
+    (("N", "T", 2, 3, 2, 2, 2, 2), -10), (("N", "N", 3, 2, 2, 3, 2, 2), -13),
+])
+def test_argument_codes_without_device(ft, args, code):
+    ta, tb, M, N, K, lda, ldb, ldc = args
+    assert ft.ftgemm_d(ta, tb, M, N, K, 1.0, 0, lda, 0, ldb, 0.0, 0, ldc, report=False, stream=0)[0] == code
+    assert ft.ftgemm_d_noft(ta, tb, M, N, K, 1.0, 0, lda, 0, ldb, 0.0, 0, ldc, stream=0) == code
+    assert ft.ftgemm_d_host(ta, tb, M, N, K, 1.0, 0, lda, 0, ldb, 0.0, 0, ldc, stream=0)[0] == code
+
+
+def test_host_settings_and_strings(ft):
+    assert ft.ftgemm_set_injection(mode=0) == 0
+    assert ft.ftgemm_set_injection(mode=1, seed=5, count=-1) == -1
+    assert ft.ftgemm_set_injection(mode=7) == -1
+    assert ft.ftgemm_set_injection(mode=2, flips=[(0, 0, 0, 3)]) == 0
+    assert ft.ftgemm_set_injection(mode=0) == 0
+    assert "timeout" in ft.ftgemm_strerror(ft.ERR_TIMEOUT) or "wait" in ft.ftgemm_strerror(ft.ERR_TIMEOUT)
+    assert ft.ftgemm_strerror(0) == "success"
+    assert ft.ftgemm_launch_count() == 0
