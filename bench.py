@@ -38,11 +38,19 @@ sys.path.insert(0, ROOT)
 
 M = N = K = 8192
 ALPHA, BETA = 1.5, 0.5
-TILES = (M // 128) * (N // 128)
-FLIPS = math.ceil(TILES / 64)
 SEED = 20230614
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # FP64 FMA pipe, max SM clock
-WORKLOAD = f"ftdgemm_nn_{M}x{N}x{K}_a{ALPHA}_b{BETA}_uniform_flips1per64tiles"
+
+
+def set_size(n: int):
+    global M, N, K, TILES, FLIPS, WORKLOAD
+    M = N = K = n
+    TILES = -(-M // 128) * -(-N // 128)
+    FLIPS = math.ceil(TILES / 64)
+    WORKLOAD = f"ftdgemm_nn_{M}x{N}x{K}_a{ALPHA}_b{BETA}_uniform_flips1per64tiles"
+
+
+set_size(8192)
 
 
 def dist_env():
@@ -113,16 +121,26 @@ def read_traffic(kernel_tag: str):
     return None
 
 
+_SAMPLE_INPUTS = {}
+
+
+def _sample_inputs(rows: int, seed: int):
+    key = (M, N, K, seed)
+    if key not in _SAMPLE_INPUTS:
+        from paper_2305_02444_gb300 import inputs
+        _SAMPLE_INPUTS.clear()
+        _SAMPLE_INPUTS[key] = (inputs.matrix(M, K, seed).T.numpy(), inputs.matrix(K, N, seed + 1).T.numpy(),
+                               inputs.matrix(M, N, seed + 2).T.numpy())
+    A, B, C = _SAMPLE_INPUTS[key]
+    return A[:rows], B, C[:rows]                                 # first `rows` rows of A and C
+
+
 def oracle_sample(rows: int, seed: int):
     """The oracle's FT-DGEMM on `rows` full rows of the workload (rows x N x K)."""
-    import numpy as np
     import oracle
-    from paper_2305_02444_gb300 import inputs
-    A = inputs.matrix(M, K, seed)[:, :rows].T.numpy()          # first `rows` rows of A
-    B = inputs.matrix(K, N, seed + 1).T.numpy()
-    C = inputs.matrix(M, N, seed + 2)[:, :rows].T.numpy()
+    A, B, C = _sample_inputs(rows, seed)
     nflips = max(1, round(FLIPS * rows / M))
-    flips = oracle.random_flips(seed, nflips, rows, N, K // 16)
+    flips = oracle.random_flips(seed, nflips, rows, N, -(-K // 16))
     t0 = time.perf_counter()
     r = oracle.ft_gemm("N", "N", ALPHA, A, B, BETA, C, BM=128, BN=128, BK=16, flips=flips)
     dt = time.perf_counter() - t0
@@ -155,7 +173,7 @@ def reference_arm(args):
         return
     rows = 128
     dt0, _ = oracle_sample(rows, SEED)               # calibration (untimed)
-    rows = int(min(M, max(128, 128 * round(rows * 10.0 / max(dt0, 1e-3) / 128))))
+    rows = int(min(M, max(128, 128 * round(rows * 6.0 / max(dt0, 1e-3) / 128))))
     for _ in range(args.warmup):
         oracle_sample(rows, SEED)
     times = [oracle_sample(rows, SEED)[0] for _ in range(args.steps)]
@@ -181,7 +199,9 @@ def main():
     ap.add_argument("--impl", default="ftgemm", choices=["ftgemm", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=8192, help="M = N = K (default 8192)")
     args = ap.parse_args()
+    set_size(args.size)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -309,7 +329,9 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "M": M, "N": N, "K": K, "alpha": ALPHA, "beta": BETA,
                    "layout": "column-major NN", "dist": "uniform[-1,1]", "tile": "128x128x16",
-                   "flips_per_call": FLIPS, "l2": "inputs larger than L2 (3 x 512 MiB vs 129 MB)"},
+                   "flips_per_call": FLIPS,
+                   "l2": f"inputs larger than L2 (3 x {M * N * 8 / 2**20:.0f} MiB vs 129 MB)"
+                   if 3 * M * N * 8 > 129e6 else "inputs smaller than L2"},
         "pct_fp64_peak": 100.0 * value / ws / FP64_PEAK_TFLOPS,
         "overhead_pct": {"ft_vs_noft": 100.0 * (t_ft / t_noft - 1.0),
                          "ft_injected_vs_noft": 100.0 * (t_inj / t_noft - 1.0),
