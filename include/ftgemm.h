@@ -64,6 +64,12 @@ extern "C" {
 #define FTGEMM_ERR_NOMEM 5      /* workspace allocation failed */
 #define FTGEMM_ERR_INJECT 6     /* an explicit fault lies outside the problem */
 #define FTGEMM_ERR_TENSORMAP 7  /* a TMA descriptor could not be encoded */
+#define FTGEMM_ERR_SCRATCH 8    /* ftgemm_d_noalloc: the problem needs more scratch than it holds */
+#define FTGEMM_ERR_UNALIGNED 9  /* ftgemm_d_noalloc: an operand is not 16-byte aligned or its
+                                   leading dimension is odd */
+
+/* Size of the device array that ftgemm_d_noalloc uses as scratch. */
+#define FTGEMM_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* One located fault: element (row, col) of C, 0-based. */
 typedef struct {
@@ -139,6 +145,41 @@ int ftgemm_d(char transA, char transB, int64_t M, int64_t N, int64_t K, double a
 int ftgemm_d_noft(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, void *stream);
+
+/* ftgemm_d for callers that cannot allocate device memory.  (The paper has no
+ * counterpart: it is an interface for this library's users.)
+ *
+ * Who needs it: callers whose device memory is owned and budgeted by their own
+ * pool allocator (a framework's caching allocator, an inference server with a
+ * fixed memory plan), which must not see a foreign cudaMalloc; callers that
+ * cannot afford the device-wide synchronisation that cudaMalloc/cudaFree
+ * imply in a latency-critical loop; and callers recovering from an
+ * out-of-memory error, where any new allocation may fail.  ftgemm_d grows a
+ * workspace with cudaMalloc on first use and when a problem is larger.
+ *
+ * This entry point calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its scratch is one static device array of FTGEMM_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that every GPU which loads the library holds until the process
+ * exits.  The caller still owns A, B and C (device pointers) and the report.
+ *  - Limit: the scratch needed is about 8 * (ceil(M/128) + ceil(N/128)) *
+ *    ceil(K/16)*16 bytes of checksum vectors plus 8 * ceil(K/256) *
+ *    max(M, N) bytes of partial sums plus small terms; a problem that needs
+ *    more returns FTGEMM_ERR_SCRATCH and touches nothing (M = N = K = 8192
+ *    needs about 10.5 MiB; 16384^3 does not fit).
+ *  - A, B and C must be 16-byte aligned with even leading dimensions (no
+ *    aligned copies can be made without memory): FTGEMM_ERR_UNALIGNED
+ *    otherwise.
+ *  - No fault injection (the injection table needs allocated memory); at
+ *    most 1024 location records per call.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the one array and it keeps the last call's contents;
+ *    the call clears what must start at zero.  Calls that overlap on the GPU
+ *    (different streams, threads or processes' graphs) race on it.
+ * Results equal ftgemm_d's (same kernels).  Returns as ftgemm_d does. */
+int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                     const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                     double *C, int64_t ldc, ftgemm_report *rep, void *stream);
 
 /* ftgemm_d on HOST matrices: copies A, B (and C unless beta == 0) to device
  * workspace, runs ftgemm_d, copies C back, and waits for the stream.  Pinned

@@ -625,6 +625,8 @@ const char *ftgemm_strerror(int code) {
     case FTGEMM_ERR_NOMEM: return "workspace allocation failed";
     case FTGEMM_ERR_INJECT: return "injected fault outside the problem";
     case FTGEMM_ERR_TENSORMAP: return "TMA descriptor encoding failed";
+    case FTGEMM_ERR_SCRATCH: return "problem needs more scratch than ftgemm_d_noalloc holds";
+    case FTGEMM_ERR_UNALIGNED: return "operand not 16-byte aligned or leading dimension odd (ftgemm_d_noalloc)";
     default: return "unknown error";
   }
 }
@@ -652,3 +654,191 @@ int ftgemm_finalize(void) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// ftgemm_d_noalloc: the fault-tolerant DGEMM for callers that cannot allocate
+// device memory.  All of its scratch (operand checksum vectors, the partial
+// sums of the checksum pass, the device report and location records) lives in
+// the file-scope array below, which every GPU that loads this library holds
+// until the process exits.  No cudaMalloc, cudaFree or allocating library
+// routine is called on this path.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FTGEMM_NOALLOC_SCRATCH_BYTES];
+
+constexpr long long NOALLOC_LOC_CAP = 1024;
+
+// Device address of g_noalloc_scratch per device, looked up on the first call
+// made with that device current (host code may not use the symbol itself).
+unsigned char *g_noalloc_ptr[MAX_DEV] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Scratch layout for one call; returns the bytes needed.
+struct NoallocLayout {
+  size_t rep, loc, acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max, total;
+};
+
+NoallocLayout noalloc_layout(bool ta_t, bool tb_t, long long M, long long N, long long K) {
+  const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN, Kp = (K + BK - 1) / BK * BK;
+  auto nch_seg = [](long long S) { return (S + ENC_CW - 1) / ENC_CW; };
+  auto nch_str = [](long long R) { return (R + ENC_RW - 1) / ENC_RW; };
+  // partial buffers of the checksum pass: worst case over the two operands
+  const long long pa = std::max(ta_t ? nch_str(K) * M : nch_seg(K) * M, tb_t ? nch_seg(K) * N : nch_str(K) * N);
+  const long long pm = std::max(ta_t ? nch_str(K) * nI : nch_seg(K) * nI, tb_t ? nch_seg(K) * nJ : nch_str(K) * nJ);
+  NoallocLayout L;
+  size_t o = 0;
+  L.rep = o; o = align256(o + sizeof(DevReport));
+  L.loc = o; o = align256(o + sizeof(DevLoc) * NOALLOC_LOC_CAP);
+  L.acs = o; o = align256(o + sizeof(double) * nI * Kp);
+  L.bcs = o; o = align256(o + sizeof(double) * nJ * Kp);
+  L.arowabs = o; o = align256(o + sizeof(double) * M);
+  L.aabsmax = o; o = align256(o + sizeof(double) * nI);
+  L.bcolabs = o; o = align256(o + sizeof(double) * N);
+  L.babsmax = o; o = align256(o + sizeof(double) * nJ);
+  L.part_abs = o; o = align256(o + sizeof(double) * pa);
+  L.part_max = o; o = align256(o + sizeof(double) * pm);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                                const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                                int64_t ldc, ftgemm_report *rep, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
+  if (rc) return rc;
+  zero_report(rep);
+  if (M == 0 || N == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (K == 0 || alpha == 0.0) {
+    if (beta != 1.0) {
+      scale_kernel<<<grid_for(M * N), 256, 0, s>>>(C, M, N, ldc, beta);
+      g_launches++;
+    }
+    if (rep && cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+  }
+  const bool ta_t = is_t(transA), tb_t = is_t(transB);
+  const NoallocLayout L = noalloc_layout(ta_t, tb_t, M, N, K);
+  if (L.total > (size_t)FTGEMM_NOALLOC_SCRATCH_BYTES) return FTGEMM_ERR_SCRATCH;
+  if (!tma_ok(A, lda) || !tma_ok(B, ldb) || !tma_ok(C, ldc)) return FTGEMM_ERR_UNALIGNED;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) {
+    cudaGetLastError();
+    return FTGEMM_ERR_NODEVICE;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return FTGEMM_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  unsigned char *base = g_noalloc_ptr[dev];
+
+  const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN;
+  const long long nks = (K + BK - 1) / BK, Kp = nks * BK;
+  double *acs = (double *)(base + L.acs), *bcs = (double *)(base + L.bcs);
+  double *arowabs = (double *)(base + L.arowabs), *aabsmax = (double *)(base + L.aabsmax);
+  double *bcolabs = (double *)(base + L.bcolabs), *babsmax = (double *)(base + L.babsmax);
+  double *part_abs = (double *)(base + L.part_abs), *part_max = (double *)(base + L.part_max);
+  DevReport *drep = (DevReport *)(base + L.rep);
+  DevLoc *dloc = (DevLoc *)(base + L.loc);
+
+  // the array keeps the previous call's contents: clear what must start at zero
+  cudaMemsetAsync(drep, 0, sizeof(DevReport), s);
+  if (Kp != K) {
+    cudaMemsetAsync(acs, 0, sizeof(double) * nI * Kp, s);
+    cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
+  }
+  // operand checksum pass (same kernels as ftgemm_d), partials in the array
+  if (!ta_t) {
+    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
+    enc_seg_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, M, K, lda, acs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max<long long>(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
+                                                                 aabsmax);
+  } else {
+    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
+    enc_str_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, K, M, lda, acs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max<long long>(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
+                                                                 aabsmax);
+  }
+  if (!tb_t) {
+    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
+    enc_str_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, K, N, ldb, bcs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max<long long>(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
+                                                                 babsmax);
+  } else {
+    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
+    enc_seg_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, N, K, ldb, bcs, Kp, part_abs, part_max);
+    enc_finish_kernel<<<grid_for(std::max<long long>(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
+                                                                 babsmax);
+  }
+  g_launches += 4;
+
+  CUtensorMap mA, mB, mC;
+  if (ta_t) rc = make_map(&mA, A, K, M, lda, BK, BM, true);
+  else rc = make_map(&mA, A, M, K, lda, BM, BK, false);
+  if (!rc) {
+    if (tb_t) rc = make_map(&mB, B, N, K, ldb, BN, BK, false);
+    else rc = make_map(&mB, B, K, N, ldb, BK, BN, true);
+  }
+  if (!rc) rc = make_map(&mC, C, M, N, ldc, BM, BN, false);
+  if (rc) return rc;
+
+  Params p;
+  memset(&p, 0, sizeof(p));
+  p.M = M; p.N = N; p.K = K; p.alpha = alpha; p.beta = beta;
+  p.A = A; p.B = B; p.C = C; p.lda = lda; p.ldb = ldb; p.ldc = ldc;
+  p.nI = (int)nI; p.nJ = (int)nJ; p.nks = (int)nks; p.Kp = Kp;
+  p.acs = acs; p.bcs = bcs; p.arowabs = arowabs; p.aabsmax = aabsmax; p.bcolabs = bcolabs; p.babsmax = babsmax;
+  p.rep = drep;
+  p.loc = dloc;
+  p.loc_cap = NOALLOC_LOC_CAP;
+  p.wait_limit_ns = wait_limit_ns();
+  cudaError_t e;
+  if (!ta_t && !tb_t) e = launch_main_nn(true, false, mA, mB, mC, p, s);
+  else if (!ta_t && tb_t) e = launch_main_nt(true, false, mA, mB, mC, p, s);
+  else if (ta_t && !tb_t) e = launch_main_tn(true, false, mA, mB, mC, p, s);
+  else e = launch_main_tt(true, false, mA, mB, mC, p, s);
+  g_launches++;
+  if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
+
+  if (rep) {
+    // copy the report into host variables of this call (no pinned staging)
+    DevReport hr;
+    DevLoc hl[64];
+    const long long ncopy = std::min<long long>(std::max<long long>(rep->cap, 0), NOALLOC_LOC_CAP);
+    if (cudaMemcpyAsync(&hr, drep, sizeof(DevReport), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return FTGEMM_ERR_CUDA;
+    rep->detected = (long long)hr.detected;
+    rep->corrected = (long long)hr.corrected;
+    rep->checksum_only = (long long)hr.checksum_only;
+    rep->unverifiable = (long long)hr.unverifiable;
+    rep->flagged_rows = (long long)hr.flagged_rows;
+    rep->flagged_cols = (long long)hr.flagged_cols;
+    rep->recomputed = (long long)hr.recomputed;
+    rep->n_loc = (long long)hr.n_loc;
+    const long long nrec = std::min<long long>(ncopy, rep->n_loc);
+    for (long long q0 = 0; rep->loc && q0 < nrec; q0 += 64) {
+      const long long nq = std::min<long long>(64, nrec - q0);
+      if (cudaMemcpy(hl, dloc + q0, sizeof(DevLoc) * nq, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FTGEMM_ERR_CUDA;
+      for (long long q = 0; q < nq; ++q) {
+        rep->loc[q0 + q].row = hl[q].row;
+        rep->loc[q0 + q].col = hl[q].col;
+        rep->loc[q0 + q].tile = hl[q].tile;
+        rep->loc[q0 + q].kind = hl[q].kind;
+        rep->loc[q0 + q].delta = hl[q].delta;
+      }
+    }
+    if (hr.err) return FTGEMM_ERR_TIMEOUT;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+}
