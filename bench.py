@@ -60,6 +60,24 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, ws: int, device) -> float:
+    """Max of x over all ranks (host-level timing reduction, not a data-path
+    collective); identity on one rank."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_tflops(ws: int, flops_per_rank_step: float, steps: int, t_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank runs its own replica)."""
+    return ws * flops_per_rank_step * steps / t_max / 1e12
+
+
 def sample_clocks_start(dev_index: int, path: str):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -191,6 +209,57 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def sweep(args):
+    """Square sweep M = N = K in {1024 .. 16384} plus the rank-k update
+    8192^2 x 256 (alpha 1.5, beta 0.5, U[-1,1], one flip per 64 tiles): FT
+    with injection, FT fault-free and the unprotected kernel, per size."""
+    import torch
+    from paper_2305_02444_gb300 import build, ftgemm, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    rows = []
+    shapes = [(1024,) * 3, (2048,) * 3, (4096,) * 3, (8192,) * 3, (16384,) * 3, (8192, 8192, 256)]
+    if args.sweep_shapes:
+        shapes = [tuple(int(x) for x in sh.split("x")) for sh in args.sweep_shapes.split(",")]
+    for (m, n, k) in shapes:
+        A = inputs.matrix(m, k, SEED, device="cuda"); B = inputs.matrix(k, n, SEED + 1, device="cuda")
+        C = inputs.matrix(m, n, SEED + 2, device="cuda")
+        tiles = -(-m // 128) * -(-n // 128)
+        nfl = math.ceil(tiles / 64)
+        reps = max(2, min(10, int(2e12 / (2.0 * m * n * k))))
+
+        def t(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps / 1e3
+
+        ft_call = lambda: ftgemm.ftgemm_d("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, report=False)
+        t_noft = t(lambda: ftgemm.ftgemm_d_noft("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m))
+        t_ft = t(ft_call)
+        ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nfl)
+        t_inj = t(ft_call)
+        rc, rep = ftgemm.ftgemm_d("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, loc_cap=0)
+        ftgemm.ftgemm_set_injection(mode=0)
+        fl = 2.0 * m * n * k
+        rows.append({"M": m, "N": n, "K": k, "tiles": tiles, "noft_tflops": fl / t_noft / 1e12,
+                     "ft_tflops": fl / t_ft / 1e12, "ft_inj_tflops": fl / t_inj / 1e12,
+                     "pct_fp64_peak_ft_inj": 100 * fl / t_inj / 1e12 / FP64_PEAK_TFLOPS,
+                     "overhead_pct": 100 * (t_ft / t_noft - 1), "overhead_inj_pct": 100 * (t_inj / t_noft - 1),
+                     "flips": nfl, "detected": rep["detected"], "corrected": rep["corrected"]})
+        print(json.dumps(rows[-1]), flush=True)
+        del A, B, C
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": rows, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,8 +269,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=8192, help="M = N = K (default 8192)")
+    ap.add_argument("--sweep", action="store_true", help="per-size results of the square sweep")
+    ap.add_argument("--sweep-shapes", default="", help="comma list of MxNxK for --sweep")
     args = ap.parse_args()
     set_size(args.size)
+    if args.sweep:
+        return sweep(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -221,11 +294,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, ws, "cuda")
 
     from paper_2305_02444_gb300 import build, ftgemm, inputs
     build.build()
@@ -317,7 +386,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    value = ws * flops * args.steps / t_inj / 1e12
+    value = job_tflops(ws, flops, args.steps, t_inj)
     det = [r["detected"] for r in reps]
     cor = [r["corrected"] for r in reps]
     avg_main = main_ms / max(1, main_n) / 1e3
@@ -348,7 +417,7 @@ def main():
                      "kernel": "ftdgemm_kernel<N,N,FT,INJ> (main FT-DGEMM kernel)",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
                      "pre_kernel_ms_per_step": aux_ms / max(1, main_n)},
-        "e2e": {"value": ws * flops / t_e2e / 1e12, "unit": "TFLOP/s",
+        "e2e": {"value": job_tflops(ws, flops, 1, t_e2e), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 3 * M * N * 8, "d2h_bytes_per_step": M * N * 8,
                 "steps": args.e2e_steps},
         "gpu_launches": int(launches),

@@ -131,6 +131,8 @@ typedef struct {
   int32_t applied;  /* 1 when the flip was made */
   double before;    /* accumulator value before the flip */
   double after;     /* accumulator value after the flip */
+  int64_t kfirst;   /* first product the flipped accumulator holds: 0, or the
+                       start of its k-split when the call split K */
 } ftgemm_flip_log;
 
 /* Fault-tolerant DGEMM (abstract; §2.2).  Encodes, verifies, locates and
@@ -214,6 +216,13 @@ int64_t ftgemm_injection_log(ftgemm_flip_log *out, int64_t cap);
  * Returns FTGEMM_ERR_TIMEOUT when the wait gave up and the context is still
  * usable (the expected result), another code otherwise. */
 int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
+
+/* K splitting (a tuning knob; results stay within the same bound): 0 picks
+ * the number of k-splits automatically (the default: grids with fewer than
+ * 4 tiles per SM split K so that every SM gets work, then a reduction kernel
+ * sums the partial tiles and runs the verification on the whole tile),
+ * 1 never splits, n >= 2 forces n splits (fewer when K is short). */
+int ftgemm_set_splitk(int nsplit);
 
 /* Number of kernels this library has launched in this process. */
 int64_t ftgemm_launch_count(void);

@@ -48,6 +48,7 @@ struct DevFlip {
   long long row, col, kstep;
   int bit, applied;
   double before, after;
+  long long kfirst;  // first product index held by the flipped accumulator (split-K)
 };
 
 struct Params {
@@ -66,6 +67,11 @@ struct Params {
   DevFlip *flips;                // injection table (INJ kernels only)
   const int *tile_off;           // ntiles + 1 offsets into flips
   unsigned long long wait_limit_ns;
+  // split-K (MODE 1 / 2 kernels)
+  int nsplit, ks_slabs;          // number of k-splits, k-slabs per split
+  double *W;                     // nsplit partial tiles, [split][N][ldw]
+  long long ldw;
+  double *wpc, *wpr;             // predicted-checksum partials [split][nI][N], [split][nJ][M]
 };
 
 constexpr int ERR_TIMEOUT = 2;
@@ -143,6 +149,13 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t sr
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
                    reinterpret_cast<uint64_t>(map)),
                "r"(src), "r"(c0), "r"(c1)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(src), "r"(c0), "r"(c1), "r"(c2)
                : "memory");
 }
 

@@ -24,6 +24,15 @@ cudaError_t launch_main_tn(bool ft, bool inj, const CUtensorMap &, const CUtenso
                            const Params &, cudaStream_t);
 cudaError_t launch_main_tt(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
                            const Params &, cudaStream_t);
+// any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
+cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
+                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
+cudaError_t launch_gemm_nt(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
+                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
+cudaError_t launch_gemm_tn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
+                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
+cudaError_t launch_gemm_tt(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
+                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
 }  // namespace ftg
 
 using namespace ftg;
@@ -47,6 +56,8 @@ struct Workspace {
   Buf rep, loc, flips, tile_off;
   Buf stA, stB, stC;        // aligned copies of unaligned operands
   Buf hA, hB, hC;           // device copies for ftgemm_d_host
+  Buf W, wpc, wpr;          // split-K partial tiles and predicted-checksum partials
+  int nsm = 0;              // SM count
   Buf pin;                  // pinned host staging (report, loc, injection upload)
   // the last injected call, for ftgemm_injection_log
   long long last_nflips = 0;
@@ -179,6 +190,47 @@ bool tma_ok(const void *p, long long ld) {
 
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
+int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
+
+// Number of k-splits for a grid of `ntiles` tiles and `nks` k-slabs on `nsm`
+// SMs.  One CTA per SM: a grid of few tiles leaves SMs idle (64 tiles of a
+// 1024^3 problem on 152 SMs), so the k loop is split and the partial tiles
+// summed in a reduction kernel.  Cost model in units of one k-slab of one
+// tile: waves x (slabs per split + per-CTA overhead) + reduction.
+int choose_splits(long long ntiles, long long nks, int nsm) {
+  if (g_splitk == 1) return 1;
+  if (g_splitk >= 2) {
+    const long long ks = (nks + g_splitk - 1) / g_splitk;
+    return (int)((nks + ks - 1) / ks);
+  }
+  if (ntiles >= 4LL * nsm || nks < 8) return 1;
+  double best = 1e300;
+  int bestS = 1;
+  for (int S = 1; S <= 32 && S <= nks; ++S) {
+    const long long ks = (nks + S - 1) / S, Se = (nks + ks - 1) / ks;
+    if (Se != S) continue;
+    const long long waves = (ntiles * Se + nsm - 1) / nsm;
+    double T = waves * (ks + 0.07);
+    if (Se > 1) T += (double)((ntiles + nsm - 1) / nsm) * (0.03 * Se + 0.3);
+    if (T < best - 1e-9) { best = T; bestS = (int)Se; }
+  }
+  return bestS;
+}
+
+// 3-D fp64 tensor map over nz column-major matrices of rows x cols (ld), stacked.
+int make_map3(CUtensorMap *m, const double *ptr, long long rows, long long cols, long long nz, long long ld) {
+  auto fn = encode_fn();
+  if (!fn) return FTGEMM_ERR_TENSORMAP;
+  cuuint64_t dims[3] = {(cuuint64_t)rows, (cuuint64_t)cols, (cuuint64_t)nz};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 8, (cuuint64_t)ld * cols * 8};
+  cuuint32_t box[3] = {(cuuint32_t)BM, (cuuint32_t)BN, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : FTGEMM_ERR_TENSORMAP;
+}
+
 cudaError_t launch_copy(const double *src, long long lds, double *dst, long long ldd, long long rows,
                         long long cols, cudaStream_t s) {
   copy2d_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
@@ -294,7 +346,7 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
   for (long long q = 0; q < nf; ++q) {
     const ftgemm_flip &f = L[perm[q]];
     hf[q].row = f.row; hf[q].col = f.col; hf[q].kstep = f.kstep; hf[q].bit = f.bit;
-    hf[q].applied = 0; hf[q].before = 0.0; hf[q].after = 0.0;
+    hf[q].applied = 0; hf[q].before = 0.0; hf[q].after = 0.0; hf[q].kfirst = 0;
     ho[tile_of(f) + 1]++;
   }
   for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
@@ -405,12 +457,41 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     cudaEventRecord(ea1, s);
     cudaEventRecord(em0, s);
   }
+  if (!w.nsm) {
+    if (cudaDeviceGetAttribute(&w.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || w.nsm <= 0) {
+      cudaGetLastError();
+      w.nsm = 152;
+    }
+  }
+  const int S = choose_splits(ntiles, nks, w.nsm);
   cudaError_t e;
-  if (!ta_t && !tb_t) e = launch_main_nn(ft, inj, mA, mB, mC, p, s);
-  else if (!ta_t && tb_t) e = launch_main_nt(ft, inj, mA, mB, mC, p, s);
-  else if (ta_t && !tb_t) e = launch_main_tn(ft, inj, mA, mB, mC, p, s);
-  else e = launch_main_tt(ft, inj, mA, mB, mC, p, s);
-  g_launches++;
+  auto launch = [&](int mode, const CUtensorMap &mW) {
+    if (!ta_t && !tb_t) return launch_gemm_nn(ft, inj, mode, mA, mB, mC, mW, p, s);
+    if (!ta_t && tb_t) return launch_gemm_nt(ft, inj, mode, mA, mB, mC, mW, p, s);
+    if (ta_t && !tb_t) return launch_gemm_tn(ft, inj, mode, mA, mB, mC, mW, p, s);
+    return launch_gemm_tt(ft, inj, mode, mA, mB, mC, mW, p, s);
+  };
+  if (S <= 1) {
+    e = launch(0, mC);
+    g_launches++;
+  } else {
+    // split-K: partial tiles into workspace, then the verifying reduction
+    const long long ldw = (M + 1) & ~1LL;
+    if (ensure(w.W, sizeof(double) * ldw * N * S) || ensure(w.wpc, sizeof(double) * S * nI * N) ||
+        ensure(w.wpr, sizeof(double) * S * nJ * M))
+      return FTGEMM_ERR_NOMEM;
+    CUtensorMap mW;
+    if ((rc = make_map3(&mW, (const double *)w.W.p, M, N, S, ldw))) return rc;
+    p.nsplit = S;
+    p.ks_slabs = (int)((nks + S - 1) / S);
+    p.W = (double *)w.W.p;
+    p.ldw = ldw;
+    p.wpc = (double *)w.wpc.p;
+    p.wpr = (double *)w.wpr.p;
+    e = launch(1, mW);
+    if (e == cudaSuccess) e = launch(2, mW);
+    g_launches += 2;
+  }
   if (g_tim.on) cudaEventRecord(em1, s);
   if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
   if (c_staged) launch_copy(Cuse, ldcU, C, ldc, M, N, s);
@@ -558,6 +639,7 @@ int64_t ftgemm_injection_log(ftgemm_flip_log *out, int64_t cap) {
     out[o].applied = h[q].applied;
     out[o].before = h[q].before;
     out[o].after = h[q].after;
+    out[o].kfirst = h[q].kfirst;
   }
   return nf;
 }
@@ -580,6 +662,13 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream) {
 }
 
 int64_t ftgemm_launch_count(void) { return g_launches.load(); }
+
+int ftgemm_set_splitk(int nsplit) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (nsplit < 0 || nsplit > 64) return -1;
+  g_splitk = nsplit;
+  return 0;
+}
 
 int ftgemm_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -638,7 +727,8 @@ int ftgemm_finalize(void) {
   Workspace &w = g_ws[dev];
   cudaDeviceSynchronize();
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
-                  &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC};
+                  &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
+                  &w.W, &w.wpc, &w.wpr};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;

@@ -1,24 +1,40 @@
 // Main-kernel instantiations for op(A) = n, op(B) = n: the unprotected kernel,
-// the fault-tolerant kernel, and the fault-tolerant kernel with the injector.
+// the fault-tolerant kernel and the fault-tolerant kernel with the injector, for
+// whole tiles (mode 0) and for split-K partials (mode 1) and reductions (mode 2).
 #include "ftgemm_kernel.cuh"
 
 namespace ftg {
 
-template <bool FT, bool INJ>
+template <bool FT, bool INJ, int MODE>
 static cudaError_t launch_variant_nn(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &c,
-                                      const Params &p, cudaStream_t s) {
-  auto k = ftdgemm_kernel<false, false, FT, INJ>;
+                                      const CUtensorMap &w, const Params &p, cudaStream_t s) {
+  auto k = ftdgemm_kernel<false, false, FT, INJ, MODE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)p.nI * (unsigned)p.nJ, NTHREADS, SMEM_BYTES, s>>>(a, b, c, p);
+  const unsigned grid = (unsigned)p.nI * (unsigned)p.nJ * (MODE == 1 ? (unsigned)p.nsplit : 1u);
+  k<<<grid, NTHREADS, SMEM_BYTES, s>>>(a, b, c, w, p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &a, const CUtensorMap &b,
+                           const CUtensorMap &c, const CUtensorMap &w, const Params &p, cudaStream_t s) {
+  if (mode == 1) {
+    if (!ft) return launch_variant_nn<false, false, 1>(a, b, c, w, p, s);
+    if (inj) return launch_variant_nn<true, true, 1>(a, b, c, w, p, s);
+    return launch_variant_nn<true, false, 1>(a, b, c, w, p, s);
+  }
+  if (mode == 2) {
+    if (!ft) return launch_variant_nn<false, false, 2>(a, b, c, w, p, s);
+    return launch_variant_nn<true, false, 2>(a, b, c, w, p, s);
+  }
+  if (!ft) return launch_variant_nn<false, false, 0>(a, b, c, w, p, s);
+  if (inj) return launch_variant_nn<true, true, 0>(a, b, c, w, p, s);
+  return launch_variant_nn<true, false, 0>(a, b, c, w, p, s);
 }
 
 cudaError_t launch_main_nn(bool ft, bool inj, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &c,
                            const Params &p, cudaStream_t s) {
-  if (!ft) return launch_variant_nn<false, false>(a, b, c, p, s);
-  if (inj) return launch_variant_nn<true, true>(a, b, c, p, s);
-  return launch_variant_nn<true, false>(a, b, c, p, s);
+  return launch_gemm_nn(ft, inj, 0, a, b, c, c, p, s);
 }
 
 }  // namespace ftg

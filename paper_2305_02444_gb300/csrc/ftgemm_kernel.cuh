@@ -95,10 +95,16 @@ __device__ __forceinline__ void recompute_elem(const Params &p, double *sC, int 
   }
 }
 
-template <bool TA, bool TB, bool FT, bool INJ>
+// MODE 0: the whole tile (mainloop + epilogue).
+// MODE 1: split-K partial: one k-range of a tile; stores the raw partial
+//         product and its predicted-checksum partials for MODE 2.
+// MODE 2: split-K reduction: sums the partials of a tile, then runs the same
+//         epilogue as MODE 0 (beta*C encode, verify, locate, correct, store).
+template <bool TA, bool TB, bool FT, bool INJ, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ftdgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, const Params p) {
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                   const Params p) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -113,11 +119,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), cbar = smem_u32(bars + 2 * STAGES);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x;
+  const int ntiles = p.nI * p.nJ;
+  const int tile = (MODE == 1) ? (int)(blockIdx.x % ntiles) : (int)blockIdx.x;
+  const int split = (MODE == 1) ? (int)(blockIdx.x / ntiles) : 0;
+  const int s_begin = (MODE == 1) ? split * p.ks_slabs : 0;              // first k-slab (global)
+  const int s_end = (MODE == 1) ? min(p.nks, s_begin + p.ks_slabs) : p.nks;
   const int I = tile % p.nI, J = tile / p.nI;
   const int i0 = I * BM, j0 = J * BN;
   const int mI = (int)min((long long)BM, p.M - i0), nJt = (int)min((long long)BN, p.N - j0);
-  const int nks = p.nks;
+  const int nks = (MODE == 2) ? 0 : s_end - s_begin;  // k-slabs this CTA accumulates
   const unsigned long long limit = p.wait_limit_ns;
   int *err = &p.rep->err;
   double *sC = reinterpret_cast<double *>(smem);  // output tile, column-major [BN][BM]
@@ -133,9 +143,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_mbar_init();
   }
   if (tid == 32) {
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmB);
-    prefetch_tmap(&tmC);
+    if (MODE != 2) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+    }
+    prefetch_tmap(MODE == 1 ? &tmW : &tmC);
   }
   if (tid < 128) { s_rfail[tid] = 0; s_cfail[tid] = 0; }
   __syncthreads();
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t sb = smem_u32(smem + st * STAGE_BYTES);
     const uint32_t fb = full0 + 8 * st;
     mbar_arrive_expect_tx(fb, tx_bytes);
-    const int k0 = s * BK;
+    const int k0 = (s_begin + s) * BK;
     if (TA) tma_load_2d(sb, &tmA, fb, k0, i0); else tma_load_2d(sb, &tmA, fb, i0, k0);
     if (TB) tma_load_2d(sb + A_BYTES, &tmB, fb, j0, k0); else tma_load_2d(sb + A_BYTES, &tmB, fb, k0, j0);
     if (FT) {
@@ -171,7 +183,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
   double csacc = 0.0;  // FT: predicted column (tid < 128) or row (tid >= 128) checksum
   int fptr = 0, fend = 0;
-  if (INJ) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+  if (INJ) {
+    fptr = p.tile_off[tile];
+    fend = p.tile_off[tile + 1];
+    while (fptr < fend && p.flips[fptr].kstep < s_begin) ++fptr;  // earlier k-splits' faults
+  }
 
   bool ok = true;
   for (int s = 0; s < nks; ++s) {
@@ -204,7 +220,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (INJ) {
       while (fptr < fend) {
         DevFlip *f = p.flips + fptr;
-        if (f->kstep != s) break;
+        if (f->kstep != s_begin + s) break;
         const int il = (int)(f->row - i0), jl = (int)(f->col - j0);
         if ((il & 15) == tx && (jl & 15) == ty) {
           const int pq = (il >> 4) * 8 + (jl >> 4);
@@ -218,6 +234,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 f->before = before;
                 f->after = acc[a][b];
                 f->applied = 1;
+                f->kfirst = (long long)s_begin * BK;
               }
         }
         ++fptr;
@@ -242,8 +259,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   compute_sync();
   if (*reinterpret_cast<volatile int *>(&cnt[C_ABORT])) return;
 
+  if (MODE == 1) {
+    // split-K partial: raw accumulators and predicted-checksum partials
+#pragma unroll
+    for (int pp = 0; pp < 8; ++pp)
+#pragma unroll
+      for (int qq = 0; qq < 8; ++qq) sC[(ty + 16 * qq) * BM + tx + 16 * pp] = acc[pp][qq];
+    if (FT) {
+      if (tid < 128) {
+        if (tid < nJt) p.wpc[((long long)split * p.nI + I) * p.N + j0 + tid] = csacc;
+      } else if (tid - 128 < mI) {
+        p.wpr[((long long)split * p.nJ + J) * p.M + i0 + tid - 128] = csacc;
+      }
+    }
+    fence_proxy_async_smem();
+    compute_sync();
+    if (tid == 0) {
+      tma_store_3d(&tmW, smem_u32(sC), i0, j0, split);
+      bulk_commit();
+      bulk_wait_all();
+    }
+    return;
+  }
+  if (MODE == 2) {
+    // split-K reduction: acc = sum over splits of the partial tiles (ascending split)
+    for (int sp = 0; sp < p.nsplit; ++sp) {
+      const double *Ws = p.W + (long long)sp * p.ldw * p.N;
+#pragma unroll
+      for (int pp = 0; pp < 8; ++pp)
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) {
+          const int il = tx + 16 * pp, jl = ty + 16 * qq;
+          if (il < mI && jl < nJt) acc[pp][qq] += Ws[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldw];
+        }
+      if (FT) {
+        if (tid < 128) {
+          if (tid < nJt) csacc += p.wpc[((long long)sp * p.nI + I) * p.N + j0 + tid];
+        } else if (tid - 128 < mI) {
+          csacc += p.wpr[((long long)sp * p.nJ + J) * p.M + i0 + tid - 128];
+        }
+      }
+    }
+  }
+
   // ----------------------------------------------------------------- epilogue
   const bool use_c = (p.beta != 0.0);
+  // rounding terms of the threshold: K products, L sums, the epilogue, and
+  // (split-K) one addition per partial
+  const long long nextra = 3 + ((MODE == 2) ? p.nsplit : 0);
   if (use_c) {
     if (tid == 0) {
       mbar_arrive_expect_tx(cbar, CTILE_BYTES);
@@ -254,27 +317,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (*reinterpret_cast<volatile int *>(&cnt[C_ABORT])) return;
   }
 
+  // Row and column sums of a staged 128x128 tile by all 256 threads: thread t
+  // takes row (t mod 128) over half of the columns and column (t mod 128) over
+  // half of the rows (rows visited in a rotated order so a warp's loads hit
+  // distinct banks); the two halves are combined through shared memory.  The
+  // absolute sums, needed only for the threshold's upper bound, run on the
+  // FP32 pipe with upward rounding (each partial sum stays an upper bound).
+  const int r = tid & 127, h = tid >> 7;
   // beta-side sums of C for the predicted checksums and the thresholds
   if (FT && use_c) {
-    if (tid < 128) {
-      double s = 0.0, a = 0.0;
-      for (int j = 0; j < BN; ++j) {
-        const double c = sC[j * BM + tid];
-        s += c;
-        a += fabs(c);
-      }
-      s_rc[tid] = s;
-      s_rca[tid] = a;
-    } else {
-      const int w = warp - 4;
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = w * 32 + jj;
-        const double v0 = sC[j * BM + lane], v1 = sC[j * BM + lane + 32];
-        const double v2 = sC[j * BM + lane + 64], v3 = sC[j * BM + lane + 96];
-        const double s = warp_sum((v0 + v1) + (v2 + v3));
-        const double a = warp_sum((fabs(v0) + fabs(v1)) + (fabs(v2) + fabs(v3)));
-        if (lane == 0) { s_cc[j] = s; s_cca[j] = a; }
-      }
+    double rs = 0.0, cs = 0.0;
+    float ra = 0.0f, ca = 0.0f;
+#pragma unroll 8
+    for (int q = 0; q < 64; ++q) {
+      const double vr = sC[(64 * h + q) * BM + r];
+      const double vc = sC[r * BM + 64 * h + ((q + r) & 63)];
+      rs += vr;
+      cs += vc;
+      ra = __fadd_ru(ra, __double2float_ru(fabs(vr)));
+      ca = __fadd_ru(ca, __double2float_ru(fabs(vc)));
+    }
+    if (h) { s_ro[r] = rs; s_co[r] = cs; s_pr[r] = (double)ra; s_pc[r] = (double)ca; }
+    compute_sync();
+    if (!h) {
+      s_rc[r] = rs + s_ro[r];
+      s_cc[r] = cs + s_co[r];
+      s_rca[r] = (double)__fadd_ru(ra, (float)s_pr[r]);
+      s_cca[r] = (double)__fadd_ru(ca, (float)s_pc[r]);
     }
   }
   if (FT) compute_sync();
@@ -291,18 +360,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (FT) {
     // reference checksums of the computed tile
-    if (tid < 128) {
-      double s = 0.0;
-      for (int j = 0; j < BN; ++j) s += sC[j * BM + tid];
-      s_ro[tid] = s;
-    } else {
-      const int w = warp - 4;
-      for (int jj = 0; jj < 32; ++jj) {
-        const int j = w * 32 + jj;
-        const double s = warp_sum((sC[j * BM + lane] + sC[j * BM + lane + 32]) +
-                                  (sC[j * BM + lane + 64] + sC[j * BM + lane + 96]));
-        if (lane == 0) s_co[j] = s;
+    {
+      double rs = 0.0, cs = 0.0;
+#pragma unroll 8
+      for (int q = 0; q < 64; ++q) {
+        rs += sC[(64 * h + q) * BM + r];
+        cs += sC[r * BM + 64 * h + ((q + r) & 63)];
       }
+      if (h) { s_pr[r] = rs; s_pc[r] = cs; }
+      compute_sync();
+      if (!h) { s_ro[r] = rs + s_pr[r]; s_co[r] = cs + s_pc[r]; }
     }
     compute_sync();
     // verify: predicted vs reference, per column (tid < 128) and per row
@@ -313,11 +380,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (j < nJt) {
           const double pc = use_c ? fma(p.alpha, csacc, p.beta * s_cc[j]) : p.alpha * csacc;
           const double S = fabs(p.alpha) * p.bcolabs[j0 + j] * p.aabsmax[I] + (use_c ? fabs(p.beta) * s_cca[j] : 0.0);
-          const double n = (double)(p.K + mI + 3);
+          const double n = (double)(p.K + mI + nextra);
           const double tau = 2.01 * n * u * S + n * 0x1p-1021;
           s_pc[j] = pc;
           s_tc[j] = tau;
-          if (!isfinite(pc)) atomicAdd(&cnt[C_UNVER], 1);
+          if (!isfinite(pc) || !isfinite(tau)) atomicAdd(&cnt[C_UNVER], 1);
           else if (!(fabs(s_co[j] - pc) <= tau)) s_fc[atomicAdd(&cnt[C_NC], 1)] = j;
         }
       } else {
@@ -325,11 +392,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (i < mI) {
           const double pr = use_c ? fma(p.alpha, csacc, p.beta * s_rc[i]) : p.alpha * csacc;
           const double S = fabs(p.alpha) * p.arowabs[i0 + i] * p.babsmax[J] + (use_c ? fabs(p.beta) * s_rca[i] : 0.0);
-          const double n = (double)(p.K + nJt + 3);
+          const double n = (double)(p.K + nJt + nextra);
           const double tau = 2.01 * n * u * S + n * 0x1p-1021;
           s_pr[i] = pr;
           s_tr[i] = tau;
-          if (!isfinite(pr)) atomicAdd(&cnt[C_UNVER], 1);
+          if (!isfinite(pr) || !isfinite(tau)) atomicAdd(&cnt[C_UNVER], 1);
           else if (!(fabs(s_ro[i] - pr) <= tau)) s_fr[atomicAdd(&cnt[C_NR], 1)] = i;
         }
       }

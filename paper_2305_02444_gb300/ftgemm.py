@@ -49,7 +49,7 @@ class Inject(ctypes.Structure):
 
 class FlipLog(ctypes.Structure):
     _fields_ = [("row", _i64), ("col", _i64), ("kstep", _i64), ("bit", ctypes.c_int32),
-                ("applied", ctypes.c_int32), ("before", _dbl), ("after", _dbl)]
+                ("applied", ctypes.c_int32), ("before", _dbl), ("after", _dbl), ("kfirst", _i64)]
 
 
 _lib = None
@@ -75,6 +75,8 @@ def lib():
         L.ftgemm_injection_log.restype = _i64
         L.ftgemm_selftest_wait_timeout.argtypes = [_i64, _vp]
         L.ftgemm_launch_count.restype = _i64
+        L.ftgemm_set_splitk.argtypes = [ctypes.c_int]
+        L.ftgemm_set_splitk.restype = ctypes.c_int
         L.ftgemm_timing.argtypes = [ctypes.c_int]
         L.ftgemm_timing.restype = ctypes.c_int
         L.ftgemm_timing_read.argtypes = [ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
@@ -206,6 +208,11 @@ def ftgemm_injection_log():
 
 def ftgemm_selftest_wait_timeout(limit_ns: int, stream=None) -> int:
     return lib().ftgemm_selftest_wait_timeout(limit_ns, _stream(stream))
+
+
+def ftgemm_set_splitk(nsplit: int) -> int:
+    """0 automatic k-splitting, 1 never, n >= 2 force n splits."""
+    return lib().ftgemm_set_splitk(nsplit)
 
 
 def ftgemm_launch_count() -> int:

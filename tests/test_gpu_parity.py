@@ -32,8 +32,22 @@ def ft():
     from paper_2305_02444_gb300 import ftgemm
     ftgemm.lib()
     ftgemm.ftgemm_set_injection(mode=0)
+    ftgemm.ftgemm_set_splitk(0)
     yield ftgemm
     ftgemm.ftgemm_set_injection(mode=0)
+    ftgemm.ftgemm_set_splitk(0)
+
+
+class splitk:
+    """Force a k-split setting for a block (0 auto, 1 off, n splits)."""
+    def __init__(self, ft, n):
+        self.ft, self.n = ft, n
+
+    def __enter__(self):
+        assert self.ft.ftgemm_set_splitk(self.n) == 0
+
+    def __exit__(self, *a):
+        self.ft.ftgemm_set_splitk(0)
 
 
 def stored_dims(t, rows_op, cols_op):
@@ -214,10 +228,12 @@ def flip_value(x: float, bit: int) -> float:
     return struct.unpack("<d", struct.pack("<Q", u))[0]
 
 
-def run_injected(ft, P, alpha, beta, flips):
+def run_injected(ft, P, alpha, beta, flips, nsplit=1):
+    """Injected call; nsplit=1 keeps whole-K accumulators, as in the oracle's scheme."""
     assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
     try:
-        rc, rep, out = run_gpu(ft, P, alpha, beta)
+        with splitk(ft, nsplit):
+            rc, rep, out = run_gpu(ft, P, alpha, beta)
         log = ft.ftgemm_injection_log()
     finally:
         ft.ftgemm_set_injection(mode=0)
@@ -248,10 +264,15 @@ def check_log_against_oracle(orc, P, flips, log):
         assert struct.unpack("<Q", struct.pack("<d", L["before"]))[0] ^ \
             struct.unpack("<Q", struct.pack("<d", L["after"]))[0] == 1 << bit
         kend = min(P["K"], KSTEP * (s + 1))
-        part = orc.partial(P["ta"], P["tb"], i, j, kend, opA, opB)
-        a_row = (opA if P["ta"] == "N" else opA.T)[i, :kend]
-        b_col = (opB if P["tb"] == "N" else opB.T)[:kend, j]
-        bound = 2 * (kend + 1) * 2.0 ** -53 * np.abs(a_row * b_col).sum()
+        kf = L["kfirst"]
+        assert 0 <= kf < kend and kf % KSTEP == 0
+        a_row = (opA if P["ta"] == "N" else opA.T)[i, kf:kend]
+        b_col = (opB if P["tb"] == "N" else opB.T)[kf:kend, j]
+        if kf == 0:
+            part = orc.partial(P["ta"], P["tb"], i, j, kend, opA, opB)
+        else:   # the accumulator of a k-split holds products kf .. kend-1
+            part = float(np.dot(a_row, b_col))
+        bound = 2 * (kend - kf + 1) * 2.0 ** -53 * np.abs(a_row * b_col).sum()
         assert abs(L["before"] - part) <= bound
 
 
@@ -349,7 +370,7 @@ def test_random_mode_matches_published_generator(ft, orc):
     seed, count = 0xC0FFEE, 12
     assert ft.ftgemm_set_injection(mode=1, seed=seed, count=count) == 0
     try:
-        rc, rep, out = run_gpu(ft, P, 1.0, 1.0)
+        rc, rep, out = run_gpu(ft, P, 1.0, 1.0)   # automatic k-split: kfirst may be > 0
         log = ft.ftgemm_injection_log()
     finally:
         ft.ftgemm_set_injection(mode=0)
@@ -378,3 +399,63 @@ def test_host_buffers_api(ft, orc):
     rc, rep = ft.ftgemm_d_host("T", "T", 200, 190, 180, 1.5, A, P["lda"], B, P["ldb"], 0.5, C, P["ldc"])
     assert rc == 0 and rep["detected"] == 0
     assert_parity(orc, P, C, ref, E)
+
+
+# ------------------------------------------------------------------------------ split-K
+
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+@pytest.mark.parametrize("nsplit", [1, 2, 3, 7, 16])
+def test_splitk_forced_parity(ft, orc, ta, tb, nsplit):
+    """Forced k-splits (partial tiles + verifying reduction) match the oracle,
+    FT and unprotected, ragged tiles, K not a multiple of the split."""
+    P = make_problem(ta, tb, 300, 260, 700, seed=nsplit * 13 + 1)
+    ref, E = oracle_ref(orc, P, 1.5, 0.5)
+    with splitk(ft, nsplit):
+        rc, rep, out = run_gpu(ft, P, 1.5, 0.5)
+        assert rc == 0
+        assert_parity(orc, P, out, ref, E)
+        assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
+        rc, _, out = run_gpu(ft, P, 1.5, 0.5, noft=True)
+        assert rc == 0
+        assert_parity(orc, P, out, ref, E)
+
+
+def test_splitk_auto_small_square(ft, orc):
+    """1024^3 gives 64 tiles on 152 SMs: the automatic split is used."""
+    P = make_problem("N", "N", 1024, 1024, 1024, seed=77)
+    ref, E = oracle_ref(orc, P, 1.5, 0.5)
+    n0 = ft.ftgemm_launch_count()
+    rc, rep, out = run_gpu(ft, P, 1.5, 0.5)
+    assert rc == 0
+    assert ft.ftgemm_launch_count() - n0 == 4 + 2     # checksum pass + partials + reduction
+    assert_parity(orc, P, out, ref, E)
+    assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
+
+
+@pytest.mark.parametrize("nsplit", [4, 32])
+def test_splitk_injection(ft, orc, nsplit):
+    """Flips in different k-splits: each flips the accumulator of its split
+    (kfirst in the log); clearly-above-threshold ones are detected and
+    corrected to the parity bound by the reduction's verification."""
+    P = make_problem("N", "T", 256, 256, 512, seed=91)
+    alpha, beta = 1.5, 0.5
+    ref, E = oracle_ref(orc, P, alpha, beta)
+    flips = [(3, 5, 0, 58), (100, 200, 9, 60), (200, 40, 17, 55), (255, 255, 31, 61), (130, 7, 22, 3)]
+    rc, rep, out, log = run_injected(ft, P, alpha, beta, flips, nsplit=nsplit)
+    assert rc == 0
+    check_log_against_oracle(orc, P, flips, log)
+    ks = -(-32 // nsplit) * KSTEP
+    assert all(L["kfirst"] == (L["kstep"] * KSTEP // ks) * ks for L in log)
+    opA = np_logical(P["A"], P["ar"]); opB = np_logical(P["B"], P["br"]).T
+    expect_detected, extra = set(), np.zeros_like(E)
+    for (i, j, s, bit), L in zip(flips, log):
+        d = L["after"] - L["before"]
+        eff = abs(alpha * d) if math.isfinite(d) else math.inf
+        tr, tc = tile_taus(orc, P, alpha, beta, i, j)
+        if eff > 4 * max(tr, tc):
+            expect_detected.add((i, j))
+        else:
+            extra[i, j] = 2 * eff
+    got = {l[:2] for l in rep["locs"]}
+    assert expect_detected <= got
+    assert_parity(orc, P, out, ref, E, extra=extra)
