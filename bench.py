@@ -244,6 +244,7 @@ def sweep(args):
         ft_call = lambda: ftgemm.ftgemm_d("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, report=False)
         t_noft = t(lambda: ftgemm.ftgemm_d_noft("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m))
         t_ft = t(ft_call)
+        t_unf = t(lambda: ftgemm.ftgemm_d_unfused("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, report=False))
         ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nfl)
         t_inj = t(ft_call)
         rc, rep = ftgemm.ftgemm_d("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, loc_cap=0)
@@ -253,6 +254,7 @@ def sweep(args):
                      "ft_tflops": fl / t_ft / 1e12, "ft_inj_tflops": fl / t_inj / 1e12,
                      "pct_fp64_peak_ft_inj": 100 * fl / t_inj / 1e12 / FP64_PEAK_TFLOPS,
                      "overhead_pct": 100 * (t_ft / t_noft - 1), "overhead_inj_pct": 100 * (t_inj / t_noft - 1),
+                     "unfused_overhead_pct": 100 * (t_unf / t_noft - 1),
                      "flips": nfl, "detected": rep["detected"], "corrected": rep["corrected"]})
         print(json.dumps(rows[-1]), flush=True)
         del A, B, C
@@ -362,6 +364,14 @@ def main():
     t_ft, _ = timed(lambda: ft_call(False), args.steps)
     ft_ms, ft_n, ft_aux = ftgemm.ftgemm_timing_read()
     ftgemm.ftgemm_timing(False)
+
+    def unfused_call():
+        rc, _ = ftgemm.ftgemm_d_unfused("N", "N", M, N, K, ALPHA, A, M, B, K, BETA, C, M, report=False)
+        if rc:
+            raise RuntimeError(f"ftgemm_d_unfused: {ftgemm.ftgemm_strerror(rc)}")
+    unfused_call()
+    t_unf, _ = timed(unfused_call, max(2, args.steps // 2))
+    t_unf = t_unf / max(2, args.steps // 2) * args.steps
     clocks = sample_clocks_stop(proc, fh, clk_path)
 
     # 3) end to end through the host-buffer entry point (pinned host memory)
@@ -406,7 +416,8 @@ def main():
                          "ft_injected_vs_noft": 100.0 * (t_inj / t_noft - 1.0),
                          "noft_tflops": flops * args.steps / t_noft / 1e12,
                          "ft_tflops": flops * args.steps / t_ft / 1e12,
-                         "main_kernel_ft_vs_noft": 100.0 * ((ft_ms / max(1, ft_n)) / (noft_ms / max(1, noft_n)) - 1.0)},
+                         "main_kernel_ft_vs_noft": 100.0 * ((ft_ms / max(1, ft_n)) / (noft_ms / max(1, noft_n)) - 1.0),
+                         "unfused_vs_noft": 100.0 * (t_unf / t_noft - 1.0)},
         "errors": {"injected_per_step": FLIPS, "detected_per_step": det[-1] if det else None,
                    "corrected_per_step": cor[-1] if cor else None,
                    "detected_total": sum(det), "corrected_total": sum(cor),

@@ -65,8 +65,8 @@ extern "C" {
 #define FTGEMM_ERR_INJECT 6     /* an explicit fault lies outside the problem */
 #define FTGEMM_ERR_TENSORMAP 7  /* a TMA descriptor could not be encoded */
 #define FTGEMM_ERR_SCRATCH 8    /* ftgemm_d_noalloc: the problem needs more scratch than it holds */
-#define FTGEMM_ERR_UNALIGNED 9  /* ftgemm_d_noalloc: an operand is not 16-byte aligned or its
-                                   leading dimension is odd */
+#define FTGEMM_ERR_UNALIGNED 9  /* ftgemm_d_noalloc / ftgemm_d_unfused: an operand is not
+                                   16-byte aligned or its leading dimension is odd */
 
 /* Size of the device array that ftgemm_d_noalloc uses as scratch. */
 #define FTGEMM_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -180,6 +180,19 @@ int ftgemm_d_noft(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
  *    (different streams, threads or processes' graphs) race on it.
  * Results equal ftgemm_d's (same kernels).  Returns as ftgemm_d does. */
 int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                     const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                     double *C, int64_t ldc, ftgemm_report *rep, void *stream);
+
+/* The unfused ablation: the same ABFT scheme and result as ftgemm_d, but
+ * computed in separate passes, as FT-GEMM's unfused baseline (§2.2: fusing
+ * the memory-bound checksum work into the GEMM took the ABFT overhead from
+ * about 15% to 2.94% on Cascade Lake): the operand checksum pass; one pass
+ * over C that copies it and takes its tile row/column sums; two skinny GEMMs
+ * for the predicted checksums; the unprotected GEMM; a verify / locate /
+ * correct pass over the finished C.  For measuring what fusion saves on
+ * GB300.  Operands must be 16-byte aligned with even leading dimensions
+ * (FTGEMM_ERR_UNALIGNED otherwise); fault injection does not apply. */
+int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                      const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                      double *C, int64_t ldc, ftgemm_report *rep, void *stream);
 

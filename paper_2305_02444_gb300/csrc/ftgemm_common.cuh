@@ -72,6 +72,12 @@ struct Params {
   double *W;                     // nsplit partial tiles, [split][N][ldw]
   long long ldw;
   double *wpc, *wpr;             // predicted-checksum partials [split][nI][N], [split][nJ][M]
+  // unfused ablation (MODE 3): predicted checksums and C sums from separate passes
+  const double *P1, *P2;         // nI x N (ld ldp1) and M x nJ (ld ldp2), column-major
+  long long ldp1, ldp2;
+  const double *ccs, *ccsa, *crs, *crsa;  // [I][N] column sums, [J][M] row sums of C (and |C|)
+  double *Cout;                  // where the verified tile lives (p.C is the copy of C_in)
+  long long ldcout;
 };
 
 constexpr int ERR_TIMEOUT = 2;

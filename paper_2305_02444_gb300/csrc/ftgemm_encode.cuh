@@ -123,6 +123,56 @@ __global__ void enc_finish_kernel(const double *__restrict__ part_abs, int nchun
   }
 }
 
+// Unfused ablation: one pass over C that keeps a copy of C_in (needed to
+// recompute an element after the GEMM overwrote C) and takes, per 128x128
+// tile, the column sums over the tile's rows and the row sums over its
+// columns (and the absolute sums, FP32 with upward rounding, as in the fused
+// epilogue).  grid = tiles, 256 threads, 128 KiB dynamic shared memory.
+__global__ void __launch_bounds__(256) enc_c_kernel(const double *__restrict__ C, long long ldc,
+                                                    double *__restrict__ Cc, long long ldcc, long long M,
+                                                    long long N, int nI, double *__restrict__ ccs,
+                                                    double *__restrict__ ccsa, double *__restrict__ crs,
+                                                    double *__restrict__ crsa) {
+  extern __shared__ double tbuf[];  // [128 columns][128 rows]
+  __shared__ double part[4][128];
+  const int tile = blockIdx.x, I = tile % nI, J = tile / nI;
+  const long long i0 = (long long)I * 128, j0 = (long long)J * 128;
+  const int mI = (int)min(128LL, M - i0), nJt = (int)min(128LL, N - j0);
+  for (int e = threadIdx.x; e < 128 * 128; e += 256) {
+    const int il = e & 127, jl = e >> 7;
+    double v = 0.0;
+    if (il < mI && jl < nJt) {
+      v = C[(i0 + il) + (j0 + jl) * ldc];
+      Cc[(i0 + il) + (j0 + jl) * ldcc] = v;
+    }
+    tbuf[jl * 128 + il] = v;
+  }
+  __syncthreads();
+  const int r = threadIdx.x & 127, h = threadIdx.x >> 7;
+  double rs = 0.0, cs = 0.0;
+  float ra = 0.0f, ca = 0.0f;
+  for (int q = 0; q < 64; ++q) {
+    const double vr = tbuf[(64 * h + q) * 128 + r];
+    const double vc = tbuf[r * 128 + 64 * h + ((q + r) & 63)];
+    rs += vr;
+    cs += vc;
+    ra = __fadd_ru(ra, __double2float_ru(fabs(vr)));
+    ca = __fadd_ru(ca, __double2float_ru(fabs(vc)));
+  }
+  if (h) { part[0][r] = rs; part[1][r] = cs; part[2][r] = (double)ra; part[3][r] = (double)ca; }
+  __syncthreads();
+  if (!h) {
+    if (r < mI) {
+      crs[(long long)J * M + i0 + r] = rs + part[0][r];
+      crsa[(long long)J * M + i0 + r] = (double)__fadd_ru(ra, (float)part[2][r]);
+    }
+    if (r < nJt) {
+      ccs[(long long)I * N + j0 + r] = cs + part[1][r];
+      ccsa[(long long)I * N + j0 + r] = (double)__fadd_ru(ca, (float)part[3][r]);
+    }
+  }
+}
+
 // C <- beta*C (beta == 0 writes zeros without reading C)
 __global__ void scale_kernel(double *C, long long M, long long N, long long ldc, double beta) {
   const long long total = M * N;

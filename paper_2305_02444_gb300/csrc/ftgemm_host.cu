@@ -57,6 +57,7 @@ struct Workspace {
   Buf stA, stB, stC;        // aligned copies of unaligned operands
   Buf hA, hB, hC;           // device copies for ftgemm_d_host
   Buf W, wpc, wpr;          // split-K partial tiles and predicted-checksum partials
+  Buf uC, uccs, uccsa, ucrs, ucrsa, uP1, uP2;  // unfused ablation: copy of C, C sums, skinny GEMMs
   int nsm = 0;              // SM count
   Buf pin;                  // pinned host staging (report, loc, injection upload)
   // the last injected call, for ftgemm_injection_log
@@ -360,6 +361,37 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
   return 0;
 }
 
+// Copy the device report (and up to rep->cap location records) into rep,
+// waiting for the stream.
+int copy_report(Workspace &w, ftgemm_report *rep, cudaStream_t s) {
+  const long long ncopy = std::min<long long>(std::max<long long>(rep->cap, 0), LOC_CAP_DEV);
+  const size_t need = sizeof(DevReport) + sizeof(DevLoc) * (size_t)ncopy;
+  if (ensure_pinned(w.pin, need + 4096)) return FTGEMM_ERR_NOMEM;
+  DevReport *hr = (DevReport *)w.pin.p;
+  DevLoc *hl = (DevLoc *)((char *)w.pin.p + sizeof(DevReport));
+  cudaMemcpyAsync(hr, w.rep.p, sizeof(DevReport), cudaMemcpyDeviceToHost, s);
+  if (ncopy > 0 && rep->loc) cudaMemcpyAsync(hl, w.loc.p, sizeof(DevLoc) * ncopy, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  rep->detected = (long long)hr->detected;
+  rep->corrected = (long long)hr->corrected;
+  rep->checksum_only = (long long)hr->checksum_only;
+  rep->unverifiable = (long long)hr->unverifiable;
+  rep->flagged_rows = (long long)hr->flagged_rows;
+  rep->flagged_cols = (long long)hr->flagged_cols;
+  rep->recomputed = (long long)hr->recomputed;
+  rep->n_loc = (long long)hr->n_loc;
+  if (rep->loc)
+    for (long long q = 0; q < std::min<long long>(ncopy, rep->n_loc); ++q) {
+      rep->loc[q].row = hl[q].row;
+      rep->loc[q].col = hl[q].col;
+      rep->loc[q].tile = hl[q].tile;
+      rep->loc[q].kind = hl[q].kind;
+      rep->loc[q].delta = hl[q].delta;
+    }
+  if (hr->err) return FTGEMM_ERR_TIMEOUT;
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+}
+
 int gemm_impl(char transA, char transB, long long M, long long N, long long K, double alpha, const double *A,
               long long lda, const double *B, long long ldb, double beta, double *C, long long ldc,
               ftgemm_report *rep, cudaStream_t s, bool ft) {
@@ -497,32 +529,8 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
   if (c_staged) launch_copy(Cuse, ldcU, C, ldc, M, N, s);
 
   if (rep) {
-    const long long ncopy = std::min<long long>(std::max<long long>(rep->cap, 0), LOC_CAP_DEV);
-    const size_t need = sizeof(DevReport) + sizeof(DevLoc) * (size_t)ncopy;
     if (inj) cudaStreamSynchronize(s);  // the pinned buffer held the injection upload
-    if (ensure_pinned(w.pin, need + 4096)) return FTGEMM_ERR_NOMEM;
-    DevReport *hr = (DevReport *)w.pin.p;
-    DevLoc *hl = (DevLoc *)((char *)w.pin.p + sizeof(DevReport));
-    cudaMemcpyAsync(hr, w.rep.p, sizeof(DevReport), cudaMemcpyDeviceToHost, s);
-    if (ncopy > 0 && rep->loc) cudaMemcpyAsync(hl, w.loc.p, sizeof(DevLoc) * ncopy, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
-    rep->detected = (long long)hr->detected;
-    rep->corrected = (long long)hr->corrected;
-    rep->checksum_only = (long long)hr->checksum_only;
-    rep->unverifiable = (long long)hr->unverifiable;
-    rep->flagged_rows = (long long)hr->flagged_rows;
-    rep->flagged_cols = (long long)hr->flagged_cols;
-    rep->recomputed = (long long)hr->recomputed;
-    rep->n_loc = (long long)hr->n_loc;
-    if (rep->loc)
-      for (long long q = 0; q < std::min<long long>(ncopy, rep->n_loc); ++q) {
-        rep->loc[q].row = hl[q].row;
-        rep->loc[q].col = hl[q].col;
-        rep->loc[q].tile = hl[q].tile;
-        rep->loc[q].kind = hl[q].kind;
-        rep->loc[q].delta = hl[q].delta;
-      }
-    if (hr->err) return FTGEMM_ERR_TIMEOUT;
+    return copy_report(w, rep, s);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
@@ -576,6 +584,93 @@ int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
   cudaMemcpyAsync(C, w.hC.p, cbytes, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
   return rc;
+}
+
+int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                     int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                     ftgemm_report *rep, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
+  if (rc) return rc;
+  zero_report(rep);
+  if (M == 0 || N == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (K == 0 || alpha == 0.0)  // BLAS quick return: same path as ftgemm_d
+    return gemm_impl(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rep, s, true);
+  if (!tma_ok(A, lda) || !tma_ok(B, ldb) || !tma_ok(C, ldc)) return FTGEMM_ERR_UNALIGNED;
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return FTGEMM_ERR_NODEVICE;
+  Workspace &w = *wp;
+  const bool ta_t = is_t(transA), tb_t = is_t(transB);
+  const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN, ntiles = nI * nJ;
+  const long long nks = (K + BK - 1) / BK, Kp = nks * BK;
+  const long long ldcc = (M + 1) & ~1LL, ldp1 = (nI + 1) & ~1LL, ldp2 = (M + 1) & ~1LL;
+  // pass 1: operand checksum vectors (as in ftgemm_d)
+  if (ensure(w.acs, sizeof(double) * nI * Kp) || ensure(w.bcs, sizeof(double) * nJ * Kp) ||
+      ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
+      ensure(w.bcolabs, sizeof(double) * N) || ensure(w.babsmax, sizeof(double) * nJ) ||
+      ensure(w.uC, sizeof(double) * ldcc * N) || ensure(w.uccs, sizeof(double) * nI * N) ||
+      ensure(w.uccsa, sizeof(double) * nI * N) || ensure(w.ucrs, sizeof(double) * nJ * M) ||
+      ensure(w.ucrsa, sizeof(double) * nJ * M) || ensure(w.uP1, sizeof(double) * ldp1 * N) ||
+      ensure(w.uP2, sizeof(double) * ldp2 * nJ))
+    return FTGEMM_ERR_NOMEM;
+  if ((rc = run_encode(ta_t, tb_t, M, N, K, A, lda, B, ldb, Kp, (double *)w.acs.p, (double *)w.aabsmax.p,
+                       (double *)w.arowabs.p, (double *)w.bcs.p, (double *)w.babsmax.p, (double *)w.bcolabs.p,
+                       w, s)))
+    return rc;
+  // pass 2: copy of C_in and its per-tile row/column sums
+  if (beta != 0.0) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(enc_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
+      attr = true;
+    }
+    enc_c_kernel<<<(unsigned)ntiles, 256, 128 * 128 * 8, s>>>(C, ldc, (double *)w.uC.p, ldcc, M, N, (int)nI,
+                                                               (double *)w.uccs.p, (double *)w.uccsa.p,
+                                                               (double *)w.ucrs.p, (double *)w.ucrsa.p);
+    g_launches++;
+  }
+  // passes 3-4: predicted checksums as separate GEMMs on the unprotected kernel:
+  // P1 = acs^T-view x op(B) (nI x N), P2 = op(A) x bcs-view (M x nJ)
+  if ((rc = gemm_impl('T', transB, nI, N, K, 1.0, (const double *)w.acs.p, Kp, B, ldb, 0.0, (double *)w.uP1.p,
+                      ldp1, nullptr, s, false)))
+    return rc;
+  if ((rc = gemm_impl(transA, 'N', M, nJ, K, 1.0, A, lda, (const double *)w.bcs.p, Kp, 0.0, (double *)w.uP2.p,
+                      ldp2, nullptr, s, false)))
+    return rc;
+  // pass 5: the GEMM itself, unprotected
+  if ((rc = gemm_impl(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, s, false))) return rc;
+  // pass 6: verify / locate / correct on the finished C (MODE 3)
+  CUtensorMap mC;
+  if ((rc = make_map(&mC, C, M, N, ldc, BM, BN, false))) return rc;
+  Params p;
+  memset(&p, 0, sizeof(p));
+  p.M = M; p.N = N; p.K = K; p.alpha = alpha; p.beta = beta;
+  p.A = A; p.B = B; p.lda = lda; p.ldb = ldb;
+  p.C = (double *)w.uC.p; p.ldc = ldcc;          // copy of C_in for recomputation
+  p.Cout = C; p.ldcout = ldc;
+  p.nI = (int)nI; p.nJ = (int)nJ; p.nks = (int)nks; p.Kp = Kp;
+  p.arowabs = (const double *)w.arowabs.p; p.aabsmax = (const double *)w.aabsmax.p;
+  p.bcolabs = (const double *)w.bcolabs.p; p.babsmax = (const double *)w.babsmax.p;
+  p.P1 = (const double *)w.uP1.p; p.ldp1 = ldp1; p.P2 = (const double *)w.uP2.p; p.ldp2 = ldp2;
+  p.ccs = (const double *)w.uccs.p; p.ccsa = (const double *)w.uccsa.p;
+  p.crs = (const double *)w.ucrs.p; p.crsa = (const double *)w.ucrsa.p;
+  p.rep = (DevReport *)w.rep.p;
+  p.loc = (DevLoc *)w.loc.p;
+  p.loc_cap = LOC_CAP_DEV;
+  p.wait_limit_ns = wait_limit_ns();
+  p.nsplit = 1;
+  cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
+  cudaError_t e;
+  if (!ta_t && !tb_t) e = launch_gemm_nn(true, false, 3, mC, mC, mC, mC, p, s);
+  else if (!ta_t && tb_t) e = launch_gemm_nt(true, false, 3, mC, mC, mC, mC, p, s);
+  else if (ta_t && !tb_t) e = launch_gemm_tn(true, false, 3, mC, mC, mC, mC, p, s);
+  else e = launch_gemm_tt(true, false, 3, mC, mC, mC, mC, p, s);
+  g_launches++;
+  if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
+  if (rep) return copy_report(w, rep, s);
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
 
 int ftgemm_encode_operands(char transA, char transB, int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
@@ -728,7 +823,7 @@ int ftgemm_finalize(void) {
   cudaDeviceSynchronize();
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
-                  &w.W, &w.wpc, &w.wpr};
+                  &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;

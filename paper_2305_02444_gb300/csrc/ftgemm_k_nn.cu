@@ -23,6 +23,7 @@ cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &a, co
     if (inj) return launch_variant_nn<true, true, 1>(a, b, c, w, p, s);
     return launch_variant_nn<true, false, 1>(a, b, c, w, p, s);
   }
+  if (mode == 3) return launch_variant_nn<true, false, 3>(a, b, c, w, p, s);
   if (mode == 2) {
     if (!ft) return launch_variant_nn<false, false, 2>(a, b, c, w, p, s);
     return launch_variant_nn<true, false, 2>(a, b, c, w, p, s);

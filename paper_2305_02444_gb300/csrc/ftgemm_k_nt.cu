@@ -23,6 +23,7 @@ cudaError_t launch_gemm_nt(bool ft, bool inj, int mode, const CUtensorMap &a, co
     if (inj) return launch_variant_nt<true, true, 1>(a, b, c, w, p, s);
     return launch_variant_nt<true, false, 1>(a, b, c, w, p, s);
   }
+  if (mode == 3) return launch_variant_nt<true, false, 3>(a, b, c, w, p, s);
   if (mode == 2) {
     if (!ft) return launch_variant_nt<false, false, 2>(a, b, c, w, p, s);
     return launch_variant_nt<true, false, 2>(a, b, c, w, p, s);

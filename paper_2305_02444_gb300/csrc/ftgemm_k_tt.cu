@@ -23,6 +23,7 @@ cudaError_t launch_gemm_tt(bool ft, bool inj, int mode, const CUtensorMap &a, co
     if (inj) return launch_variant_tt<true, true, 1>(a, b, c, w, p, s);
     return launch_variant_tt<true, false, 1>(a, b, c, w, p, s);
   }
+  if (mode == 3) return launch_variant_tt<true, false, 3>(a, b, c, w, p, s);
   if (mode == 2) {
     if (!ft) return launch_variant_tt<false, false, 2>(a, b, c, w, p, s);
     return launch_variant_tt<true, false, 2>(a, b, c, w, p, s);

@@ -100,6 +100,8 @@ __device__ __forceinline__ void recompute_elem(const Params &p, double *sC, int 
 //         product and its predicted-checksum partials for MODE 2.
 // MODE 2: split-K reduction: sums the partials of a tile, then runs the same
 //         epilogue as MODE 0 (beta*C encode, verify, locate, correct, store).
+// MODE 3: verify-only pass of the unfused ablation: the tile of a finished
+//         GEMM, predicted checksums and C sums computed by separate passes.
 template <bool TA, bool TB, bool FT, bool INJ, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ftdgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int I = tile % p.nI, J = tile / p.nI;
   const int i0 = I * BM, j0 = J * BN;
   const int mI = (int)min((long long)BM, p.M - i0), nJt = (int)min((long long)BN, p.N - j0);
-  const int nks = (MODE == 2) ? 0 : s_end - s_begin;  // k-slabs this CTA accumulates
+  const int nks = (MODE >= 2) ? 0 : s_end - s_begin;  // k-slabs this CTA accumulates
   const unsigned long long limit = p.wait_limit_ns;
   int *err = &p.rep->err;
   double *sC = reinterpret_cast<double *>(smem);  // output tile, column-major [BN][BM]
@@ -302,12 +304,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   }
 
+  if (MODE == 3) {
+    // predicted checksums without alpha/beta, from the separate skinny GEMMs
+    if (tid < 128) {
+      if (tid < nJt) csacc = p.P1[(long long)I + (long long)(j0 + tid) * p.ldp1];
+    } else if (tid - 128 < mI) {
+      csacc = p.P2[(long long)(i0 + tid - 128) + (long long)J * p.ldp2];
+    }
+  }
+
   // ----------------------------------------------------------------- epilogue
   const bool use_c = (p.beta != 0.0);
   // rounding terms of the threshold: K products, L sums, the epilogue, and
   // (split-K) one addition per partial
-  const long long nextra = 3 + ((MODE == 2) ? p.nsplit : 0);
-  if (use_c) {
+  // (split-K) one addition per partial; MODE 3's predicted checksums come from
+  // a separate GEMM that may itself have split K (at most 32 partials)
+  const long long nextra = 3 + ((MODE == 2) ? p.nsplit : 0) + ((MODE == 3) ? 32 : 0);
+  if (use_c || MODE == 3) {  // MODE 3 loads the finished output tile instead
     if (tid == 0) {
       mbar_arrive_expect_tx(cbar, CTILE_BYTES);
       tma_load_2d(smem_u32(sC), &tmC, cbar, i0, j0);
@@ -325,7 +338,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // FP32 pipe with upward rounding (each partial sum stays an upper bound).
   const int r = tid & 127, h = tid >> 7;
   // beta-side sums of C for the predicted checksums and the thresholds
-  if (FT && use_c) {
+  if (MODE == 3 && use_c) {
+    // from the separate pass over C
+    if (tid < 128) {
+      s_cc[tid] = tid < nJt ? p.ccs[(long long)I * p.N + j0 + tid] : 0.0;
+      s_cca[tid] = tid < nJt ? p.ccsa[(long long)I * p.N + j0 + tid] : 0.0;
+    } else {
+      const int i = tid - 128;
+      s_rc[i] = i < mI ? p.crs[(long long)J * p.M + i0 + i] : 0.0;
+      s_rca[i] = i < mI ? p.crsa[(long long)J * p.M + i0 + i] : 0.0;
+    }
+  } else if (FT && use_c) {
     double rs = 0.0, cs = 0.0;
     float ra = 0.0f, ca = 0.0f;
 #pragma unroll 8
@@ -349,14 +372,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (FT) compute_sync();
 
   // out = alpha*acc + beta*C, written over the staged C tile
+  if (MODE != 3) {
 #pragma unroll
-  for (int pp = 0; pp < 8; ++pp)
+    for (int pp = 0; pp < 8; ++pp)
 #pragma unroll
-    for (int qq = 0; qq < 8; ++qq) {
-      const int idx = (ty + 16 * qq) * BM + tx + 16 * pp;
-      sC[idx] = use_c ? fma(p.alpha, acc[pp][qq], p.beta * sC[idx]) : p.alpha * acc[pp][qq];
-    }
-  compute_sync();
+      for (int qq = 0; qq < 8; ++qq) {
+        const int idx = (ty + 16 * qq) * BM + tx + 16 * pp;
+        sC[idx] = use_c ? fma(p.alpha, acc[pp][qq], p.beta * sC[idx]) : p.alpha * acc[pp][qq];
+      }
+    compute_sync();
+  }
 
   if (FT) {
     // reference checksums of the computed tile
@@ -456,6 +481,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // (row) dimension it writes whole 16-byte chunks, so a tile ending on an odd
   // row would also write the first padding row: such tiles use plain stores.
   const bool tma_store = !((p.M & 1) && (i0 + BM > p.M));
+  if (MODE == 3 && cnt[C_NR] + cnt[C_NC] == 0) {
+    // verify-only pass: nothing was corrected, the output is already in place
+    if (tid == 0) {
+      DevReport *r = p.rep;
+      if (cnt[C_UNVER]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[C_UNVER]);
+    }
+    return;
+  }
+  double *Cst = (MODE == 3) ? p.Cout : p.C;
+  const long long ldst = (MODE == 3) ? p.ldcout : p.ldc;
   if (tma_store) {
     fence_proxy_async_smem();
     compute_sync();
@@ -463,7 +498,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     compute_sync();
     for (int e = tid; e < mI * nJt; e += NCOMPUTE) {
       const int il = e % mI, jl = e / mI;
-      p.C[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldc] = sC[jl * BM + il];
+      Cst[(long long)(i0 + il) + (long long)(j0 + jl) * ldst] = sC[jl * BM + il];
     }
   }
   if (tid == 0) {

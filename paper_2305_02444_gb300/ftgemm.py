@@ -68,6 +68,7 @@ def lib():
         L.ftgemm_d_noft.argtypes = _GEMM_ARGS + [_vp]
         L.ftgemm_d_host.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
         L.ftgemm_d_noalloc.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
+        L.ftgemm_d_unfused.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
         L.ftgemm_encode_operands.argtypes = [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _vp, _i64,
                                              _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.ftgemm_set_injection.argtypes = [ctypes.POINTER(Inject)]
@@ -83,7 +84,7 @@ def lib():
         L.ftgemm_timing_read.restype = ctypes.c_int
         L.ftgemm_strerror.argtypes = [ctypes.c_int]
         L.ftgemm_strerror.restype = ctypes.c_char_p
-        for f in ("ftgemm_d", "ftgemm_d_noft", "ftgemm_d_host", "ftgemm_d_noalloc", "ftgemm_encode_operands",
+        for f in ("ftgemm_d", "ftgemm_d_noft", "ftgemm_d_host", "ftgemm_d_noalloc", "ftgemm_d_unfused", "ftgemm_encode_operands",
                   "ftgemm_set_injection", "ftgemm_selftest_wait_timeout", "ftgemm_finalize"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -156,6 +157,20 @@ def ftgemm_d_host(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 
     rc = lib().ftgemm_d_host(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
                              _ptr(C), ldc, ctypes.byref(r), _stream(stream))
     return rc, _report_dict(r, locs, loc_cap)
+
+
+def ftgemm_d_unfused(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, report=True,
+                     loc_cap=4096, stream=None):
+    """The unfused ablation (separate checksum, GEMM and verify passes);
+    returns (rc, report dict or None)."""
+    if report:
+        r, locs = _report(loc_cap)
+        rc = lib().ftgemm_d_unfused(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb,
+                                    beta, _ptr(C), ldc, ctypes.byref(r), _stream(stream))
+        return rc, _report_dict(r, locs, loc_cap)
+    rc = lib().ftgemm_d_unfused(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                                _ptr(C), ldc, None, _stream(stream))
+    return rc, None
 
 
 def ftgemm_d_noalloc(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, report=True,

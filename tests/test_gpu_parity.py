@@ -459,3 +459,29 @@ def test_splitk_injection(ft, orc, nsplit):
     got = {l[:2] for l in rep["locs"]}
     assert expect_detected <= got
     assert_parity(orc, P, out, ref, E, extra=extra)
+
+
+# ------------------------------------------------------------------------------ unfused ablation
+
+@pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
+@pytest.mark.parametrize("M,N,K,alpha,beta", [(300, 260, 200, 1.5, 0.5), (256, 384, 1000, -1.0, 0.0),
+                                              (130, 140, 64, 2.0, -1.0), (1024, 512, 512, 1.0, 1.0)])
+def test_unfused_ablation_parity(ft, orc, ta, tb, M, N, K, alpha, beta):
+    """The unfused form (separate checksum passes, skinny GEMMs for the
+    predicted checksums, unprotected GEMM, verify-only pass) gives the same
+    result and a clean report."""
+    P = make_problem(ta, tb, M, N, K, seed=M + N + K)
+    ref, E = oracle_ref(orc, P, alpha, beta)
+    dA, dB, dC = P["A"].cuda(), P["B"].cuda(), P["C"].cuda()
+    rc, rep = ft.ftgemm_d_unfused(ta, tb, M, N, K, alpha, dA, P["lda"], dB, P["ldb"], beta, dC, P["ldc"])
+    torch.cuda.synchronize()
+    assert rc == 0, ft.ftgemm_strerror(rc)
+    assert_parity(orc, P, dC.cpu(), ref, E)
+    for k in ("detected", "flagged_rows", "flagged_cols", "unverifiable", "checksum_only"):
+        assert rep[k] == 0, (k, rep)
+
+
+def test_unfused_requires_aligned_operands(ft):
+    A = torch.zeros(9 * 8, dtype=torch.float64, device="cuda")
+    rc, _ = ft.ftgemm_d_unfused("N", "N", 9, 8, 8, 1.0, A, 9, A, 8, 0.0, A, 10)
+    assert rc == ft.ERR_UNALIGNED
