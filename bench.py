@@ -262,6 +262,78 @@ def sweep(args):
     print(json.dumps({"sweep": rows, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS}), flush=True)
 
 
+def batched(args):
+    """512 independent FT-DGEMMs, M, N, K each log-uniform in [32, 1024], NN,
+    U[-1,1], alpha = 1, beta in {0, 1} per problem, one exponent-bit flip in
+    each of a random 10% of the problems; one persistent launch captured in a
+    CUDA graph, schedule picked by the autotuner."""
+    import numpy as np
+    import torch
+    from paper_2305_02444_gb300 import autotune, build, ftgemm, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    count = 512
+    shapes = inputs.batched_sizes(count, SEED)
+    rng = np.random.default_rng(SEED)
+    betas = rng.integers(0, 2, size=count).astype(float)
+    probs, keep = [], []
+    useful = padded = 0.0
+    for q, (m, n, k) in enumerate(shapes):
+        lda, ldb, ldc = m + (m & 1), k + (k & 1), m + (m & 1)
+        A = inputs.matrix(m, k, SEED + 3 * q, ld=lda, device="cuda", fill_pad=0.0)
+        B = inputs.matrix(k, n, SEED + 3 * q + 1, ld=ldb, device="cuda", fill_pad=0.0)
+        C = inputs.matrix(m, n, SEED + 3 * q + 2, ld=ldc, device="cuda", fill_pad=0.0)
+        keep += [A, B, C]
+        probs.append(("N", "N", m, n, k, 1.0, A, lda, B, ldb, float(betas[q]), C, ldc))
+        useful += 2.0 * m * n * k
+        padded += 2.0 * (-(-m // 128) * 128) * (-(-n // 128) * 128) * (-(-k // 16) * 16)
+    hit = sorted(rng.choice(count, size=count // 10, replace=False).tolist())
+    flips = [(int(rng.integers(shapes[q][0])), int(rng.integers(shapes[q][1])),
+              int(rng.integers(-(-shapes[q][2] // 16))), int(rng.integers(52, 63)), q) for q in hit]
+    sched, tune_ms = autotune.tune_batched([("N", "N", m, n, k) for (m, n, k) in shapes])
+    ftgemm.ftgemm_set_injection(mode=2, flips=flips)
+    plan_ft = ftgemm.BatchedPlan(probs, ft=True, schedule=sched)
+    ftgemm.ftgemm_set_injection(mode=0)
+    plan_noft = ftgemm.BatchedPlan(probs, ft=False, schedule=sched)
+
+    def t(plan, steps):
+        for _ in range(args.warmup):
+            plan.launch()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            plan.launch()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps / 1e3
+
+    steps = max(args.steps, 10)
+    t_ft = t(plan_ft, steps)
+    rc, reps = plan_ft.report()
+    t_noft = t(plan_noft, steps)
+    det = sum(r["detected"] for r in reps)
+    cor = sum(r["corrected"] for r in reps)
+    hit_det = sum(1 for q in hit if reps[q]["detected"] >= 1)
+    line = {"metric": "batched FT-DGEMM TFLOP/s (FP64)", "value": useful / t_ft / 1e12, "unit": "TFLOP/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": t_ft * 1e3,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched_512_loguniform32to1024_NN_alpha1_beta01_flips10pct",
+                       "problems": count, "useful_flop": useful, "padded_flop_128x128x16": padded,
+                       "schedule": sched, "graph": True},
+            "pct_fp64_peak": 100.0 * useful / t_ft / 1e12 / FP64_PEAK_TFLOPS,
+            "padded_tflops": padded / t_ft / 1e12,
+            "noft_tflops": useful / t_noft / 1e12,
+            "overhead_pct": 100.0 * (t_ft / t_noft - 1.0),
+            "errors": {"problems_with_flip": len(hit), "detected": det, "corrected": cor,
+                       "flipped_problems_detected": hit_det, "rc": rc},
+            "autotune_ms": tune_ms}
+    plan_ft.destroy()
+    plan_noft.destroy()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,10 +345,15 @@ def main():
     ap.add_argument("--size", type=int, default=8192, help="M = N = K (default 8192)")
     ap.add_argument("--sweep", action="store_true", help="per-size results of the square sweep")
     ap.add_argument("--sweep-shapes", default="", help="comma list of MxNxK for --sweep")
+    ap.add_argument("--batched", action="store_true", help="the batched workload (512 small problems)")
     args = ap.parse_args()
     set_size(args.size)
     if args.sweep:
         return sweep(args)
+    if args.batched:
+        if args.warmup < 3:
+            args.warmup = 3
+        return batched(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -107,7 +107,8 @@ typedef struct {
  * injection, §3.2). */
 typedef struct {
   int64_t row, col, kstep;
-  int32_t bit, pad;
+  int32_t bit;
+  int32_t problem;  /* batched calls: index of the problem; otherwise ignored */
 } ftgemm_flip;
 
 /* Injection setting, process-global, applied to every later ftgemm_d call
@@ -133,6 +134,7 @@ typedef struct {
   double after;     /* accumulator value after the flip */
   int64_t kfirst;   /* first product the flipped accumulator holds: 0, or the
                        start of its k-split when the call split K */
+  int64_t problem;  /* batched calls: the problem the fault was injected in */
 } ftgemm_flip_log;
 
 /* Fault-tolerant DGEMM (abstract; §2.2).  Encodes, verifies, locates and
@@ -195,6 +197,47 @@ int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K, 
 int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                      const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                      double *C, int64_t ldc, ftgemm_report *rep, void *stream);
+
+/* Batched FT-DGEMM: `count` independent problems (arrays of per-problem
+ * arguments on the host; matrix pointers are device pointers) computed by one
+ * persistent kernel per operand layout present (one for an all-'N' batch):
+ * one CTA per SM takes (problem, tile) work items from a global counter, in
+ * an order fixed by the schedule.  Each problem gets its own report
+ * (reps[p], cap/loc set by the caller; up to 64 locations per problem).
+ * Argument errors return -(100*p + i) for argument i of problem p; operands
+ * must be 16-byte aligned with even leading dimensions (FTGEMM_ERR_UNALIGNED).
+ * Injection (the process-global setting): mode 1 draws `count` faults over
+ * the batch, fault f taking splitmix64 outputs 5f..5f+4 as (problem mod count,
+ * row, col, kstep, bit) of that problem; mode 2 uses ftgemm_flip.problem.
+ * ftgemm_batched = plan create + launch + report + destroy. */
+int ftgemm_batched(int64_t count, const char *transA, const char *transB, const int64_t *M,
+                   const int64_t *N, const int64_t *K, const double *alpha,
+                   const double *const *A, const int64_t *lda, const double *const *B,
+                   const int64_t *ldb, const double *beta, double *const *C, const int64_t *ldc,
+                   ftgemm_report *reps, void *stream);
+
+/* A batch prepared once and launched many times: plan_create validates the
+ * problems, builds their TMA descriptors, checksum-pass work lists, work
+ * order and injection table in device memory owned by the plan, and captures
+ * one CUDA graph (counter reset, batched checksum pass, persistent kernels).
+ * ft = 0 builds the same batch without fault tolerance (overhead baseline).
+ * schedule: -1 default; otherwise (order) | (log2(chunk) << 4) with order
+ * 0 = problem order, 1 = tiles with the longest K first, 2 = round robin
+ * over problems, and chunk = work items taken per counter access (1, 2, 4,
+ * 8) -- the knob the autotuner searches.  plan_launch enqueues the graph on a
+ * stream; plan_report waits for that stream and fills reps (may be NULL);
+ * the matrices must stay valid while the plan lives. */
+typedef struct ftgemm_batched_plan_s *ftgemm_batched_plan;
+int ftgemm_batched_plan_create(ftgemm_batched_plan *plan, int64_t count, const char *transA,
+                               const char *transB, const int64_t *M, const int64_t *N,
+                               const int64_t *K, const double *alpha, const double *const *A,
+                               const int64_t *lda, const double *const *B, const int64_t *ldb,
+                               const double *beta, double *const *C, const int64_t *ldc, int ft,
+                               int schedule, void *stream);
+int ftgemm_batched_plan_launch(ftgemm_batched_plan plan, void *stream);
+int ftgemm_batched_plan_report(ftgemm_batched_plan plan, ftgemm_report *reps, void *stream);
+int64_t ftgemm_batched_plan_injection_log(ftgemm_batched_plan plan, ftgemm_flip_log *out, int64_t cap);
+int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan);
 
 /* ftgemm_d on HOST matrices: copies A, B (and C unless beta == 0) to device
  * workspace, runs ftgemm_d, copies C back, and waits for the stream.  Pinned

@@ -80,6 +80,13 @@ struct Params {
   long long ldcout;
 };
 
+// One problem of a batch: its TMA descriptors (global memory, 64-byte aligned)
+// and its parameters (rep/loc/flips point at the problem's own slices).
+struct __align__(64) BatchProblem {
+  CUtensorMap tmA, tmB, tmC;
+  Params p;
+};
+
 constexpr int ERR_TIMEOUT = 2;
 
 // ------------------------------------------------------------------ PTX helpers

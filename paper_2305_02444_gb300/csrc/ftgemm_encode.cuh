@@ -123,6 +123,117 @@ __global__ void enc_finish_kernel(const double *__restrict__ part_abs, int nchun
   }
 }
 
+// Batched checksum pass: one item per operand of each problem of a batch;
+// every block covers one 128-wide group of one item over the item's whole
+// other dimension, so each result is written once (no partials).
+struct EncItem {
+  const double *X;       // column-major R x S
+  long long R, S, ld;
+  double *gsum;          // group sums, gsum[G * gstride + (s or r)]
+  long long gstride;
+  double *absv;          // SEG: row abs sums (R); STR: column abs sums (S)
+  double *gmax;          // per group: max of the group's abs sums
+  int first_block;       // prefix sum of the items' group counts
+  int pad;
+};
+
+__device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b) {
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].first_block <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// SEG over groups of 128 rows, all columns of the item in one block.
+__global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__restrict__ items, int nitems) {
+  __shared__ double sh[8][128];
+  __shared__ double smx[8];
+  const int it = find_item(items, nitems, blockIdx.x);
+  const EncItem &E = items[it];
+  const int G = blockIdx.x - E.first_block;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)G * 128;
+  double rabs[4] = {0.0, 0.0, 0.0, 0.0};
+  double mx = 0.0;
+  for (long long s = w; s < E.S; s += 8) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long r = r0 + lane + 32 * q;
+      v[q] = (r < E.R) ? E.X[r + s * E.ld] : 0.0;
+      rabs[q] += fabs(v[q]);
+    }
+    const double sum = warp_sum((v[0] + v[1]) + (v[2] + v[3]));
+    const double ab = warp_sum((fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3])));
+    if (lane == 0) {
+      E.gsum[(long long)G * E.gstride + s] = sum;
+      mx = fmax(mx, ab);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh[w][lane + 32 * q] = rabs[q];
+  if (lane == 0) smx[w] = mx;
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+    const long long r = r0 + threadIdx.x;
+    if (r < E.R) E.absv[r] = t;
+  }
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int q = 0; q < 8; ++q) m = fmax(m, smx[q]);
+    E.gmax[G] = m;
+  }
+}
+
+// STR over groups of 128 columns, all rows of the item in one block.
+__global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__restrict__ items, int nitems) {
+  __shared__ double sh[8][128];
+  __shared__ double smx[8];
+  const int it = find_item(items, nitems, blockIdx.x);
+  const EncItem &E = items[it];
+  const int G = blockIdx.x - E.first_block;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long s0 = (long long)G * 128;
+  const int ns = (int)min(128LL, E.S - s0);
+  for (int s = threadIdx.x; s < 128; s += 256) {
+    for (int q = 0; q < 8; ++q) sh[q][s] = 0.0;
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (long long rb = 0; rb < E.R; rb += 256) {
+    const long long r = rb + threadIdx.x;
+    double sum = 0.0, ab = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const double v = (r < E.R) ? E.X[r + (s0 + s) * E.ld] : 0.0;
+      sum += v;
+      ab += fabs(v);
+      const double wa = warp_sum(fabs(v));
+      if (lane == 0) sh[w][s] += wa;
+    }
+    if (r < E.R) E.gsum[(long long)G * E.gstride + r] = sum;
+    mx = fmax(mx, ab);
+  }
+  const double m = warp_max(mx);
+  if (lane == 0) smx[w] = m;
+  __syncthreads();
+  if (threadIdx.x < ns) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+    E.absv[s0 + threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) {
+    double mm = 0.0;
+    for (int q = 0; q < 8; ++q) mm = fmax(mm, smx[q]);
+    E.gmax[G] = mm;
+  }
+}
+
 // Unfused ablation: one pass over C that keeps a copy of C_in (needed to
 // recompute an element after the GEMM overwrote C) and takes, per 128x128
 // tile, the column sums over the tile's rows and the row sums over its

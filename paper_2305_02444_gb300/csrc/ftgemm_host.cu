@@ -24,6 +24,14 @@ cudaError_t launch_main_tn(bool ft, bool inj, const CUtensorMap &, const CUtenso
                            const Params &, cudaStream_t);
 cudaError_t launch_main_tt(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
                            const Params &, cudaStream_t);
+cudaError_t launch_batched_nn(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
+                              int *, int *, int, cudaStream_t);
+cudaError_t launch_batched_nt(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
+                              int *, int *, int, cudaStream_t);
+cudaError_t launch_batched_tn(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
+                              int *, int *, int, cudaStream_t);
+cudaError_t launch_batched_tt(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
+                              int *, int *, int, cudaStream_t);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
 cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
                            const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
@@ -318,7 +326,7 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
       L[f].col = (long long)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 1) % (uint64_t)N);
       L[f].kstep = (long long)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 2) % (uint64_t)nks);
       L[f].bit = (int)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 3) % 63u);
-      L[f].pad = 0;
+      L[f].problem = 0;
     }
   } else {
     L = g_inj.list;
@@ -1027,3 +1035,417 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
   }
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// Batched FT-DGEMM: many independent problems in one persistent launch per
+// operand layout, captured once into a CUDA graph.
+namespace {
+
+constexpr int PLAN_LOC_CAP = 64;  // location records kept per problem
+
+}  // namespace
+
+struct ftgemm_batched_plan_s {
+  int dev = 0;
+  long long count = 0;
+  bool ft = true, inj = false;
+  int kernels = 0;                       // kernels per graph launch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void *> bufs;              // device allocations owned by the plan
+  DevReport *reps = nullptr;
+  DevLoc *locs = nullptr;
+  DevFlip *flips = nullptr;
+  long long nflips = 0;
+  std::vector<long long> flip_perm;      // sorted position -> original index
+  std::vector<int> flip_problem;         // original index -> problem
+};
+
+namespace {
+
+void plan_free(ftgemm_batched_plan_s *P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  for (void *b : P->bufs) cudaFree(b);
+  delete P;
+}
+
+template <typename T>
+int plan_alloc(ftgemm_batched_plan_s *P, T **out, size_t n) {
+  void *q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(n * sizeof(T), 256)) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_NOMEM;
+  }
+  P->bufs.push_back(q);
+  *out = (T *)q;
+  return 0;
+}
+
+long long round32(long long n) { return (n + 31) / 32 * 32; }
+
+}  // namespace
+
+extern "C" {
+
+int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, const char *transA,
+                               const char *transB, const int64_t *M, const int64_t *N, const int64_t *K,
+                               const double *alpha, const double *const *A, const int64_t *lda,
+                               const double *const *B, const int64_t *ldb, const double *beta, double *const *C,
+                               const int64_t *ldc, int ft, int schedule, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!plan_out) return -1;
+  *plan_out = nullptr;
+  if (count < 0) return -2;
+  for (long long q = 0; q < count; ++q) {
+    const int rc = check_args(transA[q], transB[q], M[q], N[q], K[q], lda[q], ldb[q], ldc[q]);
+    if (rc) return (int)(rc - 100 * q);  // -(100*problem + argument)
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_NODEVICE;
+  }
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+  const int order_kind = schedule < 0 ? 1 : (schedule & 15);
+  const int chunk = schedule < 0 ? 1 : (1 << ((schedule >> 4) & 3));
+  auto *P = new ftgemm_batched_plan_s();
+  P->dev = dev;
+  P->count = count;
+  P->ft = ft != 0;
+  int rc = 0;
+#define PLAN_TRY(x)        \
+  do {                     \
+    if ((rc = (x))) {      \
+      plan_free(P);        \
+      return rc;           \
+    }                      \
+  } while (0)
+
+  // problems with work, their tiles and checksum-vector offsets
+  std::vector<char> work(count, 0);
+  std::vector<long long> nI(count), nJ(count), nks(count), Kp(count), tiles(count);
+  std::vector<long long> off_acs(count), off_bcs(count), off_ar(count), off_am(count), off_bc(count), off_bm(count);
+  long long enc_total = 0;
+  for (long long q = 0; q < count; ++q) {
+    work[q] = M[q] > 0 && N[q] > 0 && K[q] > 0 && alpha[q] != 0.0;
+    nI[q] = (M[q] + BM - 1) / BM; nJ[q] = (N[q] + BN - 1) / BN;
+    nks[q] = (K[q] + BK - 1) / BK; Kp[q] = nks[q] * BK;
+    tiles[q] = work[q] ? nI[q] * nJ[q] : 0;
+    if (work[q] && (!tma_ok(A[q], lda[q]) || !tma_ok(B[q], ldb[q]) || !tma_ok(C[q], ldc[q]))) {
+      plan_free(P);
+      return FTGEMM_ERR_UNALIGNED;
+    }
+    if (!work[q] || !P->ft) continue;
+    off_acs[q] = enc_total; enc_total += round32(nI[q] * Kp[q]);
+    off_bcs[q] = enc_total; enc_total += round32(nJ[q] * Kp[q]);
+    off_ar[q] = enc_total; enc_total += round32(M[q]);
+    off_am[q] = enc_total; enc_total += round32(nI[q]);
+    off_bc[q] = enc_total; enc_total += round32(N[q]);
+    off_bm[q] = enc_total; enc_total += round32(nJ[q]);
+  }
+  double *enc = nullptr;
+  PLAN_TRY(plan_alloc(P, &enc, (size_t)std::max<long long>(1, enc_total)));
+  PLAN_TRY(plan_alloc(P, &P->reps, (size_t)std::max<long long>(1, count)));
+  PLAN_TRY(plan_alloc(P, &P->locs, (size_t)std::max<long long>(1, count) * PLAN_LOC_CAP));
+  int *gerr = nullptr;
+  PLAN_TRY(plan_alloc(P, &gerr, 1));
+
+  // injection table: sorted by (problem, tile, k-step); per-problem tile offsets
+  std::vector<long long> tile_base(count + 1, 0);
+  for (long long q = 0; q < count; ++q) tile_base[q + 1] = tile_base[q] + tiles[q] + 1;
+  std::vector<ftgemm_flip> L;
+  std::vector<int> Lp;
+  if (P->ft && g_inj.mode == 1 && count > 0) {
+    for (long long f = 0; f < g_inj.count; ++f) {
+      const long long q = (long long)(splitmix64(g_inj.seed, 5 * (uint64_t)f) % (uint64_t)count);
+      if (!work[q]) continue;
+      ftgemm_flip x;
+      x.row = (long long)(splitmix64(g_inj.seed, 5 * (uint64_t)f + 1) % (uint64_t)M[q]);
+      x.col = (long long)(splitmix64(g_inj.seed, 5 * (uint64_t)f + 2) % (uint64_t)N[q]);
+      x.kstep = (long long)(splitmix64(g_inj.seed, 5 * (uint64_t)f + 3) % (uint64_t)nks[q]);
+      x.bit = (int)(splitmix64(g_inj.seed, 5 * (uint64_t)f + 4) % 63u);
+      x.problem = (int)q;
+      L.push_back(x);
+      Lp.push_back((int)q);
+    }
+  } else if (P->ft && g_inj.mode == 2) {
+    for (const auto &x : g_inj.list) {
+      const long long q = x.problem;
+      if (q < 0 || q >= count || !work[q] || x.row < 0 || x.row >= M[q] || x.col < 0 || x.col >= N[q] ||
+          x.kstep < 0 || x.kstep >= nks[q] || x.bit < 0 || x.bit > 62) {
+        plan_free(P);
+        return FTGEMM_ERR_INJECT;
+      }
+      L.push_back(x);
+      Lp.push_back((int)q);
+    }
+  }
+  P->nflips = (long long)L.size();
+  P->inj = P->nflips > 0;
+  P->flip_problem = Lp;
+  P->flip_perm.resize(P->nflips);
+  for (long long q = 0; q < P->nflips; ++q) P->flip_perm[q] = q;
+  auto ltile = [&](const ftgemm_flip &f) { return (f.row / BM) + (f.col / BN) * nI[f.problem]; };
+  std::stable_sort(P->flip_perm.begin(), P->flip_perm.end(), [&](long long a, long long b) {
+    if (L[a].problem != L[b].problem) return L[a].problem < L[b].problem;
+    const long long ta = ltile(L[a]), tb = ltile(L[b]);
+    return ta != tb ? ta < tb : L[a].kstep < L[b].kstep;
+  });
+  std::vector<DevFlip> hf(std::max<long long>(1, P->nflips));
+  std::vector<int> hoff(tile_base[count] + 1, 0);
+  for (long long q = 0; q < P->nflips; ++q) {
+    const ftgemm_flip &f = L[P->flip_perm[q]];
+    hf[q].row = f.row; hf[q].col = f.col; hf[q].kstep = f.kstep; hf[q].bit = f.bit;
+    hf[q].applied = 0; hf[q].before = 0.0; hf[q].after = 0.0; hf[q].kfirst = 0;
+    hoff[tile_base[f.problem] + ltile(f) + 1]++;
+  }
+  // offsets are global flip indices; each problem's segment starts where the previous ended
+  {
+    long long run = 0;
+    for (long long q = 0; q < count; ++q) {
+      hoff[tile_base[q]] = (int)run;
+      for (long long t = 0; t < tiles[q]; ++t) {
+        run += hoff[tile_base[q] + t + 1];
+        hoff[tile_base[q] + t + 1] = (int)run;
+      }
+    }
+  }
+  int *doff = nullptr;
+  PLAN_TRY(plan_alloc(P, &P->flips, hf.size()));
+  PLAN_TRY(plan_alloc(P, &doff, hoff.size()));
+  cudaMemcpy(P->flips, hf.data(), sizeof(DevFlip) * hf.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(doff, hoff.data(), sizeof(int) * hoff.size(), cudaMemcpyHostToDevice);
+
+  // problem descriptors (TMA maps + parameters)
+  std::vector<BatchProblem> hp(std::max<long long>(1, count));
+  for (long long q = 0; q < count; ++q) {
+    memset(&hp[q], 0, sizeof(BatchProblem));
+    if (!work[q]) continue;
+    const bool ta_t = is_t(transA[q]), tb_t = is_t(transB[q]);
+    if (ta_t) rc = make_map(&hp[q].tmA, A[q], K[q], M[q], lda[q], BK, BM, true);
+    else rc = make_map(&hp[q].tmA, A[q], M[q], K[q], lda[q], BM, BK, false);
+    if (!rc) rc = tb_t ? make_map(&hp[q].tmB, B[q], N[q], K[q], ldb[q], BN, BK, false)
+                       : make_map(&hp[q].tmB, B[q], K[q], N[q], ldb[q], BK, BN, true);
+    if (!rc) rc = make_map(&hp[q].tmC, C[q], M[q], N[q], ldc[q], BM, BN, false);
+    if (rc) {
+      plan_free(P);
+      return rc;
+    }
+    Params &pp = hp[q].p;
+    pp.M = M[q]; pp.N = N[q]; pp.K = K[q]; pp.alpha = alpha[q]; pp.beta = beta[q];
+    pp.A = A[q]; pp.B = B[q]; pp.C = C[q]; pp.lda = lda[q]; pp.ldb = ldb[q]; pp.ldc = ldc[q];
+    pp.nI = (int)nI[q]; pp.nJ = (int)nJ[q]; pp.nks = (int)nks[q]; pp.Kp = Kp[q];
+    if (P->ft) {
+      pp.acs = enc + off_acs[q]; pp.bcs = enc + off_bcs[q];
+      pp.arowabs = enc + off_ar[q]; pp.aabsmax = enc + off_am[q];
+      pp.bcolabs = enc + off_bc[q]; pp.babsmax = enc + off_bm[q];
+    }
+    pp.rep = P->reps + q;
+    pp.loc = P->locs + q * PLAN_LOC_CAP;
+    pp.loc_cap = PLAN_LOC_CAP;
+    pp.flips = P->flips;
+    pp.tile_off = doff + tile_base[q];
+    pp.wait_limit_ns = wait_limit_ns();
+    pp.nsplit = 1;
+  }
+  BatchProblem *dprobs = nullptr;
+  PLAN_TRY(plan_alloc(P, &dprobs, hp.size()));
+  cudaMemcpy(dprobs, hp.data(), sizeof(BatchProblem) * hp.size(), cudaMemcpyHostToDevice);
+
+  // checksum-pass items: op(A) 'N' and op(B) 'T' are SEG, the others STR
+  std::vector<EncItem> seg, str;
+  int seg_blocks = 0, str_blocks = 0;
+  for (long long q = 0; q < count && P->ft; ++q) {
+    if (!work[q]) continue;
+    EncItem a{}, b{};
+    if (!is_t(transA[q])) { a.X = A[q]; a.R = M[q]; a.S = K[q]; }
+    else { a.X = A[q]; a.R = K[q]; a.S = M[q]; }
+    a.ld = lda[q]; a.gsum = enc + off_acs[q]; a.gstride = Kp[q]; a.absv = enc + off_ar[q]; a.gmax = enc + off_am[q];
+    if (!is_t(transB[q])) { b.X = B[q]; b.R = K[q]; b.S = N[q]; }
+    else { b.X = B[q]; b.R = N[q]; b.S = K[q]; }
+    b.ld = ldb[q]; b.gsum = enc + off_bcs[q]; b.gstride = Kp[q]; b.absv = enc + off_bc[q]; b.gmax = enc + off_bm[q];
+    if (!is_t(transA[q])) { a.first_block = seg_blocks; seg_blocks += (int)nI[q]; seg.push_back(a); }
+    else { a.first_block = str_blocks; str_blocks += (int)nI[q]; str.push_back(a); }
+    if (is_t(transB[q])) { b.first_block = seg_blocks; seg_blocks += (int)nJ[q]; seg.push_back(b); }
+    else { b.first_block = str_blocks; str_blocks += (int)nJ[q]; str.push_back(b); }
+  }
+  EncItem *dseg = nullptr, *dstr = nullptr;
+  PLAN_TRY(plan_alloc(P, &dseg, std::max<size_t>(1, seg.size())));
+  PLAN_TRY(plan_alloc(P, &dstr, std::max<size_t>(1, str.size())));
+  if (!seg.empty()) cudaMemcpy(dseg, seg.data(), sizeof(EncItem) * seg.size(), cudaMemcpyHostToDevice);
+  if (!str.empty()) cudaMemcpy(dstr, str.data(), sizeof(EncItem) * str.size(), cudaMemcpyHostToDevice);
+
+  // work lists per operand layout, in the scheduled order
+  struct Group { std::vector<int> prob, local, order; };
+  Group grp[4];
+  for (long long q = 0; q < count; ++q) {
+    if (!work[q]) continue;
+    Group &g = grp[(is_t(transA[q]) ? 2 : 0) + (is_t(transB[q]) ? 1 : 0)];
+    for (long long t = 0; t < tiles[q]; ++t) { g.prob.push_back((int)q); g.local.push_back((int)t); }
+  }
+  int *counters = nullptr;
+  PLAN_TRY(plan_alloc(P, &counters, 4));
+  int *dgrp[4][3] = {};
+  for (int gi = 0; gi < 4; ++gi) {
+    Group &g = grp[gi];
+    const int total = (int)g.prob.size();
+    g.order.resize(total);
+    for (int i = 0; i < total; ++i) g.order[i] = i;
+    if (order_kind == 1) {  // longest first: k-slabs of the tile, largest first
+      std::stable_sort(g.order.begin(), g.order.end(), [&](int a, int b) { return nks[g.prob[a]] > nks[g.prob[b]]; });
+    } else if (order_kind == 2) {  // round robin over problems
+      std::stable_sort(g.order.begin(), g.order.end(), [&](int a, int b) { return g.local[a] < g.local[b]; });
+    }
+    if (!total) continue;
+    PLAN_TRY(plan_alloc(P, &dgrp[gi][0], total));
+    PLAN_TRY(plan_alloc(P, &dgrp[gi][1], total));
+    PLAN_TRY(plan_alloc(P, &dgrp[gi][2], total));
+    cudaMemcpy(dgrp[gi][0], g.order.data(), sizeof(int) * total, cudaMemcpyHostToDevice);
+    cudaMemcpy(dgrp[gi][1], g.prob.data(), sizeof(int) * total, cudaMemcpyHostToDevice);
+    cudaMemcpy(dgrp[gi][2], g.local.data(), sizeof(int) * total, cudaMemcpyHostToDevice);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    plan_free(P);
+    return FTGEMM_ERR_CUDA;
+  }
+
+  // capture: reset, checksum pass, quick returns, one persistent kernel per layout
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    plan_free(P);
+    return FTGEMM_ERR_CUDA;
+  }
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    cudaMemsetAsync(counters, 0, 4 * sizeof(int), cs);
+    cudaMemsetAsync(gerr, 0, sizeof(int), cs);
+    cudaMemsetAsync(P->reps, 0, sizeof(DevReport) * std::max<long long>(1, count), cs);
+    if (P->ft && enc_total) {
+      cudaMemsetAsync(enc, 0, sizeof(double) * enc_total, cs);
+      if (seg_blocks) { enc_seg_batched_kernel<<<seg_blocks, 256, 0, cs>>>(dseg, (int)seg.size()); P->kernels++; }
+      if (str_blocks) { enc_str_batched_kernel<<<str_blocks, 256, 0, cs>>>(dstr, (int)str.size()); P->kernels++; }
+    }
+    for (long long q = 0; q < count; ++q)
+      if (!work[q] && M[q] > 0 && N[q] > 0 && beta[q] != 1.0) {
+        scale_kernel<<<grid_for(M[q] * N[q]), 256, 0, cs>>>(C[q], M[q], N[q], ldc[q], beta[q]);
+        P->kernels++;
+      }
+    for (int gi = 0; gi < 4; ++gi) {
+      const int total = (int)grp[gi].prob.size();
+      if (!total) continue;
+      const int grid = std::min(nsm, (total + chunk - 1) / chunk);
+      cudaError_t e;
+      if (gi == 0) e = launch_batched_nn(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
+      else if (gi == 1) e = launch_batched_nt(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
+      else if (gi == 2) e = launch_batched_tn(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
+      else e = launch_batched_tt(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
+      ok = ok && e == cudaSuccess;
+      P->kernels++;
+    }
+    ok = (cudaStreamEndCapture(cs, &P->graph) == cudaSuccess) && ok;
+  }
+  if (ok) ok = cudaGraphInstantiate(&P->exec, P->graph, 0) == cudaSuccess;
+  cudaStreamDestroy(cs);
+  if (!ok) {
+    cudaGetLastError();
+    plan_free(P);
+    return FTGEMM_ERR_CUDA;
+  }
+  (void)stream;
+#undef PLAN_TRY
+  *plan_out = P;
+  return 0;
+}
+
+int ftgemm_batched_plan_launch(ftgemm_batched_plan plan, void *stream) {
+  if (!plan || !plan->exec) return -1;
+  if (cudaGraphLaunch(plan->exec, (cudaStream_t)stream) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_CUDA;
+  }
+  g_launches += plan->kernels;
+  return 0;
+}
+
+int ftgemm_batched_plan_report(ftgemm_batched_plan plan, ftgemm_report *reps, void *stream) {
+  if (!plan) return -1;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = plan->count;
+  std::vector<DevReport> hr(std::max<long long>(1, n));
+  std::vector<DevLoc> hl(std::max<long long>(1, n) * PLAN_LOC_CAP);
+  if (cudaMemcpyAsync(hr.data(), plan->reps, sizeof(DevReport) * hr.size(), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(hl.data(), plan->locs, sizeof(DevLoc) * hl.size(), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_CUDA;
+  }
+  int err = 0;
+  for (long long q = 0; q < n; ++q) {
+    if (hr[q].err) err = FTGEMM_ERR_TIMEOUT;
+    if (!reps) continue;
+    ftgemm_report &r = reps[q];
+    r.detected = (long long)hr[q].detected;
+    r.corrected = (long long)hr[q].corrected;
+    r.checksum_only = (long long)hr[q].checksum_only;
+    r.unverifiable = (long long)hr[q].unverifiable;
+    r.flagged_rows = (long long)hr[q].flagged_rows;
+    r.flagged_cols = (long long)hr[q].flagged_cols;
+    r.recomputed = (long long)hr[q].recomputed;
+    r.n_loc = (long long)hr[q].n_loc;
+    if (r.loc)
+      for (long long k = 0; k < std::min<long long>({r.cap, (long long)PLAN_LOC_CAP, r.n_loc}); ++k) {
+        const DevLoc &d = hl[q * PLAN_LOC_CAP + k];
+        r.loc[k].row = d.row; r.loc[k].col = d.col; r.loc[k].tile = d.tile; r.loc[k].kind = d.kind;
+        r.loc[k].delta = d.delta;
+      }
+  }
+  return err;
+}
+
+int64_t ftgemm_batched_plan_injection_log(ftgemm_batched_plan plan, ftgemm_flip_log *out, int64_t cap) {
+  if (!plan) return -1;
+  const long long nf = plan->nflips;
+  if (nf == 0 || cap <= 0 || !out) return nf;
+  std::vector<DevFlip> h((size_t)nf);
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(h.data(), plan->flips, sizeof(DevFlip) * nf, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -FTGEMM_ERR_CUDA;
+  for (long long q = 0; q < nf; ++q) {
+    const long long o = plan->flip_perm[q];
+    if (o >= cap) continue;
+    out[o].row = h[q].row; out[o].col = h[q].col; out[o].kstep = h[q].kstep; out[o].bit = h[q].bit;
+    out[o].applied = h[q].applied; out[o].before = h[q].before; out[o].after = h[q].after;
+    out[o].kfirst = h[q].kfirst;
+    out[o].problem = plan->flip_problem[o];
+  }
+  return nf;
+}
+
+int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan) {
+  if (!plan) return -1;
+  cudaDeviceSynchronize();
+  plan_free(plan);
+  return 0;
+}
+
+int ftgemm_batched(int64_t count, const char *transA, const char *transB, const int64_t *M, const int64_t *N,
+                   const int64_t *K, const double *alpha, const double *const *A, const int64_t *lda,
+                   const double *const *B, const int64_t *ldb, const double *beta, double *const *C,
+                   const int64_t *ldc, ftgemm_report *reps, void *stream) {
+  ftgemm_batched_plan plan = nullptr;
+  int rc = ftgemm_batched_plan_create(&plan, count, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                      1, -1, stream);
+  if (rc) return rc;
+  rc = ftgemm_batched_plan_launch(plan, stream);
+  if (!rc) rc = ftgemm_batched_plan_report(plan, reps, stream);
+  ftgemm_batched_plan_destroy(plan);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,6 +1,7 @@
 // Main-kernel instantiations for op(A) = t, op(B) = t: the unprotected kernel,
 // the fault-tolerant kernel and the fault-tolerant kernel with the injector, for
-// whole tiles (mode 0) and for split-K partials (mode 1) and reductions (mode 2).
+// whole tiles (mode 0), split-K partials (mode 1) and reductions (mode 2), the
+// verify-only pass (mode 3), and the persistent batched kernel.
 #include "ftgemm_kernel.cuh"
 
 namespace ftg {
@@ -36,6 +37,28 @@ cudaError_t launch_gemm_tt(bool ft, bool inj, int mode, const CUtensorMap &a, co
 cudaError_t launch_main_tt(bool ft, bool inj, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &c,
                            const Params &p, cudaStream_t s) {
   return launch_gemm_tt(ft, inj, 0, a, b, c, c, p, s);
+}
+
+template <bool FT, bool INJ>
+static cudaError_t launch_batched_variant_tt(const BatchProblem *probs, const int *order, const int *tile_prob,
+                                              const int *tile_local, int total, int chunk, int *counter, int *gerr,
+                                              int grid, cudaStream_t s) {
+  auto k = ftdgemm_batched_kernel<true, true, FT, INJ>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  k<<<grid, NTHREADS, SMEM_BYTES, s>>>(probs, order, tile_prob, tile_local, total, chunk, counter, gerr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_tt(bool ft, bool inj, const BatchProblem *probs, const int *order,
+                               const int *tile_prob, const int *tile_local, int total, int chunk, int *counter,
+                               int *gerr, int grid, cudaStream_t s) {
+  if (!ft) return launch_batched_variant_tt<false, false>(probs, order, tile_prob, tile_local, total, chunk,
+                                                            counter, gerr, grid, s);
+  if (inj) return launch_batched_variant_tt<true, true>(probs, order, tile_prob, tile_local, total, chunk,
+                                                          counter, gerr, grid, s);
+  return launch_batched_variant_tt<true, false>(probs, order, tile_prob, tile_local, total, chunk, counter,
+                                                  gerr, grid, s);
 }
 
 }  // namespace ftg

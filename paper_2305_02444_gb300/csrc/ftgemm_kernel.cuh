@@ -103,13 +103,9 @@ __device__ __forceinline__ void recompute_elem(const Params &p, double *sC, int 
 // MODE 3: verify-only pass of the unfused ablation: the tile of a finished
 //         GEMM, predicted checksums and C sums computed by separate passes.
 template <bool TA, bool TB, bool FT, bool INJ, int MODE>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    ftdgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
-                   const Params p) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem =
-      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+__device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const CUtensorMap *tmC,
+                                         const CUtensorMap *tmW, const Params &p, const int tile, const int split,
+                                         unsigned char *smem) {
   double *epi = reinterpret_cast<double *>(smem + TILE_REGION);
   double *s_rc = epi, *s_rca = epi + 128, *s_cc = epi + 256, *s_cca = epi + 384;
   double *s_ro = epi + 512, *s_co = epi + 640, *s_pr = epi + 768, *s_pc = epi + 896;
@@ -121,9 +117,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), cbar = smem_u32(bars + 2 * STAGES);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntiles = p.nI * p.nJ;
-  const int tile = (MODE == 1) ? (int)(blockIdx.x % ntiles) : (int)blockIdx.x;
-  const int split = (MODE == 1) ? (int)(blockIdx.x / ntiles) : 0;
   const int s_begin = (MODE == 1) ? split * p.ks_slabs : 0;              // first k-slab (global)
   const int s_end = (MODE == 1) ? min(p.nks, s_begin + p.ks_slabs) : p.nks;
   const int I = tile % p.nI, J = tile / p.nI;
@@ -146,14 +139,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   if (tid == 32) {
     if (MODE != 2) {
-      prefetch_tmap(&tmA);
-      prefetch_tmap(&tmB);
+      prefetch_tmap(tmA);
+      prefetch_tmap(tmB);
     }
-    prefetch_tmap(MODE == 1 ? &tmW : &tmC);
+    prefetch_tmap(MODE == 1 ? tmW : tmC);
   }
   if (tid < 128) { s_rfail[tid] = 0; s_cfail[tid] = 0; }
+  // a previous tile of a persistent CTA read and wrote the ring with generic
+  // accesses: order them before this tile's TMA writes into it
+  fence_proxy_async_smem();
   __syncthreads();
-  if (cnt[C_ABORT]) return;  // an earlier CTA hit a timeout: skip the work
+  if (cnt[C_ABORT]) return;  // an earlier tile hit a timeout: skip the work
 
   // ------------------------------------------------------------------ compute
   // Thread 0 is also the producer: it fills the first STAGES slabs, then after
@@ -165,8 +161,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t fb = full0 + 8 * st;
     mbar_arrive_expect_tx(fb, tx_bytes);
     const int k0 = (s_begin + s) * BK;
-    if (TA) tma_load_2d(sb, &tmA, fb, k0, i0); else tma_load_2d(sb, &tmA, fb, i0, k0);
-    if (TB) tma_load_2d(sb + A_BYTES, &tmB, fb, j0, k0); else tma_load_2d(sb + A_BYTES, &tmB, fb, k0, j0);
+    if (TA) tma_load_2d(sb, tmA, fb, k0, i0); else tma_load_2d(sb, tmA, fb, i0, k0);
+    if (TB) tma_load_2d(sb + A_BYTES, tmB, fb, j0, k0); else tma_load_2d(sb + A_BYTES, tmB, fb, k0, j0);
     if (FT) {
       bulk_load(sb + A_BYTES + B_BYTES, p.acs + (long long)I * p.Kp + k0, CS_BYTES, fb);
       bulk_load(sb + A_BYTES + B_BYTES + CS_BYTES, p.bcs + (long long)J * p.Kp + k0, CS_BYTES, fb);
@@ -277,7 +273,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_proxy_async_smem();
     compute_sync();
     if (tid == 0) {
-      tma_store_3d(&tmW, smem_u32(sC), i0, j0, split);
+      tma_store_3d(tmW, smem_u32(sC), i0, j0, split);
       bulk_commit();
       bulk_wait_all();
     }
@@ -323,7 +319,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (use_c || MODE == 3) {  // MODE 3 loads the finished output tile instead
     if (tid == 0) {
       mbar_arrive_expect_tx(cbar, CTILE_BYTES);
-      tma_load_2d(smem_u32(sC), &tmC, cbar, i0, j0);
+      tma_load_2d(smem_u32(sC), tmC, cbar, i0, j0);
     }
     if (!mbar_wait_bounded(cbar, 0, limit, err)) atomicExch(&cnt[C_ABORT], 1);
     compute_sync();  // every thread leaves together if the C tile never landed
@@ -503,7 +499,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   if (tid == 0) {
     if (tma_store) {
-      tma_store_2d(&tmC, smem_u32(sC), i0, j0);
+      tma_store_2d(tmC, smem_u32(sC), i0, j0);
       bulk_commit();
     }
     if (FT) {
@@ -519,6 +515,53 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (cnt[C_RECOMP]) atomicAdd(&r->recomputed, (unsigned long long)cnt[C_RECOMP]);
     }
     if (tma_store) bulk_wait_all();
+  }
+}
+
+// One CTA per tile (MODE 0, 2, 3) or per tile and k-split (MODE 1).
+template <bool TA, bool TB, bool FT, bool INJ, int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ftdgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
+                   const Params p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int ntiles = p.nI * p.nJ;
+  const int tile = (MODE == 1) ? (int)(blockIdx.x % ntiles) : (int)blockIdx.x;
+  const int split = (MODE == 1) ? (int)(blockIdx.x / ntiles) : 0;
+  ftd_tile<TA, TB, FT, INJ, MODE>(&tmA, &tmB, &tmC, &tmW, p, tile, split, smem);
+}
+
+// Persistent batched kernel: one CTA per SM takes `chunk` work items at a time
+// from a global counter; item q is tile tile_local[order[q]] of problem
+// tile_prob[order[q]] (the order is the schedule the host chose).  A bounded
+// wait that expires in any tile stops every CTA before its next tile.
+template <bool TA, bool TB, bool FT, bool INJ>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    ftdgemm_batched_kernel(const BatchProblem *__restrict__ probs, const int *__restrict__ order,
+                           const int *__restrict__ tile_prob, const int *__restrict__ tile_local, int total,
+                           int chunk, int *counter, int *gerr) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ int s_next, s_stop;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_stop = *reinterpret_cast<volatile int *>(gerr) != 0;
+      s_next = s_stop ? total : atomicAdd(counter, chunk);
+    }
+    __syncthreads();
+    const int base = s_next;
+    if (base >= total) break;
+    for (int c = 0; c < chunk && base + c < total; ++c) {
+      const int g = order[base + c];
+      const BatchProblem *bp = probs + tile_prob[g];
+      ftd_tile<TA, TB, FT, INJ, 0>(&bp->tmA, &bp->tmB, &bp->tmC, &bp->tmC, bp->p, tile_local[g], 0, smem);
+      __syncthreads();
+      if (threadIdx.x == 0 && *reinterpret_cast<volatile int *>(&bp->p.rep->err) != 0) atomicExch(gerr, ERR_TIMEOUT);
+    }
   }
 }
 

@@ -39,7 +39,7 @@ class Report(ctypes.Structure):
 
 class Flip(ctypes.Structure):
     _fields_ = [("row", _i64), ("col", _i64), ("kstep", _i64), ("bit", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("problem", ctypes.c_int32)]
 
 
 class Inject(ctypes.Structure):
@@ -49,7 +49,8 @@ class Inject(ctypes.Structure):
 
 class FlipLog(ctypes.Structure):
     _fields_ = [("row", _i64), ("col", _i64), ("kstep", _i64), ("bit", ctypes.c_int32),
-                ("applied", ctypes.c_int32), ("before", _dbl), ("after", _dbl), ("kfirst", _i64)]
+                ("applied", ctypes.c_int32), ("before", _dbl), ("after", _dbl), ("kfirst", _i64),
+                ("problem", _i64)]
 
 
 _lib = None
@@ -82,6 +83,25 @@ def lib():
         L.ftgemm_timing.restype = ctypes.c_int
         L.ftgemm_timing_read.argtypes = [ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
         L.ftgemm_timing_read.restype = ctypes.c_int
+        _pp = ctypes.POINTER(ctypes.c_void_p)
+        _pc = ctypes.c_char_p
+        _pi = ctypes.POINTER(_i64)
+        _pd = ctypes.POINTER(_dbl)
+        L.ftgemm_batched.argtypes = [_i64, _pc, _pc, _pi, _pi, _pi, _pd, _pp, _pi, _pp, _pi, _pd, _pp, _pi,
+                                     ctypes.POINTER(Report), _vp]
+        L.ftgemm_batched.restype = ctypes.c_int
+        L.ftgemm_batched_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), _i64, _pc, _pc, _pi, _pi, _pi,
+                                                 _pd, _pp, _pi, _pp, _pi, _pd, _pp, _pi, ctypes.c_int,
+                                                 ctypes.c_int, _vp]
+        L.ftgemm_batched_plan_create.restype = ctypes.c_int
+        L.ftgemm_batched_plan_launch.argtypes = [ctypes.c_void_p, _vp]
+        L.ftgemm_batched_plan_launch.restype = ctypes.c_int
+        L.ftgemm_batched_plan_report.argtypes = [ctypes.c_void_p, ctypes.POINTER(Report), _vp]
+        L.ftgemm_batched_plan_report.restype = ctypes.c_int
+        L.ftgemm_batched_plan_injection_log.argtypes = [ctypes.c_void_p, ctypes.POINTER(FlipLog), _i64]
+        L.ftgemm_batched_plan_injection_log.restype = _i64
+        L.ftgemm_batched_plan_destroy.argtypes = [ctypes.c_void_p]
+        L.ftgemm_batched_plan_destroy.restype = ctypes.c_int
         L.ftgemm_strerror.argtypes = [ctypes.c_int]
         L.ftgemm_strerror.restype = ctypes.c_char_p
         for f in ("ftgemm_d", "ftgemm_d_noft", "ftgemm_d_host", "ftgemm_d_noalloc", "ftgemm_d_unfused", "ftgemm_encode_operands",
@@ -195,7 +215,8 @@ def ftgemm_encode_operands(transA, transB, M, N, K, A, lda, B, ldb, acs, aabsmax
 
 
 def ftgemm_set_injection(mode=0, seed=0, count=0, flips=None):
-    """mode 0 off, 1 seeded random (count per call), 2 explicit list of (row, col, kstep, bit)."""
+    """mode 0 off, 1 seeded random (count per call), 2 explicit list of
+    (row, col, kstep, bit) or, for batched calls, (row, col, kstep, bit, problem)."""
     cfg = Inject()
     cfg.mode = mode
     cfg.seed = seed & (2 ** 64 - 1)
@@ -204,8 +225,9 @@ def ftgemm_set_injection(mode=0, seed=0, count=0, flips=None):
     if mode == 2:
         fl = list(flips or [])
         keep = (Flip * max(1, len(fl)))()
-        for q, (r, c, s, b) in enumerate(fl):
-            keep[q].row, keep[q].col, keep[q].kstep, keep[q].bit = int(r), int(c), int(s), int(b)
+        for q, f in enumerate(fl):
+            keep[q].row, keep[q].col, keep[q].kstep, keep[q].bit = (int(x) for x in f[:4])
+            keep[q].problem = int(f[4]) if len(f) > 4 else 0
         cfg.list = ctypes.cast(keep, ctypes.POINTER(Flip))
         cfg.n_list = len(fl)
     return lib().ftgemm_set_injection(ctypes.byref(cfg))
@@ -253,3 +275,89 @@ def ftgemm_strerror(code: int) -> str:
 
 def ftgemm_finalize() -> int:
     return lib().ftgemm_finalize()
+
+
+class _BatchArgs:
+    """ctypes arrays for a list of problems (ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc)."""
+
+    def __init__(self, problems):
+        n = len(problems)
+        self.n = n
+        self.ta = ctypes.create_string_buffer(bytes("".join(p[0] for p in problems), "ascii"), max(1, n))
+        self.tb = ctypes.create_string_buffer(bytes("".join(p[1] for p in problems), "ascii"), max(1, n))
+        I64 = _i64 * max(1, n)
+        D = _dbl * max(1, n)
+        P = ctypes.c_void_p * max(1, n)
+        self.M = I64(*[p[2] for p in problems]); self.N = I64(*[p[3] for p in problems])
+        self.K = I64(*[p[4] for p in problems]); self.alpha = D(*[p[5] for p in problems])
+        self.A = P(*[_ptr(p[6]) for p in problems]); self.lda = I64(*[p[7] for p in problems])
+        self.B = P(*[_ptr(p[8]) for p in problems]); self.ldb = I64(*[p[9] for p in problems])
+        self.beta = D(*[p[10] for p in problems])
+        self.C = P(*[_ptr(p[11]) for p in problems]); self.ldc = I64(*[p[12] for p in problems])
+
+    def args(self):
+        c = ctypes.cast
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        return (self.n, self.ta, self.tb, self.M, self.N, self.K, self.alpha, c(self.A, pp), self.lda,
+                c(self.B, pp), self.ldb, self.beta, c(self.C, pp), self.ldc)
+
+
+def _reports(n, cap):
+    reps = (Report * max(1, n))()
+    keep = []
+    for q in range(n):
+        locs = (Loc * max(1, cap))()
+        keep.append(locs)
+        reps[q].cap = cap
+        reps[q].loc = ctypes.cast(locs, ctypes.POINTER(Loc))
+    return reps, keep
+
+
+def ftgemm_batched(problems, loc_cap=16, stream=None):
+    """Batched FT-DGEMM; returns (rc, list of per-problem report dicts)."""
+    a = _BatchArgs(problems)
+    reps, keep = _reports(a.n, loc_cap)
+    rc = lib().ftgemm_batched(*a.args(), reps, _stream(stream))
+    return rc, [_report_dict(reps[q], keep[q], loc_cap) for q in range(a.n)]
+
+
+class BatchedPlan:
+    """A batch captured once into a CUDA graph (see ftgemm_batched_plan_create)."""
+
+    def __init__(self, problems, ft=True, schedule=-1, stream=None):
+        self._args = _BatchArgs(problems)
+        self.n = self._args.n
+        self.h = ctypes.c_void_p()
+        rc = lib().ftgemm_batched_plan_create(ctypes.byref(self.h), *self._args.args(), 1 if ft else 0,
+                                              schedule, _stream(stream))
+        if rc:
+            raise RuntimeError(f"ftgemm_batched_plan_create: {rc} {ftgemm_strerror(rc)}")
+
+    def launch(self, stream=None):
+        rc = lib().ftgemm_batched_plan_launch(self.h, _stream(stream))
+        if rc:
+            raise RuntimeError(f"ftgemm_batched_plan_launch: {ftgemm_strerror(rc)}")
+
+    def report(self, loc_cap=16, stream=None):
+        reps, keep = _reports(self.n, loc_cap)
+        rc = lib().ftgemm_batched_plan_report(self.h, reps, _stream(stream))
+        return rc, [_report_dict(reps[q], keep[q], loc_cap) for q in range(self.n)]
+
+    def injection_log(self):
+        n = lib().ftgemm_batched_plan_injection_log(self.h, None, 0)
+        if n <= 0:
+            return []
+        buf = (FlipLog * n)()
+        lib().ftgemm_batched_plan_injection_log(self.h, buf, n)
+        return [{f: getattr(buf[q], f) for f, _ in FlipLog._fields_} for q in range(n)]
+
+    def destroy(self):
+        if self.h:
+            lib().ftgemm_batched_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
