@@ -223,14 +223,15 @@ def sweep(args):
     if args.sweep_shapes:
         shapes = [tuple(int(x) for x in sh.split("x")) for sh in args.sweep_shapes.split(",")]
     for (m, n, k) in shapes:
-        A = inputs.matrix(m, k, SEED, device="cuda"); B = inputs.matrix(k, n, SEED + 1, device="cuda")
-        C = inputs.matrix(m, n, SEED + 2, device="cuda")
+        A = inputs.matrix(m, k, SEED, args.sweep_dist, device="cuda")
+        B = inputs.matrix(k, n, SEED + 1, args.sweep_dist, device="cuda")
+        C = inputs.matrix(m, n, SEED + 2, args.sweep_dist, device="cuda")
         tiles = -(-m // 128) * -(-n // 128)
         nfl = math.ceil(tiles / 64)
-        reps = max(2, min(10, int(2e12 / (2.0 * m * n * k))))
+        reps = args.sweep_reps or max(2, min(10, int(2e12 / (2.0 * m * n * k))))
 
         def t(fn):
-            for _ in range(3):
+            for _ in range(args.sweep_warmup):
                 fn()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -244,7 +245,8 @@ def sweep(args):
         ft_call = lambda: ftgemm.ftgemm_d("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, report=False)
         t_noft = t(lambda: ftgemm.ftgemm_d_noft("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m))
         t_ft = t(ft_call)
-        t_unf = t(lambda: ftgemm.ftgemm_d_unfused("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, report=False))
+        t_unf = float("nan") if args.no_unfused else \
+            t(lambda: ftgemm.ftgemm_d_unfused("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, report=False))
         ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nfl)
         t_inj = t(ft_call)
         rc, rep = ftgemm.ftgemm_d("N", "N", m, n, k, ALPHA, A, m, B, k, BETA, C, m, loc_cap=0)
@@ -345,6 +347,10 @@ def main():
     ap.add_argument("--size", type=int, default=8192, help="M = N = K (default 8192)")
     ap.add_argument("--sweep", action="store_true", help="per-size results of the square sweep")
     ap.add_argument("--sweep-shapes", default="", help="comma list of MxNxK for --sweep")
+    ap.add_argument("--sweep-warmup", type=int, default=3)
+    ap.add_argument("--sweep-reps", type=int, default=0, help="timed calls per path (0: by size)")
+    ap.add_argument("--sweep-dist", default="uniform", help="input distribution for --sweep")
+    ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--batched", action="store_true", help="the batched workload (512 small problems)")
     args = ap.parse_args()
     set_size(args.size)

@@ -77,7 +77,9 @@ typedef struct {
   int32_t tile;  /* tile id: I + J * ceil(M / FTGEMM_BM) */
   int32_t kind;  /* 0: found at a flagged row x flagged column intersection;
                     1: found by the fallback that recomputes whole row/column
-                       segments of a tile */
+                       segments of a tile;
+                    2: found by a per-k-panel check (accumulator corrected
+                       before the end of K) */
   double delta;  /* stored value minus recomputed value (may be Inf/NaN) */
 } ftgemm_loc;
 
@@ -96,6 +98,8 @@ typedef struct {
   int64_t flagged_rows;  /* row mismatches raised by the first verification */
   int64_t flagged_cols;  /* column mismatches raised by the first verification */
   int64_t recomputed;    /* elements recomputed, wrong or not */
+  int64_t panel_detected; /* of `detected`, found by a per-k-panel check
+                            (ftgemm_set_panel_check) before the end of K */
   int64_t n_loc;         /* location records produced */
   int64_t cap;           /* capacity of loc (input) */
   ftgemm_loc *loc;       /* caller-owned host array of cap records (input) */
@@ -239,6 +243,28 @@ int ftgemm_batched_plan_report(ftgemm_batched_plan plan, ftgemm_report *reps, vo
 int64_t ftgemm_batched_plan_injection_log(ftgemm_batched_plan plan, ftgemm_flip_log *out, int64_t cap);
 int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan);
 
+/* Split-precision FT-GEMM on the BF16 tensor cores (FP32 accumulation):
+ *  - nslices = 0: the plain BF16 form: op(A) and op(B) rounded to bf16, FP32
+ *    accumulation over K, out = alpha * acc + beta * C in FP64;
+ *  - nslices = S in 1..15: FP64 emulated by error-free splitting (Ozaki,
+ *    Ogita, Oishi, Rump 2012): every row of op(A) and column of op(B) is
+ *    scaled by a power of two and split into S integer slices of w bits
+ *    (w = 8, 7, 6, 5 for K <= 256, 1024, 4096, larger: the FP32 accumulation
+ *    of a slice pair stays exact over the chunk of K it covers); the
+ *    S(S+1)/2 slice pairs with s + t < S are bf16 tensor-core products folded
+ *    into FP64 with their power-of-two weights.  S = 11 (w = 5) keeps about
+ *    55 bits of every row's largest element; entries far smaller than their
+ *    row's (column's) largest keep fewer bits.
+ * ft = 1: predicted checksums in FP32 from the staged slices, reference sums,
+ * verification and correction (FP64 recomputation from the original operands)
+ * in FP64; ft = 0 compiles the checks out (overhead baseline).  Injection
+ * (ftgemm_set_injection) flips bits of the FP64 accumulator after the slice
+ * pair numbered `kstep` has been folded in (kstep < number of pairs).
+ * Returns -14 for an invalid nslices. */
+int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                   double *C, int64_t ldc, int nslices, int ft, ftgemm_report *rep, void *stream);
+
 /* ftgemm_d on HOST matrices: copies A, B (and C unless beta == 0) to device
  * workspace, runs ftgemm_d, copies C back, and waits for the stream.  Pinned
  * host memory makes the copies fastest; pageable memory also works. */
@@ -279,6 +305,16 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
  * sums the partial tiles and runs the verification on the whole tile),
  * 1 never splits, n >= 2 forces n splits (fewer when K is short). */
 int ftgemm_set_splitk(int nsplit);
+
+/* Per-k-panel verification (FT-BLAS style; FT-GEMM blocks K by K_C, §2.1):
+ * kslabs > 0 makes later ftgemm_d calls also verify every tile's
+ * accumulators after every kslabs k-slabs (kslabs * 16 products) against the
+ * predicted checksums of the products done so far, correcting a located
+ * accumulator in place, so that faults arriving at different times stay
+ * separable and are caught before they spread through the remaining sum.
+ * The end-of-tile verification still runs.  0 (default) turns it off.  Such
+ * calls never split K. */
+int ftgemm_set_panel_check(int kslabs);
 
 /* Number of kernels this library has launched in this process. */
 int64_t ftgemm_launch_count(void);

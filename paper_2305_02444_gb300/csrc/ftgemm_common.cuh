@@ -32,7 +32,7 @@ constexpr int MAX_INTERSECT = 64;  // flagged row x column intersections per til
 // Device copy of the fault report (zeroed by the host before each call).
 struct DevReport {
   unsigned long long detected, corrected, checksum_only, unverifiable;
-  unsigned long long flagged_rows, flagged_cols, recomputed, n_loc;
+  unsigned long long flagged_rows, flagged_cols, recomputed, n_loc, panel_detected;
   int err;  // FTGEMM_ERR_TIMEOUT when a bounded wait expired
   int pad;
 };
@@ -76,9 +76,44 @@ struct Params {
   const double *P1, *P2;         // nI x N (ld ldp1) and M x nJ (ld ldp2), column-major
   long long ldp1, ldp2;
   const double *ccs, *ccsa, *crs, *crsa;  // [I][N] column sums, [J][M] row sums of C (and |C|)
+  int panel_slabs;               // PANEL kernels: verify the accumulators every panel_slabs k-slabs
   double *Cout;                  // where the verified tile lives (p.C is the copy of C_in)
   long long ldcout;
 };
+
+// ---------------------------------------------------------------- split precision
+constexpr int SP_BM = 128, SP_BN = 128, SP_BK = 64;  // bf16 k-slab of 128 bytes per row
+constexpr int SP_STAGES = 4;
+constexpr int SP_A_BYTES = SP_BM * SP_BK * 2, SP_B_BYTES = SP_BN * SP_BK * 2;  // 16 KiB each
+constexpr int SP_STAGE_BYTES = SP_A_BYTES + SP_B_BYTES;
+constexpr int SP_MAX_PAIRS = 128;
+constexpr int SP_SMEM_BYTES = SP_STAGES * SP_STAGE_BYTES + 4 * SP_BK * 4 + 4 * 128 * 8 + 2 * 128 * 4 + 256 +
+                              2 * SP_STAGES * 8 + 1024;
+
+struct SplitParams {
+  long long M, N, K, Kp;        // Kp: K rounded up to SP_BK (slices are zero padded)
+  double alpha, beta;
+  int S, w, npairs, kchunk;     // slices, bits per slice, kept pairs, products per exact FP32 chunk
+  int pair_s[SP_MAX_PAIRS], pair_t[SP_MAX_PAIRS];
+  const int *eA, *eB;           // row exponents of op(A), column exponents of op(B)
+  const double *A, *B;          // original operands (recomputation)
+  long long lda, ldb;
+  bool ta, tb;
+  double *C;
+  long long ldc;
+  int nI, nJ;
+  DevReport *rep;
+  DevLoc *loc;
+  long long loc_cap;
+  unsigned long long wait_limit_ns;
+  int verify;                   // 1: fault tolerant
+  // injection: flips of the FP64 accumulator of (row, col) after pair `kstep` is folded in
+  const DevFlip *flips_unused;
+  DevFlip *flips;
+  const int *tile_off;
+  int inj;
+};
+
 
 // One problem of a batch: its TMA descriptors (global memory, 64-byte aligned)
 // and its parameters (rep/loc/flips point at the problem's own slices).

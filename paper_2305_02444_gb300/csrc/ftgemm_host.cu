@@ -32,6 +32,18 @@ cudaError_t launch_batched_tn(bool, bool, const BatchProblem *, const int *, con
                               int *, int *, int, cudaStream_t);
 cudaError_t launch_batched_tt(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
                               int *, int *, int, cudaStream_t);
+cudaError_t launch_panel_nn(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
+                            cudaStream_t);
+cudaError_t launch_panel_nt(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
+                            cudaStream_t);
+cudaError_t launch_panel_tn(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
+                            cudaStream_t);
+cudaError_t launch_panel_tt(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
+                            cudaStream_t);
+cudaError_t launch_split(bool ta, bool tb, bool ft, const CUtensorMap &a, const CUtensorMap &b,
+                         const SplitParams &p, cudaStream_t s);
+cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
+                           int S, int w, int plain, void *out, cudaStream_t s);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
 cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
                            const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
@@ -66,6 +78,7 @@ struct Workspace {
   Buf hA, hB, hC;           // device copies for ftgemm_d_host
   Buf W, wpc, wpr;          // split-K partial tiles and predicted-checksum partials
   Buf uC, uccs, uccsa, ucrs, ucrsa, uP1, uP2;  // unfused ablation: copy of C, C sums, skinny GEMMs
+  Buf spA, spB, spEA, spEB;  // split precision: bf16 slices and row/column exponents
   int nsm = 0;              // SM count
   Buf pin;                  // pinned host staging (report, loc, injection upload)
   // the last injected call, for ftgemm_injection_log
@@ -200,6 +213,7 @@ bool tma_ok(const void *p, long long ld) {
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
+int g_panel = 0;   // verify the accumulators every g_panel k-slabs (0: only at the end of the tile)
 
 // Number of k-splits for a grid of `ntiles` tiles and `nks` k-slabs on `nsm`
 // SMs.  One CTA per SM: a grid of few tiles leaves SMs idle (64 tiles of a
@@ -311,6 +325,7 @@ void zero_report(ftgemm_report *rep) {
   if (!rep) return;
   rep->detected = rep->corrected = rep->checksum_only = rep->unverifiable = 0;
   rep->flagged_rows = rep->flagged_cols = rep->recomputed = rep->n_loc = 0;
+  rep->panel_detected = 0;
 }
 
 // Build and upload the injection table for this call (FT path only).
@@ -387,6 +402,7 @@ int copy_report(Workspace &w, ftgemm_report *rep, cudaStream_t s) {
   rep->flagged_rows = (long long)hr->flagged_rows;
   rep->flagged_cols = (long long)hr->flagged_cols;
   rep->recomputed = (long long)hr->recomputed;
+  rep->panel_detected = (long long)hr->panel_detected;
   rep->n_loc = (long long)hr->n_loc;
   if (rep->loc)
     for (long long q = 0; q < std::min<long long>(ncopy, rep->n_loc); ++q) {
@@ -503,7 +519,9 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
       w.nsm = 152;
     }
   }
-  const int S = choose_splits(ntiles, nks, w.nsm);
+  const bool panel = ft && g_panel > 0 && nks > g_panel;
+  const int S = panel ? 1 : choose_splits(ntiles, nks, w.nsm);
+  p.panel_slabs = panel ? g_panel : 0;
   cudaError_t e;
   auto launch = [&](int mode, const CUtensorMap &mW) {
     if (!ta_t && !tb_t) return launch_gemm_nn(ft, inj, mode, mA, mB, mC, mW, p, s);
@@ -511,7 +529,13 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     if (ta_t && !tb_t) return launch_gemm_tn(ft, inj, mode, mA, mB, mC, mW, p, s);
     return launch_gemm_tt(ft, inj, mode, mA, mB, mC, mW, p, s);
   };
-  if (S <= 1) {
+  if (panel) {
+    if (!ta_t && !tb_t) e = launch_panel_nn(inj, mA, mB, mC, p, s);
+    else if (!ta_t && tb_t) e = launch_panel_nt(inj, mA, mB, mC, p, s);
+    else if (ta_t && !tb_t) e = launch_panel_tn(inj, mA, mB, mC, p, s);
+    else e = launch_panel_tt(inj, mA, mB, mC, p, s);
+    g_launches++;
+  } else if (S <= 1) {
     e = launch(0, mC);
     g_launches++;
   } else {
@@ -766,6 +790,13 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream) {
 
 int64_t ftgemm_launch_count(void) { return g_launches.load(); }
 
+int ftgemm_set_panel_check(int kslabs) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (kslabs < 0) return -1;
+  g_panel = kslabs;
+  return 0;
+}
+
 int ftgemm_set_splitk(int nsplit) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (nsplit < 0 || nsplit > 64) return -1;
@@ -831,7 +862,8 @@ int ftgemm_finalize(void) {
   cudaDeviceSynchronize();
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
-                  &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2};
+                  &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
+                  &w.spA, &w.spB, &w.spEA, &w.spEB};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -1017,6 +1049,7 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
     rep->flagged_rows = (long long)hr.flagged_rows;
     rep->flagged_cols = (long long)hr.flagged_cols;
     rep->recomputed = (long long)hr.recomputed;
+    rep->panel_detected = (long long)hr.panel_detected;
     rep->n_loc = (long long)hr.n_loc;
     const long long nrec = std::min<long long>(ncopy, rep->n_loc);
     for (long long q0 = 0; rep->loc && q0 < nrec; q0 += 64) {
@@ -1397,6 +1430,7 @@ int ftgemm_batched_plan_report(ftgemm_batched_plan plan, ftgemm_report *reps, vo
     r.flagged_rows = (long long)hr[q].flagged_rows;
     r.flagged_cols = (long long)hr[q].flagged_cols;
     r.recomputed = (long long)hr[q].recomputed;
+    r.panel_detected = (long long)hr[q].panel_detected;
     r.n_loc = (long long)hr[q].n_loc;
     if (r.loc)
       for (long long k = 0; k < std::min<long long>({r.cap, (long long)PLAN_LOC_CAP, r.n_loc}); ++k) {
@@ -1449,3 +1483,104 @@ int ftgemm_batched(int64_t count, const char *transA, const char *transB, const 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Split-precision FT-GEMM (BF16 tensor cores; see ftgemm_split.cuh).
+namespace {
+
+int make_map_slices(CUtensorMap *m, const void *ptr, long long Kp, long long R, long long S) {
+  auto fn = encode_fn();
+  if (!fn) return FTGEMM_ERR_TENSORMAP;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)SP_BK, (cuuint32_t)SP_BM, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : FTGEMM_ERR_TENSORMAP;
+}
+
+}  // namespace
+
+extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
+                              const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                              int64_t ldc, int nslices, int ft, ftgemm_report *rep, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
+  if (rc) return rc;
+  if (nslices < 0 || nslices > 15) return -14;
+  zero_report(rep);
+  if (M == 0 || N == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (K == 0 || alpha == 0.0)
+    return gemm_impl(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rep, s, true);
+  int dev = 0;
+  Workspace *wp = workspace(&dev);
+  if (!wp) return FTGEMM_ERR_NODEVICE;
+  Workspace &w = *wp;
+  const bool ta_t = is_t(transA), tb_t = is_t(transB);
+  const bool plain = nslices == 0;
+  const int S = plain ? 1 : nslices;
+  const long long Kp = (K + SP_BK - 1) / SP_BK * SP_BK;
+  // bits per slice: the FP32 accumulation of a pair stays exact over kchunk products
+  int wbits = 0;
+  long long kchunk = Kp;
+  if (!plain) {
+    wbits = K <= 256 ? 8 : K <= 1024 ? 7 : K <= 4096 ? 6 : 5;
+    const long long lim = (1LL << 24) / (((1LL << wbits) - 1) * ((1LL << wbits) - 1));
+    kchunk = std::max<long long>(SP_BK, lim / SP_BK * SP_BK);
+  }
+  const long long nI = (M + SP_BM - 1) / SP_BM, nJ = (N + SP_BN - 1) / SP_BN;
+  if (ensure(w.spA, (size_t)S * M * Kp * 2) || ensure(w.spB, (size_t)S * N * Kp * 2) ||
+      ensure(w.spEA, sizeof(int) * M) || ensure(w.spEB, sizeof(int) * N))
+    return FTGEMM_ERR_NOMEM;
+  if (plain) {
+    cudaMemsetAsync(w.spEA.p, 0, sizeof(int) * M, s);
+    cudaMemsetAsync(w.spEB.p, 0, sizeof(int) * N, s);
+  }
+  // op(A)(i, k): 'T' has k contiguous; op(B)(k, j) seen as row j: 'N' has k contiguous
+  if (launch_slicing(A, lda, ta_t ? 1 : 0, M, K, Kp, (int *)w.spEA.p, S, wbits, plain, w.spA.p, s) != cudaSuccess ||
+      launch_slicing(B, ldb, tb_t ? 0 : 1, N, K, Kp, (int *)w.spEB.p, S, wbits, plain, w.spB.p, s) != cudaSuccess)
+    return FTGEMM_ERR_CUDA;
+  g_launches += plain ? 2 : 4;
+  CUtensorMap mA, mB;
+  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S))) return rc;
+
+  SplitParams p;
+  memset(&p, 0, sizeof(p));
+  p.M = M; p.N = N; p.K = K; p.Kp = Kp; p.alpha = alpha; p.beta = beta;
+  p.S = plain ? 0 : S; p.w = wbits; p.kchunk = (int)kchunk;
+  // kept pairs s + t < S, smallest weights (largest s + t) first
+  int np = 0;
+  for (int d = S - 1; d >= 0; --d)
+    for (int a = 0; a <= d; ++a) { p.pair_s[np] = a; p.pair_t[np] = d - a; ++np; }
+  p.npairs = np;
+  p.eA = (const int *)w.spEA.p; p.eB = (const int *)w.spEB.p;
+  p.A = A; p.B = B; p.lda = lda; p.ldb = ldb; p.ta = ta_t; p.tb = tb_t;
+  p.C = C; p.ldc = ldc; p.nI = (int)nI; p.nJ = (int)nJ;
+  p.rep = (DevReport *)w.rep.p; p.loc = (DevLoc *)w.loc.p; p.loc_cap = LOC_CAP_DEV;
+  p.wait_limit_ns = wait_limit_ns();
+  p.verify = ft;
+  cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
+  bool inj = false;
+  if (ft) {
+    Params tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    if ((rc = upload_injection(M, N, np, nI, nI * nJ, w, s, tmp, &inj))) return rc;
+    p.flips = tmp.flips; p.tile_off = tmp.tile_off; p.inj = inj ? 1 : 0;
+  }
+  cudaEvent_t em0 = nullptr, em1 = nullptr;
+  if (g_tim.on) {
+    timing_record(g_tim.main_ev, &em0, &em1);
+    cudaEventRecord(em0, s);
+  }
+  if (launch_split(ta_t, tb_t, ft != 0, mA, mB, p, s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  if (g_tim.on) cudaEventRecord(em1, s);
+  g_launches++;
+  if (rep) {
+    if (inj) cudaStreamSynchronize(s);
+    return copy_report(w, rep, s);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+}

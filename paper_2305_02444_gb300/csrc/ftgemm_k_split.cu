@@ -1,0 +1,44 @@
+// Split-precision kernel instantiations (all operand layouts, with and without
+// the fault tolerance) and the slicing kernels' launchers.
+#include <cuda_bf16.h>
+
+#include "ftgemm_split.cuh"
+
+namespace ftg {
+
+template <bool TA, bool TB, bool FT>
+static cudaError_t launch_split_variant(const CUtensorMap &a, const CUtensorMap &b, const SplitParams &p,
+                                        cudaStream_t s) {
+  auto k = ftsplit_kernel<TA, TB, FT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)p.nI * (unsigned)p.nJ, 256, SP_SMEM_BYTES, s>>>(a, b, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(bool ta, bool tb, bool ft, const CUtensorMap &a, const CUtensorMap &b,
+                         const SplitParams &p, cudaStream_t s) {
+  if (ft) {
+    if (!ta && !tb) return launch_split_variant<false, false, true>(a, b, p, s);
+    if (!ta && tb) return launch_split_variant<false, true, true>(a, b, p, s);
+    if (ta && !tb) return launch_split_variant<true, false, true>(a, b, p, s);
+    return launch_split_variant<true, true, true>(a, b, p, s);
+  }
+  if (!ta && !tb) return launch_split_variant<false, false, false>(a, b, p, s);
+  if (!ta && tb) return launch_split_variant<false, true, false>(a, b, p, s);
+  if (ta && !tb) return launch_split_variant<true, false, false>(a, b, p, s);
+  return launch_split_variant<true, true, false>(a, b, p, s);
+}
+
+cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
+                           int S, int w, int plain, void *out, cudaStream_t s) {
+  if (!plain) {
+    if (trans) split_rowexp_kernel<<<(unsigned)((R + 7) / 8), 256, 0, s>>>(X, ld, trans, R, K, e);
+    else split_rowexp_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(X, ld, trans, R, K, e);
+  }
+  dim3 grid((unsigned)((Kp + 63) / 64), (unsigned)((R + 63) / 64));
+  split_slice_kernel<<<grid, 256, 0, s>>>(X, ld, trans, R, K, Kp, e, S, w, plain, (__nv_bfloat16 *)out);
+  return cudaGetLastError();
+}
+
+}  // namespace ftg

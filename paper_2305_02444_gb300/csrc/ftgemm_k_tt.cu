@@ -61,4 +61,14 @@ cudaError_t launch_batched_tt(bool ft, bool inj, const BatchProblem *probs, cons
                                                   gerr, grid, s);
 }
 
+// fault-tolerant whole-tile kernel with the per-k-panel verification
+cudaError_t launch_panel_tt(bool inj, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &c,
+                             const Params &p, cudaStream_t s) {
+  auto k = inj ? ftdgemm_kernel<true, true, true, true, 0, true> : ftdgemm_kernel<true, true, true, false, 0, true>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)p.nI * (unsigned)p.nJ, NTHREADS, SMEM_BYTES, s>>>(a, b, c, c, p);
+  return cudaGetLastError();
+}
+
 }  // namespace ftg

@@ -56,7 +56,7 @@ __device__ __forceinline__ double glob_b(const Params &p, long long k, long long
 }
 
 // counters in shared memory
-enum { C_NR = 0, C_NC, C_DET, C_CSONLY, C_UNVER, C_RECOMP, C_ABORT, C_FAIL, C_NCNT };
+enum { C_NR = 0, C_NC, C_DET, C_CSONLY, C_UNVER, C_RECOMP, C_ABORT, C_FAIL, C_PNR, C_PNC, C_PDET, C_NCNT };
 
 // Recompute element (il, jl) of the tile from the original operands with one
 // warp (lanes split k), compare with the staged value and rewrite it.
@@ -102,7 +102,7 @@ __device__ __forceinline__ void recompute_elem(const Params &p, double *sC, int 
 //         epilogue as MODE 0 (beta*C encode, verify, locate, correct, store).
 // MODE 3: verify-only pass of the unfused ablation: the tile of a finished
 //         GEMM, predicted checksums and C sums computed by separate passes.
-template <bool TA, bool TB, bool FT, bool INJ, int MODE>
+template <bool TA, bool TB, bool FT, bool INJ, int MODE, bool PANEL = false>
 __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const CUtensorMap *tmC,
                                          const CUtensorMap *tmW, const Params &p, const int tile, const int split,
                                          unsigned char *smem) {
@@ -187,10 +187,14 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     while (fptr < fend && p.flips[fptr].kstep < s_begin) ++fptr;  // earlier k-splits' faults
   }
 
+  // A thread whose bounded wait expired stops waiting and computing but keeps
+  // iterating, so that every thread reaches the same CTA-wide barriers of the
+  // panel checks; the abort is acted on after the loop.
   bool ok = true;
   for (int s = 0; s < nks; ++s) {
     const int st = s % STAGES;
-    if (!mbar_wait_bounded(full0 + 8 * st, (s / STAGES) & 1, limit, err)) { ok = false; break; }
+    if (ok && !mbar_wait_bounded(full0 + 8 * st, (s / STAGES) & 1, limit, err)) ok = false;
+    if (ok) {
     const unsigned char *sA = smem + st * STAGE_BYTES;
     const unsigned char *sB = sA + A_BYTES;
 #pragma unroll
@@ -238,13 +242,124 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
         ++fptr;
       }
     }
+    }  // ok
     __syncwarp();
-    if (lane == 0) mbar_arrive(empty0 + 8 * st);
-    if (tid == 0 && s >= 1 && issued < nks) {
+    if (lane == 0 && ok) mbar_arrive(empty0 + 8 * st);
+    if (tid == 0 && ok && s >= 1 && issued < nks) {
       // refill the stage of slab s-1 once every warp has released it
       const int sp = s - 1;
-      if (!mbar_wait_bounded(empty0 + 8 * (sp % STAGES), (sp / STAGES) & 1, limit, err)) { ok = false; break; }
-      issue(issued++);
+      if (!mbar_wait_bounded(empty0 + 8 * (sp % STAGES), (sp / STAGES) & 1, limit, err)) ok = false;
+      else issue(issued++);
+    }
+    if (PANEL && p.panel_slabs > 0 && (s + 1) % p.panel_slabs == 0 && s + 1 < nks &&
+        __syncthreads_or(!ok) == 0) {
+      // ---- verification of the accumulators after this k-panel -------------
+      const long long kbeg = (long long)s_begin * BK;
+      const long long kdone = min(p.K, (long long)(s_begin + s + 1) * BK);
+      double rsum[8], csum[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        rsum[a] = 0.0;
+        csum[a] = 0.0;
+      }
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          rsum[a] += acc[a][b];
+          csum[b] += acc[a][b];
+        }
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        rsum[a] += __shfl_xor_sync(0xffffffffu, rsum[a], 16);  // lanes l, l^16: same rows
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) csum[a] += __shfl_xor_sync(0xffffffffu, csum[a], o);  // same columns
+      }
+      double *s_rpart = epi, *s_csum = epi + 1024, *s_rsum = epi + 1152, *s_val = epi;
+      if (lane < 16) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) s_rpart[warp * 128 + tx + 16 * a] = rsum[a];
+      }
+      if (tx == 0) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) s_csum[ty + 16 * b] = csum[b];
+      }
+      compute_sync();
+      if (tid < 128) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += s_rpart[w * 128 + tid];
+        s_rsum[tid] = t;
+      }
+      compute_sync();
+      {
+        const double u = 0x1p-53;
+        if (tid < 128) {
+          const int j = tid;
+          if (j < nJt) {
+            const double n = (double)(kdone - kbeg + mI + 3);
+            const double tau = 2.01 * n * u * (p.bcolabs[j0 + j] * p.aabsmax[I]) + n * 0x1p-1021;
+            if (isfinite(csacc) && isfinite(tau) && !(fabs(s_csum[j] - csacc) <= tau))
+              s_fc[atomicAdd(&cnt[C_PNC], 1)] = j;
+          }
+        } else {
+          const int i = tid - 128;
+          if (i < mI) {
+            const double n = (double)(kdone - kbeg + nJt + 3);
+            const double tau = 2.01 * n * u * (p.arowabs[i0 + i] * p.babsmax[J]) + n * 0x1p-1021;
+            if (isfinite(csacc) && isfinite(tau) && !(fabs(s_rsum[i] - csacc) <= tau))
+              s_fr[atomicAdd(&cnt[C_PNR], 1)] = i;
+          }
+        }
+      }
+      compute_sync();
+      const int pnr = cnt[C_PNR], pnc = cnt[C_PNC];
+      if (pnr > 0 && pnc > 0 && pnr * pnc <= MAX_INTERSECT) {
+        // recompute each flagged intersection over the products done so far
+        for (int e = warp; e < pnr * pnc; e += NCOMPUTE / 32) {
+          const long long gi = i0 + s_fr[e / pnc], gj = j0 + s_fc[e % pnc];
+          double dot = 0.0, ab = 0.0;
+          for (long long k = kbeg + lane; k < kdone; k += 32) {
+            const double av = glob_a<TA, TB>(p, gi, k), bv = glob_b<TA, TB>(p, k, gj);
+            dot = fma(av, bv, dot);
+            ab = fma(fabs(av), fabs(bv), ab);
+          }
+          dot = warp_sum(dot);
+          ab = warp_sum(ab);
+          if (lane == 0) { s_val[2 * e] = dot; s_val[2 * e + 1] = ab; }
+        }
+        compute_sync();
+        // the owning thread replaces its accumulator
+        for (int e = 0; e < pnr * pnc; ++e) {
+          const int il = s_fr[e / pnc], jl = s_fc[e % pnc];
+          if ((il & 15) == tx && (jl & 15) == ty) {
+            const int pq = (il >> 4) * 8 + (jl >> 4);
+            const double nv = s_val[2 * e];
+            const double n = (double)(kdone - kbeg + 3);
+            const double te = 2.01 * n * 0x1p-53 * s_val[2 * e + 1] + n * 0x1p-1021;
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+              for (int b = 0; b < 8; ++b)
+                if (a * 8 + b == pq) {
+                  const double old = acc[a][b];
+                  if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
+                    atomicAdd(&cnt[C_PDET], 1);
+                    const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
+                    if ((long long)q < p.loc_cap) {
+                      DevLoc L;
+                      L.row = i0 + il; L.col = j0 + jl; L.tile = tile; L.kind = 2; L.delta = old - nv;
+                      p.loc[q] = L;
+                    }
+                  }
+                  acc[a][b] = nv;
+                }
+          }
+        }
+      }
+      compute_sync();
+      if (tid == 0) { cnt[C_PNR] = 0; cnt[C_PNC] = 0; }
+      compute_sync();
     }
   }
   if (!ok) {
@@ -513,13 +628,18 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
       if (cnt[C_CSONLY]) atomicAdd(&r->checksum_only, (unsigned long long)cnt[C_CSONLY]);
       if (cnt[C_UNVER]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[C_UNVER]);
       if (cnt[C_RECOMP]) atomicAdd(&r->recomputed, (unsigned long long)cnt[C_RECOMP]);
+      if (PANEL && cnt[C_PDET]) {
+        atomicAdd(&r->detected, (unsigned long long)cnt[C_PDET]);
+        atomicAdd(&r->corrected, (unsigned long long)cnt[C_PDET]);
+        atomicAdd(&r->panel_detected, (unsigned long long)cnt[C_PDET]);
+      }
     }
     if (tma_store) bulk_wait_all();
   }
 }
 
 // One CTA per tile (MODE 0, 2, 3) or per tile and k-split (MODE 1).
-template <bool TA, bool TB, bool FT, bool INJ, int MODE>
+template <bool TA, bool TB, bool FT, bool INJ, int MODE, bool PANEL = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ftdgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmW,
@@ -530,7 +650,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int ntiles = p.nI * p.nJ;
   const int tile = (MODE == 1) ? (int)(blockIdx.x % ntiles) : (int)blockIdx.x;
   const int split = (MODE == 1) ? (int)(blockIdx.x / ntiles) : 0;
-  ftd_tile<TA, TB, FT, INJ, MODE>(&tmA, &tmB, &tmC, &tmW, p, tile, split, smem);
+  ftd_tile<TA, TB, FT, INJ, MODE, PANEL>(&tmA, &tmB, &tmC, &tmW, p, tile, split, smem);
 }
 
 // Persistent batched kernel: one CTA per SM takes `chunk` work items at a time

@@ -1,0 +1,461 @@
+// Split-precision FT-GEMM on the BF16 tensor cores (mma.sync m16n8k16, FP32
+// accumulation), for C = alpha * op(A) * op(B) + beta * C with FP64 inputs
+// and output.
+//
+// Two forms share one kernel:
+//  - emulated FP64 (Ozaki, Ogita, Oishi and Rump's error-free splitting): each
+//    row of op(A) is scaled by a power of two sigma_i so that |x| < 1, and
+//    split into S integer slices of w bits, x = sum_s n_s 2^{-w(s+1)} + r,
+//    |n_s| < 2^w (exact in bf16 for w <= 8); op(B)'s columns likewise.  Every
+//    kept slice pair (s, t), s + t < S, is one integer product whose FP32
+//    accumulation is exact while K_chunk * (2^w - 1)^2 < 2^24; the pair's
+//    FP32 tile is folded into FP64 accumulators with the pair's power-of-two
+//    weight 2^{-w(s+t+2)}; out = alpha * sigma_i tau_j acc64 + beta * C.
+//  - plain BF16: op(A), op(B) rounded to bf16, one pair, FP32 accumulation
+//    over the whole K (the usual BF16-in / FP32-accumulate GEMM).
+//
+// Fault tolerance: the predicted checksums are carried in FP32 (each slab's
+// column sums of the A slice and row sums of the B slice are taken on the CUDA
+// cores from the staged tiles, then multiplied into the other operand's slab),
+// folded into FP64 with the same weights; the reference sums of the FP64
+// accumulators, the verification and the correction (an FP64 dot product of
+// the original FP64 operands) stay in FP64.  The threshold is the FP32
+// rounding bound of the predicted checksums (accumulated alongside as an
+// absolute-value checksum) plus the FP64 folding bound.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "ftgemm_common.cuh"
+
+namespace ftg {
+
+// ---------------------------------------------------------------- slicing
+
+// Row exponent: e with max_k |x(r, k)| < 2^e (0 for an all-zero row).
+// X is op(X) given by (ptr, ld, trans): element (r, k) = trans ? X[k + r*ld] : X[r + k*ld].
+__global__ void split_rowexp_kernel(const double *__restrict__ X, long long ld, int trans, long long R,
+                                    long long K, int *__restrict__ e) {
+  // one warp per row for trans (k contiguous); one thread per row otherwise (r contiguous)
+  if (trans) {
+    const long long r = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    double m = 0.0;
+    for (long long k = lane; k < K; k += 32) m = fmax(m, fabs(X[k + r * ld]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+  } else {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double m = 0.0;
+    for (long long k = 0; k < K; ++k) m = fmax(m, fabs(X[r + k * ld]));
+    e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+  }
+}
+
+// Slices: out[s][r][k] (bf16, row length Kp, zero padded), 64 x 64 tiles through
+// shared memory so that both the read and the write are coalesced.
+__global__ void __launch_bounds__(256) split_slice_kernel(const double *__restrict__ X, long long ld, int trans,
+                                                          long long R, long long K, long long Kp,
+                                                          const int *__restrict__ e, int S, int w, int plain,
+                                                          __nv_bfloat16 *__restrict__ out) {
+  __shared__ double t[64][65];
+  const long long r0 = (long long)blockIdx.y * 64, k0 = (long long)blockIdx.x * 64;
+  for (int q = threadIdx.x; q < 64 * 64; q += 256) {
+    int rr, kk;
+    if (trans) { kk = q & 63; rr = q >> 6; } else { rr = q & 63; kk = q >> 6; }
+    const long long r = r0 + rr, k = k0 + kk;
+    double v = 0.0;
+    if (r < R && k < K) v = trans ? X[k + r * ld] : X[r + k * ld];
+    t[rr][kk] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64 * 64; q += 256) {
+    const int kk = q & 63, rr = q >> 6;
+    const long long r = r0 + rr, k = k0 + kk;
+    if (r >= R || k >= Kp) continue;
+    double x = t[rr][kk];
+    if (plain) {
+      out[r * Kp + k] = __double2bfloat16(x);
+      continue;
+    }
+    x = ldexp(x, -e[r]);  // |x| < 1, exact
+    for (int s = 0; s < S; ++s) {
+      const double v = ldexp(x, w);
+      const double n = trunc(v);
+      out[((long long)s * R + r) * Kp + k] = __double2bfloat16(n);  // |n| < 2^w <= 256: exact
+      x = v - n;                                                      // exact
+    }
+  }
+}
+
+// ---------------------------------------------------------------- GEMM kernel
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// bf16 element (row, k) of a [128][64] slab written by TMA with 128-byte swizzle.
+__device__ __forceinline__ float slab_at(const unsigned char *slab, int row, int k) {
+  const __nv_bfloat16 *p = reinterpret_cast<const __nv_bfloat16 *>(
+      slab + row * 128 + ((((k >> 3) ^ (row & 7)) << 4) | ((k & 7) << 1)));
+  return __bfloat162float(*p);
+}
+
+template <bool TA, bool TB>
+__device__ __forceinline__ double sp_glob_a(const SplitParams &p, long long i, long long k) {
+  return TA ? p.A[k + i * p.lda] : p.A[i + k * p.lda];
+}
+template <bool TA, bool TB>
+__device__ __forceinline__ double sp_glob_b(const SplitParams &p, long long k, long long j) {
+  return TB ? p.B[j + k * p.ldb] : p.B[k + j * p.ldb];
+}
+
+// One CTA per 128 x 128 tile; 8 warps as 2 (rows) x 4 (columns), warp tile
+// 64 x 32 = 4 x 4 mma tiles.  tmA / tmB: 3-D maps {Kp, R, S} of the slices.
+template <bool TA, bool TB, bool FT>
+__global__ void __launch_bounds__(256, 1)
+    ftsplit_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ SplitParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float *s_csA = reinterpret_cast<float *>(smem + SP_STAGES * SP_STAGE_BYTES);  // [2][64]: sum and abs sum
+  float *s_csB = s_csA + 2 * SP_BK;
+  double *s_r = reinterpret_cast<double *>(s_csB + 2 * SP_BK);  // [4][128]: reference/predicted scratch
+  int *s_fr = reinterpret_cast<int *>(s_r + 4 * 128);
+  int *s_fc = s_fr + 128;
+  int *cnt = s_fc + 128;  // [0] nr [1] nc [2] det [3] abort [4] unverifiable
+  uint64_t *bars = reinterpret_cast<uint64_t *>(cnt + 64);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + SP_STAGES);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x, I = tile % p.nI, J = tile / p.nI;
+  const int i0 = I * SP_BM, j0 = J * SP_BN;
+  const int mI = (int)min((long long)SP_BM, p.M - i0), nJt = (int)min((long long)SP_BN, p.N - j0);
+  const int wm = warp >> 2, wn = warp & 3;  // warp tile rows wm*64.., cols wn*32..
+  const int g = lane >> 2, t4 = lane & 3;
+  int *err = &p.rep->err;
+  const unsigned long long limit = p.wait_limit_ns;
+
+  if (tid == 0) {
+    for (int c = 0; c < 8; ++c) cnt[c] = 0;
+    for (int s = 0; s < SP_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 8);
+    }
+    fence_mbar_init();
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+  }
+  __syncthreads();
+
+  // work list: (pair q, k-chunk c, slab b) in the order pairs x chunks x slabs
+  const int nslab_total = (int)(p.Kp / SP_BK);
+  const int chunk_slabs = max(1, p.kchunk / SP_BK);
+  const int nchunks = (nslab_total + chunk_slabs - 1) / chunk_slabs;
+  const int nsteps = p.npairs * nslab_total;  // every pair sweeps all slabs once
+  auto step_coords = [&](int step, int &pq, int &slab) {
+    pq = step / nslab_total;
+    slab = step % nslab_total;
+  };
+  auto issue = [&](int step) {
+    int pq, slab;
+    step_coords(step, pq, slab);
+    const int st = step % SP_STAGES;
+    const uint32_t sb = smem_u32(smem + st * SP_STAGE_BYTES);
+    const uint32_t fb = full0 + 8 * st;
+    mbar_arrive_expect_tx(fb, SP_STAGE_BYTES);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb),
+        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(fb), "r"(slab * SP_BK), "r"(i0), "r"(p.pair_s[pq])
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb + SP_A_BYTES),
+        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(fb), "r"(slab * SP_BK), "r"(j0), "r"(p.pair_t[pq])
+        : "memory");
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < SP_STAGES && issued < nsteps; ++issued) issue(issued);
+
+  float acc32[4][4][4];
+  double acc64[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) { acc32[a][b][c] = 0.f; acc64[a][b][c] = 0.0; }
+  float cs32 = 0.f, ca32 = 0.f;     // FT: this pair-chunk's predicted checksum (t < 128: column, else row)
+  double cs64 = 0.0, ca64 = 0.0;    // folded predicted checksum and its absolute bound
+  int fptr = 0, fend = 0;
+  if (FT && p.inj) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+
+  bool ok = true;
+  for (int step = 0; step < nsteps; ++step) {
+    int pq, slab;
+    step_coords(step, pq, slab);
+    const int st = step % SP_STAGES;
+    if (ok && !mbar_wait_bounded(full0 + 8 * st, (step / SP_STAGES) & 1, limit, err)) ok = false;
+    if (ok) {
+      const unsigned char *sA = smem + st * SP_STAGE_BYTES, *sB = sA + SP_A_BYTES;
+      const uint32_t aA = smem_u32(sA), aB = smem_u32(sB);
+#pragma unroll
+      for (int kk = 0; kk < SP_BK / 16; ++kk) {
+        uint32_t af[4][4], bf[4][2];
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+          const int r = wm * 64 + mt * 16 + (lane & 15), c = kk * 2 + (lane >> 4);
+          ldsm_x4(aA + r * 128 + ((c ^ (r & 7)) << 4), af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+        }
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          const int q = lane >> 3;
+          const int r = wn * 32 + np * 16 + (q >> 1) * 8 + (lane & 7), c = kk * 2 + (q & 1);
+          ldsm_x4(aB + r * 128 + ((c ^ (r & 7)) << 4), bf[2 * np][0], bf[2 * np][1], bf[2 * np + 1][0],
+                  bf[2 * np + 1][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+            mma_bf16(acc32[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bf[nt][0], bf[nt][1]);
+      }
+    }  // ok
+    if (FT) {
+      // slab checksums of the staged slices on the CUDA cores: column sums of
+      // the A slice over the tile's rows and row sums of the B slice over the
+      // tile's columns (signed and absolute, exact in FP32), then the predicted
+      // checksum FMAs.  The barriers run in every thread, stalled or not.
+      const unsigned char *sA = smem + st * SP_STAGE_BYTES, *sB = sA + SP_A_BYTES;
+      float *tmp = reinterpret_cast<float *>(s_r);  // [4 parts][4 kinds][64]
+      const int k = tid & 63, part = tid >> 6;
+      if (ok) {
+        float sa = 0.f, saa = 0.f, sb = 0.f, sba = 0.f;
+        for (int r = part * 32; r < part * 32 + 32; ++r) {
+          const float av = slab_at(sA, r, k), bv = slab_at(sB, r, k);
+          sa += av; saa += fabsf(av);
+          sb += bv; sba += fabsf(bv);
+        }
+        tmp[(part * 4 + 0) * 64 + k] = sa;
+        tmp[(part * 4 + 1) * 64 + k] = saa;
+        tmp[(part * 4 + 2) * 64 + k] = sb;
+        tmp[(part * 4 + 3) * 64 + k] = sba;
+      }
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (ok && tid < 4 * SP_BK) {
+        const int kind = tid >> 6;  // 0 A sum, 1 A abs, 2 B sum, 3 B abs
+        const float v = (tmp[(0 * 4 + kind) * 64 + k] + tmp[(1 * 4 + kind) * 64 + k]) +
+                        (tmp[(2 * 4 + kind) * 64 + k] + tmp[(3 * 4 + kind) * 64 + k]);
+        if (kind < 2) s_csA[kind * SP_BK + k] = v; else s_csB[(kind - 2) * SP_BK + k] = v;
+      }
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (ok) {
+        if (tid < 128) {
+#pragma unroll 8
+          for (int kk = 0; kk < SP_BK; ++kk) {
+            const float bv = slab_at(sB, tid, kk);
+            cs32 = fmaf(s_csA[kk], bv, cs32);
+            ca32 = fmaf(s_csA[SP_BK + kk], fabsf(bv), ca32);
+          }
+        } else {
+#pragma unroll 8
+          for (int kk = 0; kk < SP_BK; ++kk) {
+            const float av = slab_at(sA, tid - 128, kk);
+            cs32 = fmaf(av, s_csB[kk], cs32);
+            ca32 = fmaf(fabsf(av), s_csB[SP_BK + kk], ca32);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && ok) mbar_arrive(empty0 + 8 * st);
+    if (tid == 0 && ok && step >= 1 && issued < nsteps) {
+      const int sp = step - 1;
+      if (!mbar_wait_bounded(empty0 + 8 * (sp % SP_STAGES), (sp / SP_STAGES) & 1, limit, err)) ok = false;
+      else issue(issued++);
+    }
+    // end of a k-chunk (or of the pair): fold the exact FP32 tile into FP64
+    const bool chunk_end = ((slab + 1) % chunk_slabs == 0) || (slab + 1 == nslab_total);
+    if (chunk_end) {
+      const double wgt = ldexp(1.0, -p.w * (p.pair_s[pq] + p.pair_t[pq] + 2));
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            acc64[a][b][c] = fma(wgt, (double)acc32[a][b][c], acc64[a][b][c]);
+            acc32[a][b][c] = 0.f;
+          }
+      if (FT) {
+        cs64 = fma(wgt, (double)cs32, cs64);
+        ca64 = fma(wgt, (double)ca32, ca64);
+        cs32 = 0.f;
+        ca32 = 0.f;
+      }
+      if (FT && p.inj && slab + 1 == nslab_total) {
+        // injection point: after pair pq has been folded in (kstep = pair index)
+        while (fptr < fend) {
+          DevFlip *f = p.flips + fptr;
+          if (f->kstep != pq) break;
+          const int il = (int)(f->row - i0), jl = (int)(f->col - j0);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int ri = wm * 64 + a * 16 + g + ((c >> 1) << 3), cj = wn * 32 + b * 8 + 2 * t4 + (c & 1);
+                if (ri == il && cj == jl) {
+                  const double before = acc64[a][b][c];
+                  acc64[a][b][c] = flip_bit(before, f->bit);
+                  f->before = before;
+                  f->after = acc64[a][b][c];
+                  f->applied = 1;
+                  f->kfirst = 0;
+                }
+              }
+          ++fptr;
+        }
+      }
+    }
+  }
+  (void)nchunks;
+  if (!ok) {
+    atomicExch(&cnt[3], 1);
+    if (tid == 0)
+      for (int s = issued > SP_STAGES ? issued - SP_STAGES : 0; s < issued; ++s)
+        mbar_wait_bounded(full0 + 8 * (s % SP_STAGES), (s / SP_STAGES) & 1, limit, err);
+  }
+  __syncthreads();
+  if (cnt[3]) return;
+
+  // ------------------------------------------------------------- epilogue
+  // acc64 (unscaled: sum of the kept pairs) -> staged tile sC (column-major [128][128] doubles)
+  double *sC = reinterpret_cast<double *>(smem);  // 128 KiB: the ring is free
+  fence_proxy_async_smem();
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ri = wm * 64 + a * 16 + g + ((c >> 1) << 3), cj = wn * 32 + b * 8 + 2 * t4 + (c & 1);
+        sC[cj * SP_BM + ri] = acc64[a][b][c];
+      }
+  __syncthreads();
+  double *s_ref = s_r, *s_pred = s_r + 128, *s_tau = s_r + 256;
+  if (FT) {
+    // reference sums of the accumulators, one per thread: column (tid < 128) or row
+    double ref = 0.0;
+    if (tid < 128) {
+      for (int i = 0; i < SP_BM; ++i) ref += sC[tid * SP_BM + i];
+    } else {
+      for (int j = 0; j < SP_BN; ++j) ref += sC[j * SP_BM + tid - 128];
+    }
+    // the predicted checksum carries the FP32 rounding of up to kchunk products
+    // per pair-chunk; the accumulators carry one FP64 rounding per fold
+    const double u32 = 0x1p-24, u64 = 0x1p-53;
+    const double n32 = (double)(min((long long)p.kchunk, p.Kp) + 128 + 2);
+    const double nfold = (double)(p.npairs * ((p.Kp + p.kchunk - 1) / p.kchunk) + 128 + 2);
+    // (x2: the plain BF16 form's accumulators carry the same FP32 rounding)
+    const double tau = 4.02 * n32 * u32 * ca64 + 2.01 * nfold * u64 * ca64 + 0x1p-1000;
+    const int idx = tid & 127;
+    const bool valid = (tid < 128) ? (idx < nJt) : (idx < mI);
+    if (valid) {
+      if (!isfinite(cs64) || !isfinite(tau)) atomicAdd(&cnt[4], 1);
+      else if (!(fabs(ref - cs64) <= tau)) {
+        if (tid < 128) s_fc[atomicAdd(&cnt[1], 1)] = idx;
+        else s_fr[atomicAdd(&cnt[0], 1)] = idx;
+      }
+    }
+  }
+  __syncthreads();
+  // scale to the output: out = alpha * 2^(eA_i + eB_j) * acc + beta * C  (C read only if beta != 0)
+  const bool use_c = p.beta != 0.0;
+  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
+    const int il = e & 127, jl = e >> 7;
+    if (il < mI && jl < nJt) {
+      const long long gi = i0 + il, gj = j0 + jl;
+      const double v = ldexp(sC[e], p.eA[gi] + p.eB[gj]);
+      sC[e] = use_c ? fma(p.alpha, v, p.beta * p.C[gi + gj * p.ldc]) : p.alpha * v;
+    }
+  }
+  __syncthreads();
+  if (FT) {
+    const int nr = cnt[0], nc = cnt[1];
+    // flagged intersections (or whole flagged segments when one side is empty
+    // or there are more than 64): recompute in FP64 from the original operands
+    const int ncand = (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) ? nr * nc
+                      : (nr + nc > 0) ? (nr * nJt + nc * mI) : 0;
+    for (int e = warp; e < ncand; e += 8) {
+      int il, jl;
+      if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) { il = s_fr[e / nc]; jl = s_fc[e % nc]; }
+      else if (e < nr * nJt) { il = s_fr[e / nJt]; jl = e % nJt; }
+      else { il = (e - nr * nJt) % mI; jl = s_fc[(e - nr * nJt) / mI]; }
+      const long long gi = i0 + il, gj = j0 + jl;
+      double dot = 0.0, ab = 0.0;
+      for (long long k = lane; k < p.K; k += 32) {
+        const double av = sp_glob_a<TA, TB>(p, gi, k), bv = sp_glob_b<TA, TB>(p, k, gj);
+        dot = fma(av, bv, dot);
+        ab = fma(fabs(av), fabs(bv), ab);
+      }
+      dot = warp_sum(dot);
+      ab = warp_sum(ab);
+      if (lane == 0) {
+        const double c = use_c ? p.C[gi + gj * p.ldc] : 0.0;
+        const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
+        // the emulated value may differ from the FP64 one by the splitting error
+        // (plain BF16: the input rounding) plus FP64 roundings
+        const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
+        const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
+                                           : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
+        const double te = fabs(p.alpha) * split_err +
+                          2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
+        const double old = sC[jl * SP_BM + il];
+        if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
+          atomicAdd(&cnt[2], 1);
+          const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
+          if ((long long)q < p.loc_cap) {
+            DevLoc L;
+            L.row = gi; L.col = gj; L.tile = tile; L.kind = 0; L.delta = old - nv;
+            p.loc[q] = L;
+          }
+        }
+        sC[jl * SP_BM + il] = nv;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      DevReport *r = p.rep;
+      if (cnt[0]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[0]);
+      if (cnt[1]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[1]);
+      if (cnt[2]) { atomicAdd(&r->detected, (unsigned long long)cnt[2]); atomicAdd(&r->corrected, (unsigned long long)cnt[2]); }
+      if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
+    }
+  }
+  // store (plain coalesced stores: rows of the tile are contiguous in C)
+  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
+    const int il = e & 127, jl = e >> 7;
+    if (il < mI && jl < nJt) p.C[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldc] = sC[e];
+  }
+}
+
+}  // namespace ftg

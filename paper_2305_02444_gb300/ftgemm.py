@@ -34,7 +34,8 @@ class Loc(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("detected", _i64), ("corrected", _i64), ("checksum_only", _i64),
                 ("unverifiable", _i64), ("flagged_rows", _i64), ("flagged_cols", _i64),
-                ("recomputed", _i64), ("n_loc", _i64), ("cap", _i64), ("loc", ctypes.POINTER(Loc))]
+                ("recomputed", _i64), ("panel_detected", _i64), ("n_loc", _i64), ("cap", _i64),
+                ("loc", ctypes.POINTER(Loc))]
 
 
 class Flip(ctypes.Structure):
@@ -70,6 +71,8 @@ def lib():
         L.ftgemm_d_host.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
         L.ftgemm_d_noalloc.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
         L.ftgemm_d_unfused.argtypes = _GEMM_ARGS + [ctypes.POINTER(Report), _vp]
+        L.ftgemm_d_split.argtypes = _GEMM_ARGS + [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Report), _vp]
+        L.ftgemm_d_split.restype = ctypes.c_int
         L.ftgemm_encode_operands.argtypes = [ctypes.c_char, ctypes.c_char, _i64, _i64, _i64, _vp, _i64,
                                              _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.ftgemm_set_injection.argtypes = [ctypes.POINTER(Inject)]
@@ -77,6 +80,8 @@ def lib():
         L.ftgemm_injection_log.restype = _i64
         L.ftgemm_selftest_wait_timeout.argtypes = [_i64, _vp]
         L.ftgemm_launch_count.restype = _i64
+        L.ftgemm_set_panel_check.argtypes = [ctypes.c_int]
+        L.ftgemm_set_panel_check.restype = ctypes.c_int
         L.ftgemm_set_splitk.argtypes = [ctypes.c_int]
         L.ftgemm_set_splitk.restype = ctypes.c_int
         L.ftgemm_timing.argtypes = [ctypes.c_int]
@@ -193,6 +198,20 @@ def ftgemm_d_unfused(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ld
     return rc, None
 
 
+def ftgemm_d_split(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices=11, ft=True,
+                   report=True, loc_cap=4096, stream=None):
+    """Split-precision FT-GEMM on the BF16 tensor cores (nslices 0: plain BF16;
+    S >= 1: FP64 emulated with S slices); returns (rc, report dict or None)."""
+    if report:
+        r, locs = _report(loc_cap)
+        rc = lib().ftgemm_d_split(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                                  _ptr(C), ldc, nslices, 1 if ft else 0, ctypes.byref(r), _stream(stream))
+        return rc, _report_dict(r, locs, loc_cap)
+    rc = lib().ftgemm_d_split(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
+                              _ptr(C), ldc, nslices, 1 if ft else 0, None, _stream(stream))
+    return rc, None
+
+
 def ftgemm_d_noalloc(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, report=True,
                      loc_cap=1024, stream=None):
     """ftgemm_d without any device allocation (scratch in a static device
@@ -245,6 +264,11 @@ def ftgemm_injection_log():
 
 def ftgemm_selftest_wait_timeout(limit_ns: int, stream=None) -> int:
     return lib().ftgemm_selftest_wait_timeout(limit_ns, _stream(stream))
+
+
+def ftgemm_set_panel_check(kslabs: int) -> int:
+    """Verify accumulators every kslabs k-slabs (0: only at the end of K)."""
+    return lib().ftgemm_set_panel_check(kslabs)
 
 
 def ftgemm_set_splitk(nsplit: int) -> int:

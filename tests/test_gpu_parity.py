@@ -485,3 +485,49 @@ def test_unfused_requires_aligned_operands(ft):
     A = torch.zeros(9 * 8, dtype=torch.float64, device="cuda")
     rc, _ = ft.ftgemm_d_unfused("N", "N", 9, 8, 8, 1.0, A, 9, A, 8, 0.0, A, 10)
     assert rc == ft.ERR_UNALIGNED
+
+
+# ------------------------------------------------------------------------------ per-k-panel verification
+
+class panel:
+    def __init__(self, ft, n):
+        self.ft, self.n = ft, n
+
+    def __enter__(self):
+        assert self.ft.ftgemm_set_panel_check(self.n) == 0
+
+    def __exit__(self, *a):
+        self.ft.ftgemm_set_panel_check(0)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal", "loguniform"])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_panel_check_fault_free(ft, orc, dist, ta, tb):
+    P = make_problem(ta, tb, 300, 260, 1500, seed=404, dist=dist)
+    ref, E = oracle_ref(orc, P, 1.5, 0.5)
+    with panel(ft, 4):
+        rc, rep, out = run_gpu(ft, P, 1.5, 0.5)
+    assert rc == 0
+    assert_parity(orc, P, out, ref, E)
+    assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0 and rep["detected"] == 0
+
+
+def test_panel_check_catches_faults_early_and_separately(ft, orc):
+    """Panels of 8 k-slabs over K = 1024 (8 panels).  A fault in panel 0 is
+    corrected at the first panel boundary (kind 2); a second fault in the same
+    element in panel 3 is caught separately at its own boundary; a fault in
+    the last panel is left to the end-of-tile verification (kind 0)."""
+    P = make_problem("N", "N", 256, 256, 1024, seed=505)
+    ref, E = oracle_ref(orc, P, 1.0, 1.0)
+    flips = [(10, 20, 3, 60), (10, 20, 27, 58), (200, 100, 5, 61), (130, 7, 62, 59)]
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        with panel(ft, 8):
+            rc, rep, out = run_gpu(ft, P, 1.0, 1.0)
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    assert rc == 0
+    assert_parity(orc, P, out, ref, E)
+    assert rep["detected"] == 4 and rep["panel_detected"] == 3
+    kinds = sorted((l[0], l[1], l[3]) for l in rep["locs"])
+    assert kinds == [(10, 20, 2), (10, 20, 2), (130, 7, 0), (200, 100, 2)]

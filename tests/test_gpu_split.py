@@ -1,0 +1,147 @@
+"""Split-precision FT-GEMM on the BF16 tensor cores against the FP64 oracle.
+
+Tolerances (stated, not tuned):
+  emulated FP64 with S slices of w bits: the parity bound of the FP64 path
+  plus the splitting bound |alpha| sigma_i tau_j K (S + 4) 2^(-wS), where
+  sigma_i, tau_j are the power-of-two row/column scales (every row of op(A)
+  and column of op(B) keeps w*S bits relative to its largest element);
+  plain BF16: |alpha| (2^-7 + 2.01 (K+2) 2^-24) sum_k |a_ik||b_kj| (bf16
+  input rounding + FP32 accumulation) plus the FP64 parity bound.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ft():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_02444_gb300 import build
+    build.build()
+    from paper_2305_02444_gb300 import ftgemm
+    ftgemm.lib()
+    ftgemm.ftgemm_set_injection(mode=0)
+    yield ftgemm
+    ftgemm.ftgemm_set_injection(mode=0)
+
+
+def wbits(K):
+    return 8 if K <= 256 else 7 if K <= 1024 else 6 if K <= 4096 else 5
+
+
+def problem(ta, tb, M, N, K, seed, dist="uniform"):
+    from paper_2305_02444_gb300 import inputs
+    ar, ac = (M, K) if ta == "N" else (K, M)
+    br, bc = (K, N) if tb == "N" else (N, K)
+    A = inputs.matrix(ar, ac, seed, dist)
+    B = inputs.matrix(br, bc, seed + 1, dist)
+    C = inputs.matrix(M, N, seed + 2, dist)
+    return A, B, C, ar, br
+
+
+def run(ft, ta, tb, M, N, K, alpha, beta, A, B, C, ar, br, S, ftflag=True):
+    dA, dB, dC = A.cuda(), B.cuda(), C.cuda()
+    rc, rep = ft.ftgemm_d_split(ta, tb, M, N, K, alpha, dA, ar, dB, br, beta, dC, M, nslices=S,
+                                ft=ftflag)
+    torch.cuda.synchronize()
+    assert rc == 0, ft.ftgemm_strerror(rc)
+    return dC.cpu().T.numpy(), rep
+
+
+def scales(ta, tb, A, B, ar, br):
+    opA = A[:, :ar].T.numpy(); opA = opA if ta == "N" else opA.T
+    opB = B[:, :br].T.numpy(); opB = opB if tb == "N" else opB.T
+    sa = np.array([2.0 ** math.frexp(float(np.abs(r).max()))[1] if np.abs(r).max() > 0 else 1.0 for r in opA])
+    sb = np.array([2.0 ** math.frexp(float(np.abs(c).max()))[1] if np.abs(c).max() > 0 else 1.0 for c in opB.T])
+    return opA, opB, sa, sb
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")])
+@pytest.mark.parametrize("M,N,K,S", [(300, 260, 200, 7), (130, 257, 1000, 8), (256, 128, 5000, 11)])
+def test_emulated_fp64_parity(ft, orc, ta, tb, M, N, K, S):
+    A, B, C, ar, br = problem(ta, tb, M, N, K, seed=M + K)
+    alpha, beta = 1.5, 0.5
+    got, rep = run(ft, ta, tb, M, N, K, alpha, beta, A, B, C, ar, br, S)
+    ref, E = orc.gemm(ta, tb, alpha, A[:, :ar].T.numpy(), B[:, :br].T.numpy(), beta, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales(ta, tb, A, B, ar, br)
+    w = wbits(K)
+    split = abs(alpha) * np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-w * S)
+    assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+    assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0 and rep["detected"] == 0
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
+def test_plain_bf16_form(ft, orc, ta, tb):
+    M, N, K = 300, 200, 700
+    A, B, C, ar, br = problem(ta, tb, M, N, K, seed=31)
+    alpha, beta = 1.0, 1.0
+    got, rep = run(ft, ta, tb, M, N, K, alpha, beta, A, B, C, ar, br, 0)
+    ref, E = orc.gemm(ta, tb, alpha, A[:, :ar].T.numpy(), B[:, :br].T.numpy(), beta, C.T.numpy(), want_E=True)
+    opA, opB, _, _ = scales(ta, tb, A, B, ar, br)
+    absab = np.abs(opA) @ np.abs(opB)
+    tol = abs(alpha) * (2.0 ** -7 + 2.01 * (K + 2) * 2.0 ** -24) * absab + orc.parity_tol(K, E)
+    assert np.all(np.abs(got - ref) <= tol)
+    rel = np.abs(got - ref).max() / np.abs(ref).max()
+    assert 1e-6 < rel < 1e-2   # really BF16: far from FP64, well inside its own bound
+    assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
+
+
+def test_ft_and_unprotected_give_the_same_bits(ft):
+    A, B, C, ar, br = problem("N", "N", 200, 200, 300, seed=3)
+    g1, _ = run(ft, "N", "N", 200, 200, 300, 1.25, -0.5, A, B, C, ar, br, 8, ftflag=True)
+    g0, _ = run(ft, "N", "N", 200, 200, 300, 1.25, -0.5, A, B, C, ar, br, 8, ftflag=False)
+    np.testing.assert_array_equal(g0, g1)
+
+
+def test_split_injection_detected_and_corrected(ft, orc):
+    """Flips of the top exponent bit of the FP64 accumulator after chosen slice
+    pairs (the first, a middle and the last of the 36 pairs): each moves the
+    value by at least 2 (or to a huge value / Inf / NaN), above the FP32
+    checksums' threshold, so each is detected and corrected by the FP64
+    recomputation.  (Flips far below that threshold, e.g. low exponent bits of
+    the small early-pair partial sums, are not detectable with FP32
+    checksums: their band is stated with the design.)"""
+    M, N, K, S = 256, 256, 512, 8
+    A, B, C, ar, br = problem("N", "N", M, N, K, seed=17)
+    flips = [(5, 6, 0, 62), (100, 200, 20, 62), (250, 3, 35, 62)]   # kstep = pair index (36 pairs)
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        got, rep = run(ft, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S)
+        log = ft.ftgemm_injection_log()
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    assert [L["applied"] for L in log] == [1, 1, 1]
+    ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 1.0, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales("N", "N", A, B, ar, br)
+    split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+    assert rep["detected"] == 3
+    assert sorted(l[:2] for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)
+
+
+def test_loguniform_error_is_stated(ft, orc):
+    """Six-decade log-uniform entries: the emulation keeps w*S bits relative to
+    each row's (column's) largest entry; the error stays within the stated
+    bound and is far below the plain BF16 form's."""
+    M = N = 256
+    K = 2048
+    A, B, C, ar, br = problem("N", "N", M, N, K, seed=99, dist="loguniform")
+    ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 0.0, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales("N", "N", A, B, ar, br)
+    errs = {}
+    for S in (0, 6, 9):
+        got, rep = run(ft, "N", "N", M, N, K, 1.0, 0.0, A, B, C, ar, br, S)
+        errs[S] = float(np.abs(got - ref).max() / np.abs(ref).max())
+        if S:
+            split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+            assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+        assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
+    assert errs[9] < errs[6] < errs[0]

@@ -66,6 +66,11 @@ def test_argument_codes_without_device(ft, args, code):
     assert ft.ftgemm_d_host(ta, tb, M, N, K, 1.0, 0, lda, 0, ldb, 0.0, 0, ldc, stream=0)[0] == code
 
 
+def test_split_slice_count_checked_without_device(ft):
+    assert ft.ftgemm_d_split("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4, nslices=16, report=False, stream=0)[0] == -14
+    assert ft.ftgemm_d_split("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4, nslices=-1, report=False, stream=0)[0] == -14
+
+
 def test_host_settings_and_strings(ft):
     assert ft.ftgemm_set_injection(mode=0) == 0
     assert ft.ftgemm_set_injection(mode=1, seed=5, count=-1) == -1
