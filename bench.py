@@ -336,6 +336,100 @@ def batched(args):
     print(json.dumps(line), flush=True)
 
 
+def split(args):
+    """Split precision at M = N = K = 8192 (or --size), entries sign-random with
+    |x| log-uniform in [1e-3, 1e3]: FP64 emulated with S BF16 slices and the
+    plain BF16 form, FP32 checksums / FP64 verify, one flip per 64 tiles (top
+    exponent bit of the FP64 accumulator after a random slice pair); against
+    the DFMA FP64 path on the same inputs; max error vs the FP64 oracle on
+    sampled rows."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2305_02444_gb300 import build, ftgemm, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    n = M
+    A = inputs.matrix(n, n, SEED, "loguniform", device="cuda")
+    B = inputs.matrix(n, n, SEED + 1, "loguniform", device="cuda")
+    C0 = inputs.matrix(n, n, SEED + 2, "loguniform", device="cuda")
+    C = C0.clone()
+    flops = 2.0 * n ** 3
+    tiles = (-(-n // 128)) ** 2
+    rng = np.random.default_rng(SEED)
+    rows = np.sort(rng.choice(n, size=args.split_rows, replace=False))
+    Ah, Bh, C0h = A.cpu().T.numpy(), B.cpu().T.numpy(), C0.cpu().T.numpy()
+    refs = [oracle.gemm("N", "N", 1.0, Ah[i:i + 1], Bh, 1.0, C0h[i:i + 1])[0][0] for i in rows]
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps / 1e3
+
+    def err_of(fn):
+        C.copy_(C0)
+        fn()
+        torch.cuda.synchronize()
+        out = C.cpu().T.numpy()
+        return max(float(np.abs(out[i] - r).max() / np.abs(r).max()) for i, r in zip(rows, refs))
+
+    res = {}
+    forms = [("fp64_dfma", None, 1)] + [(f"emulated_S{S}", S, 1) for S in args.split_slices] + \
+        [(f"emulated_S{S}_fp64ck", S, 2) for S in args.split_slices] + [("bf16_plain", 0, 1)]
+    for name, S, ck in forms:
+        if S is None:
+            ft_fn = lambda: ftgemm.ftgemm_d("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, report=False)
+            no_fn = lambda: ftgemm.ftgemm_d_noft("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n)
+            steps = 2
+        else:
+            ft_fn = lambda S=S, ck=ck: ftgemm.ftgemm_d_split("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n,
+                                                             nslices=S, ft=ck, report=False)
+            no_fn = lambda S=S: ftgemm.ftgemm_d_split("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, nslices=S,
+                                                      ft=False, report=False)
+            steps = max(3, args.steps)
+        t_ft = timed(ft_fn, steps)
+        t_no = timed(no_fn, steps)
+        err = err_of(ft_fn)
+        npairs = 1 if S in (None, 0) else S * (S + 1) // 2
+        nflip = math.ceil(tiles / 64)
+        if S is None:
+            ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nflip)
+        else:
+            flips = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(npairs)), 62) for _ in range(nflip)]
+            ftgemm.ftgemm_set_injection(mode=2, flips=flips)
+        C.copy_(C0)
+        if S is None:
+            rc, rep = ftgemm.ftgemm_d("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, loc_cap=0)
+        else:
+            rc, rep = ftgemm.ftgemm_d_split("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, nslices=S, ft=ck,
+                                            loc_cap=0)
+        ftgemm.ftgemm_set_injection(mode=0)
+        torch.cuda.synchronize()
+        out = C.cpu().T.numpy()
+        err_inj = max(float(np.abs(out[i] - r).max() / np.abs(r).max()) for i, r in zip(rows, refs))
+        res[name] = {"tflops_fp64_equiv": flops / t_ft / 1e12, "unprotected_tflops": flops / t_no / 1e12,
+                     "ft_overhead_pct": 100.0 * (t_ft / t_no - 1.0), "ms": t_ft * 1e3,
+                     "max_rel_err_vs_oracle": err, "max_rel_err_injected_run": err_inj,
+                     "flips": nflip, "detected": rep["detected"], "rc": rc,
+                     "slices": S, "pairs": npairs if S else (1 if S == 0 else None),
+                     "checksums": "fp64" if (S is None or ck == 2) else "fp32"}
+        print(json.dumps({name: res[name]}), flush=True)
+    base = res["fp64_dfma"]["tflops_fp64_equiv"]
+    line = {"metric": "split-precision FT-GEMM TFLOP/s (FP64-equivalent, 2MNK) and max error vs FP64 oracle",
+            "config": {"workload": f"split_{n}cubed_loguniform1e-3to1e3_flips1per64tiles", "rows_checked": len(rows)},
+            "results": res, "speedup_vs_fp64_dfma": {k: v["tflops_fp64_equiv"] / base for k, v in res.items()},
+            "mma_sync_bf16_peak_tflops_measured": 595}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,10 +446,18 @@ def main():
     ap.add_argument("--sweep-dist", default="uniform", help="input distribution for --sweep")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--batched", action="store_true", help="the batched workload (512 small problems)")
+    ap.add_argument("--split", action="store_true", help="split-precision forms (BF16 tensor cores)")
+    ap.add_argument("--split-slices", default="7,9,11", help="slice counts for --split")
+    ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
     args = ap.parse_args()
     set_size(args.size)
     if args.sweep:
         return sweep(args)
+    if args.split:
+        if args.warmup < 3:
+            args.warmup = 3
+        args.split_slices = [int(x) for x in args.split_slices.split(",") if x]
+        return split(args)
     if args.batched:
         if args.warmup < 3:
             args.warmup = 3

@@ -257,10 +257,16 @@ int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan);
  *    row's (column's) largest keep fewer bits.
  * ft = 1: predicted checksums in FP32 from the staged slices, reference sums,
  * verification and correction (FP64 recomputation from the original operands)
- * in FP64; ft = 0 compiles the checks out (overhead baseline).  Injection
+ * in FP64; ft = 2 (emulated forms only): FP64 predicted checksums from the
+ * original operands (operand checksum pass + two skinny FP64 GEMMs before the
+ * kernel), verified against the scaled result with the FP64 threshold plus
+ * the splitting bound -- far more sensitive than FP32 checksums; ft = 0
+ * compiles the checks out (overhead baseline).  Injection
  * (ftgemm_set_injection) flips bits of the FP64 accumulator after the slice
  * pair numbered `kstep` has been folded in (kstep < number of pairs).
- * Returns -14 for an invalid nslices. */
+ * Returns -14 for an invalid nslices, -15 for an invalid ft (ft = 2 needs
+ * nslices >= 1 and operands that are 16-byte aligned with even leading
+ * dimensions). */
 int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                    const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                    double *C, int64_t ldc, int nslices, int ft, ftgemm_report *rep, void *stream);

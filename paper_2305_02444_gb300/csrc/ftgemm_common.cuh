@@ -112,6 +112,10 @@ struct SplitParams {
   DevFlip *flips;
   const int *tile_off;
   int inj;
+  // CK 2: FP64 predicted checksums (skinny GEMMs) and the absolute sums
+  const double *P1, *P2;        // nI x N (ld ldp1), M x nJ (ld ldp2)
+  long long ldp1, ldp2;
+  const double *arowabs, *aabsmax, *bcolabs, *babsmax;
 };
 
 

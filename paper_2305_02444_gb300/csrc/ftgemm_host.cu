@@ -40,7 +40,7 @@ cudaError_t launch_panel_tn(bool, const CUtensorMap &, const CUtensorMap &, cons
                             cudaStream_t);
 cudaError_t launch_panel_tt(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
                             cudaStream_t);
-cudaError_t launch_split(bool ta, bool tb, bool ft, const CUtensorMap &a, const CUtensorMap &b,
+cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
                            int S, int w, int plain, void *out, cudaStream_t s);
@@ -1510,6 +1510,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
   if (rc) return rc;
   if (nslices < 0 || nslices > 15) return -14;
+  if (ft < 0 || ft > 2 || (ft == 2 && nslices == 0)) return -15;
   zero_report(rep);
   if (M == 0 || N == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1562,6 +1563,29 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   p.rep = (DevReport *)w.rep.p; p.loc = (DevLoc *)w.loc.p; p.loc_cap = LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
   p.verify = ft;
+  if (ft == 2) {
+    // FP64 predicted checksums of the 128 x 128 tiles from the original operands
+    const long long Kq = (K + BK - 1) / BK * BK, ldp1 = (nI + 1) & ~1LL, ldp2 = (M + 1) & ~1LL;
+    if (ensure(w.acs, sizeof(double) * nI * Kq) || ensure(w.bcs, sizeof(double) * nJ * Kq) ||
+        ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
+        ensure(w.bcolabs, sizeof(double) * N) || ensure(w.babsmax, sizeof(double) * nJ) ||
+        ensure(w.uP1, sizeof(double) * ldp1 * N) || ensure(w.uP2, sizeof(double) * ldp2 * nJ))
+      return FTGEMM_ERR_NOMEM;
+    if (!tma_ok(A, lda) || !tma_ok(B, ldb)) return FTGEMM_ERR_UNALIGNED;
+    if ((rc = run_encode(ta_t, tb_t, M, N, K, A, lda, B, ldb, Kq, (double *)w.acs.p, (double *)w.aabsmax.p,
+                         (double *)w.arowabs.p, (double *)w.bcs.p, (double *)w.babsmax.p, (double *)w.bcolabs.p,
+                         w, s)))
+      return rc;
+    if ((rc = gemm_impl('T', transB, nI, N, K, 1.0, (const double *)w.acs.p, Kq, B, ldb, 0.0, (double *)w.uP1.p,
+                        ldp1, nullptr, s, false)))
+      return rc;
+    if ((rc = gemm_impl(transA, 'N', M, nJ, K, 1.0, A, lda, (const double *)w.bcs.p, Kq, 0.0, (double *)w.uP2.p,
+                        ldp2, nullptr, s, false)))
+      return rc;
+    p.P1 = (const double *)w.uP1.p; p.ldp1 = ldp1; p.P2 = (const double *)w.uP2.p; p.ldp2 = ldp2;
+    p.arowabs = (const double *)w.arowabs.p; p.aabsmax = (const double *)w.aabsmax.p;
+    p.bcolabs = (const double *)w.bcolabs.p; p.babsmax = (const double *)w.babsmax.p;
+  }
   cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   bool inj = false;
   if (ft) {
@@ -1575,7 +1599,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  if (launch_split(ta_t, tb_t, ft != 0, mA, mB, p, s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  if (launch_split(ta_t, tb_t, ft, mA, mB, p, s) != cudaSuccess) return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);
   g_launches++;
   if (rep) {

@@ -6,28 +6,30 @@
 
 namespace ftg {
 
-template <bool TA, bool TB, bool FT>
+template <bool TA, bool TB, int CK>
 static cudaError_t launch_split_variant(const CUtensorMap &a, const CUtensorMap &b, const SplitParams &p,
                                         cudaStream_t s) {
-  auto k = ftsplit_kernel<TA, TB, FT>;
+  auto k = ftsplit_kernel<TA, TB, CK>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)p.nI * (unsigned)p.nJ, 256, SP_SMEM_BYTES, s>>>(a, b, p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_split(bool ta, bool tb, bool ft, const CUtensorMap &a, const CUtensorMap &b,
+template <int CK>
+static cudaError_t launch_split_ck(bool ta, bool tb, const CUtensorMap &a, const CUtensorMap &b,
+                                   const SplitParams &p, cudaStream_t s) {
+  if (!ta && !tb) return launch_split_variant<false, false, CK>(a, b, p, s);
+  if (!ta && tb) return launch_split_variant<false, true, CK>(a, b, p, s);
+  if (ta && !tb) return launch_split_variant<true, false, CK>(a, b, p, s);
+  return launch_split_variant<true, true, CK>(a, b, p, s);
+}
+
+cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s) {
-  if (ft) {
-    if (!ta && !tb) return launch_split_variant<false, false, true>(a, b, p, s);
-    if (!ta && tb) return launch_split_variant<false, true, true>(a, b, p, s);
-    if (ta && !tb) return launch_split_variant<true, false, true>(a, b, p, s);
-    return launch_split_variant<true, true, true>(a, b, p, s);
-  }
-  if (!ta && !tb) return launch_split_variant<false, false, false>(a, b, p, s);
-  if (!ta && tb) return launch_split_variant<false, true, false>(a, b, p, s);
-  if (ta && !tb) return launch_split_variant<true, false, false>(a, b, p, s);
-  return launch_split_variant<true, true, false>(a, b, p, s);
+  if (ck == 1) return launch_split_ck<1>(ta, tb, a, b, p, s);
+  if (ck == 2) return launch_split_ck<2>(ta, tb, a, b, p, s);
+  return launch_split_ck<0>(ta, tb, a, b, p, s);
 }
 
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,

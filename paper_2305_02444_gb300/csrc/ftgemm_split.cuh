@@ -125,7 +125,10 @@ __device__ __forceinline__ double sp_glob_b(const SplitParams &p, long long k, l
 
 // One CTA per 128 x 128 tile; 8 warps as 2 (rows) x 4 (columns), warp tile
 // 64 x 32 = 4 x 4 mma tiles.  tmA / tmB: 3-D maps {Kp, R, S} of the slices.
-template <bool TA, bool TB, bool FT>
+// CK 0: no checks; 1: FP32 predicted checksums from the staged slices;
+// 2: FP64 predicted checksums from the original operands (two skinny FP64
+// GEMMs before the kernel), verified against the scaled FP64 result.
+template <bool TA, bool TB, int CK>
 __global__ void __launch_bounds__(256, 1)
     ftsplit_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ SplitParams p) {
@@ -141,6 +144,7 @@ __global__ void __launch_bounds__(256, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(cnt + 64);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + SP_STAGES);
 
+  constexpr bool FT = CK == 1;  // FP32 checksum work in the mainloop
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x, I = tile % p.nI, J = tile / p.nI;
   const int i0 = I * SP_BM, j0 = J * SP_BN;
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(256, 1)
   float cs32 = 0.f, ca32 = 0.f;     // FT: this pair-chunk's predicted checksum (t < 128: column, else row)
   double cs64 = 0.0, ca64 = 0.0;    // folded predicted checksum and its absolute bound
   int fptr = 0, fend = 0;
-  if (FT && p.inj) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+  if (CK >= 1 && p.inj) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
 
   bool ok = true;
   for (int step = 0; step < nsteps; ++step) {
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(256, 1)
         cs32 = 0.f;
         ca32 = 0.f;
       }
-      if (FT && p.inj && slab + 1 == nslab_total) {
+      if (CK >= 1 && p.inj && slab + 1 == nslab_total) {
         // injection point: after pair pq has been folded in (kstep = pair index)
         while (fptr < fend) {
           DevFlip *f = p.flips + fptr;
@@ -399,7 +403,48 @@ __global__ void __launch_bounds__(256, 1)
     }
   }
   __syncthreads();
-  if (FT) {
+  if (CK == 2) {
+    // FP64 checksums: reference sums of the scaled output tile against
+    // alpha * (acs x op(B) or op(A) x bcs) + beta * (sums of C_in)
+    const int idx = tid & 127;
+    const bool col = tid < 128;
+    const bool valid = col ? (idx < nJt) : (idx < mI);
+    if (valid) {
+      double ref = 0.0, cs = 0.0, ca = 0.0, sig = 0.0;
+      if (col) {
+        const long long gj = j0 + idx;
+        for (int i = 0; i < mI; ++i) {
+          ref += sC[idx * SP_BM + i];
+          sig += ldexp(1.0, p.eA[i0 + i]);
+          if (use_c) { const double c = p.C[(i0 + i) + gj * p.ldc]; cs += c; ca += fabs(c); }
+        }
+        sig *= ldexp(1.0, p.eB[gj]);
+      } else {
+        const long long gi = i0 + idx;
+        for (int j = 0; j < nJt; ++j) {
+          ref += sC[j * SP_BM + idx];
+          sig += ldexp(1.0, p.eB[j0 + j]);
+          if (use_c) { const double c = p.C[gi + (long long)(j0 + j) * p.ldc]; cs += c; ca += fabs(c); }
+        }
+        sig *= ldexp(1.0, p.eA[gi]);
+      }
+      const double P = col ? p.P1[(long long)I + (long long)(j0 + idx) * p.ldp1]
+                           : p.P2[(long long)(i0 + idx) + (long long)J * p.ldp2];
+      const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
+      const double S64 = col ? p.bcolabs[j0 + idx] * p.aabsmax[I] : p.arowabs[i0 + idx] * p.babsmax[J];
+      const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
+      const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
+      const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) +
+                         split_err + n * 0x1p-1021;
+      if (!isfinite(pred) || !isfinite(tau)) atomicAdd(&cnt[4], 1);
+      else if (!(fabs(ref - pred) <= tau)) {
+        if (col) s_fc[atomicAdd(&cnt[1], 1)] = idx;
+        else s_fr[atomicAdd(&cnt[0], 1)] = idx;
+      }
+    }
+    __syncthreads();
+  }
+  if (CK >= 1) {
     const int nr = cnt[0], nc = cnt[1];
     // flagged intersections (or whole flagged segments when one side is empty
     // or there are more than 64): recompute in FP64 from the original operands

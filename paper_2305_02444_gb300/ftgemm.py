@@ -201,14 +201,15 @@ def ftgemm_d_unfused(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ld
 def ftgemm_d_split(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nslices=11, ft=True,
                    report=True, loc_cap=4096, stream=None):
     """Split-precision FT-GEMM on the BF16 tensor cores (nslices 0: plain BF16;
-    S >= 1: FP64 emulated with S slices); returns (rc, report dict or None)."""
+    S >= 1: FP64 emulated with S slices; ft 0 none, 1/True FP32 checksums,
+    2 FP64 checksums); returns (rc, report dict or None)."""
     if report:
         r, locs = _report(loc_cap)
         rc = lib().ftgemm_d_split(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
-                                  _ptr(C), ldc, nslices, 1 if ft else 0, ctypes.byref(r), _stream(stream))
+                                  _ptr(C), ldc, nslices, int(ft), ctypes.byref(r), _stream(stream))
         return rc, _report_dict(r, locs, loc_cap)
     rc = lib().ftgemm_d_split(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
-                              _ptr(C), ldc, nslices, 1 if ft else 0, None, _stream(stream))
+                              _ptr(C), ldc, nslices, int(ft), None, _stream(stream))
     return rc, None
 
 

@@ -145,3 +145,43 @@ def test_loguniform_error_is_stated(ft, orc):
             assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
         assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
     assert errs[9] < errs[6] < errs[0]
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+def test_emulated_with_fp64_checksums(ft, orc, ta, tb):
+    M, N, K, S = 300, 260, 1000, 8
+    A, B, C, ar, br = problem(ta, tb, M, N, K, seed=77)
+    got, rep = run(ft, ta, tb, M, N, K, 1.5, 0.5, A, B, C, ar, br, S, ftflag=2)
+    ref, E = orc.gemm(ta, tb, 1.5, A[:, :ar].T.numpy(), B[:, :br].T.numpy(), 0.5, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales(ta, tb, A, B, ar, br)
+    split = 1.5 * np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+    assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0 and rep["detected"] == 0
+
+
+def test_fp64_checksums_see_what_fp32_checksums_miss(ft, orc):
+    """Mantissa flips (bits 40..50) of the full-magnitude accumulator after the
+    last slice pair change an element by 2^-12..2^-2 of its value: the FP64
+    checksums (ft=2) detect and correct every one; the FP32 checksums (ft=1)
+    cannot see changes that small."""
+    M, N, K, S = 256, 256, 512, 8
+    npairs = S * (S + 1) // 2
+    A, B, C, ar, br = problem("N", "N", M, N, K, seed=23)
+    ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 0.0, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales("N", "N", A, B, ar, br)
+    split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    rng = np.random.default_rng(5)
+    flips = [(int(rng.integers(M)), int(rng.integers(N)), npairs - 1, bit) for bit in range(40, 51)]
+    detected = {}
+    for mode in (1, 2):
+        assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+        try:
+            got, rep = run(ft, "N", "N", M, N, K, 1.0, 0.0, A, B, C, ar, br, S, ftflag=mode)
+        finally:
+            ft.ftgemm_set_injection(mode=0)
+        detected[mode] = rep["detected"]
+        if mode == 2:
+            assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+            assert sorted(l[:2] for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)
+    assert detected[2] == len(flips)
+    assert detected[1] < len(flips) // 2
