@@ -42,6 +42,17 @@ SEED = 20230614
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # FP64 FMA pipe, max SM clock
 
 
+def measured_peaks():
+    """Measured copy bandwidth and cuBLAS bf16 throughput of this GPU model
+    (MEASURED_PEAKS.json beside this file), else the fallback figures."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "source": "fallback"}
+
+
 def set_size(n: int):
     global M, N, K, TILES, FLIPS, WORKLOAD
     M = N = K = n
@@ -382,9 +393,18 @@ def split(args):
         return max(float(np.abs(out[i] - r).max() / np.abs(r).max()) for i, r in zip(rows, refs))
 
     res = {}
-    forms = [("fp64_dfma", None, 1)] + [(f"emulated_S{S}", S, 1) for S in args.split_slices] + \
-        [(f"emulated_S{S}_fp64ck", S, 2) for S in args.split_slices] + [("bf16_plain", 0, 1)]
-    for name, S, ck in forms:
+    engines = [e for e in args.split_engine.split(",") if e]
+    forms = [("fp64_dfma", None, 1, None)]
+    for eng in engines:
+        sfx = "" if eng == "tc" else "_mma"
+        forms += [(f"emulated_S{S}_fp64ck{sfx}", S, 2, eng) for S in args.split_slices]
+        forms += [(f"bf16_plain{sfx}", 0, 0, eng)]
+    forms += [(f"emulated_S{S}_fp32ck_mma", S, 1, "mma") for S in args.split_slices] + \
+        [("bf16_plain_fp32ck_mma", 0, 1, "mma")]
+    peaks = measured_peaks()
+    for name, S, ck, eng in forms:
+        if eng is not None:
+            ftgemm.ftgemm_set_split_engine(0 if eng == "tc" else 1)
         if S is None:
             ft_fn = lambda: ftgemm.ftgemm_d("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, report=False)
             no_fn = lambda: ftgemm.ftgemm_d_noft("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n)
@@ -396,7 +416,11 @@ def split(args):
                                                       ft=False, report=False)
             steps = max(3, args.steps)
         t_ft = timed(ft_fn, steps)
+        ftgemm.ftgemm_timing(True)
         t_no = timed(no_fn, steps)
+        k_ms, k_n, _ = ftgemm.ftgemm_timing_read()
+        ftgemm.ftgemm_timing(False)
+        kms = k_ms / max(1, k_n)   # event-timed product kernel of the unprotected calls
         err = err_of(ft_fn)
         npairs = 1 if S in (None, 0) else S * (S + 1) // 2
         nflip = math.ceil(tiles / 64)
@@ -420,13 +444,20 @@ def split(args):
                      "max_rel_err_vs_oracle": err, "max_rel_err_injected_run": err_inj,
                      "flips": nflip, "detected": rep["detected"], "rc": rc,
                      "slices": S, "pairs": npairs if S else (1 if S == 0 else None),
-                     "checksums": "fp64" if (S is None or ck == 2) else "fp32"}
+                     "checksums": "fp64" if (S is None or ck == 2) else ("fp32" if ck == 1 else "none"),
+                     "engine": "dfma" if S is None else ("tcgen05" if (eng == "tc" and ck != 1) else "mma.sync"),
+                     "unprotected_kernel_ms": kms}
+        if S is not None:
+            # tensor work of the unprotected kernel: every kept pair is a 2MNK bf16 product
+            tf = npairs * flops / (kms / 1e3) / 1e12
+            res[name]["kernel_bf16_tflops"] = tf
+            res[name]["kernel_frac_of_bf16_peak"] = tf / peaks["bf16_tflops"]
         print(json.dumps({name: res[name]}), flush=True)
     base = res["fp64_dfma"]["tflops_fp64_equiv"]
     line = {"metric": "split-precision FT-GEMM TFLOP/s (FP64-equivalent, 2MNK) and max error vs FP64 oracle",
             "config": {"workload": f"split_{n}cubed_loguniform1e-3to1e3_flips1per64tiles", "rows_checked": len(rows)},
             "results": res, "speedup_vs_fp64_dfma": {k: v["tflops_fp64_equiv"] / base for k, v in res.items()},
-            "mma_sync_bf16_peak_tflops_measured": 595}
+            "mma_sync_bf16_peak_tflops_measured": 595, "bf16_peak_tflops": peaks["bf16_tflops"], "peak_source": peaks["source"]}
     print(json.dumps(line), flush=True)
 
 
@@ -449,6 +480,7 @@ def main():
     ap.add_argument("--split", action="store_true", help="split-precision forms (BF16 tensor cores)")
     ap.add_argument("--split-slices", default="7,9,11", help="slice counts for --split")
     ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
+    ap.add_argument("--split-engine", default="tc,mma", help="split engines: tc (tcgen05), mma (mma.sync)")
     args = ap.parse_args()
     set_size(args.size)
     if args.sweep:

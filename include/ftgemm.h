@@ -312,6 +312,14 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
  * 1 never splits, n >= 2 forces n splits (fewer when K is short). */
 int ftgemm_set_splitk(int nsplit);
 
+/* Engine of ftgemm_d_split (results: the same bits for the emulated forms,
+ * within the same bound for the plain BF16 form): 0 (default) runs the slice
+ * products on the tcgen05 tensor cores (FP32 accumulators and the FP64 fold
+ * in tensor memory) when ft is 0 or 2 and on the mma.sync kernel when ft is 1
+ * (its FP32 checksums are summed from the staged slices on the CUDA cores);
+ * 1 runs every call on the mma.sync kernel.  Returns -1 for another value. */
+int ftgemm_set_split_engine(int engine);
+
 /* Per-k-panel verification (FT-BLAS style; FT-GEMM blocks K by K_C, §2.1):
  * kslabs > 0 makes later ftgemm_d calls also verify every tile's
  * accumulators after every kslabs k-slabs (kslabs * 16 products) against the

@@ -42,6 +42,8 @@ cudaError_t launch_panel_tt(bool, const CUtensorMap &, const CUtensorMap &, cons
                             cudaStream_t);
 cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s);
+cudaError_t launch_split_tc(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
+                            const SplitParams &p, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
                            int S, int w, int plain, void *out, cudaStream_t s);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
@@ -212,6 +214,7 @@ bool tma_ok(const void *p, long long ld) {
 
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
+int g_split_engine = 0;  // split precision: 0 tcgen05 (FP32 checksums: mma.sync), 1 mma.sync
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
 int g_panel = 0;   // verify the accumulators every g_panel k-slabs (0: only at the end of the tile)
 
@@ -794,6 +797,13 @@ int ftgemm_set_panel_check(int kslabs) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (kslabs < 0) return -1;
   g_panel = kslabs;
+  return 0;
+}
+
+int ftgemm_set_split_engine(int engine) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (engine < 0 || engine > 1) return -1;
+  g_split_engine = engine;
   return 0;
 }
 
@@ -1599,7 +1609,10 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  if (launch_split(ta_t, tb_t, ft, mA, mB, p, s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  const bool tc = g_split_engine == 0 && ft != 1;
+  if ((tc ? launch_split_tc(ta_t, tb_t, ft, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
+      cudaSuccess)
+    return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);
   g_launches++;
   if (rep) {

@@ -30,66 +30,6 @@
 
 namespace ftg {
 
-// ---------------------------------------------------------------- slicing
-
-// Row exponent: e with max_k |x(r, k)| < 2^e (0 for an all-zero row).
-// X is op(X) given by (ptr, ld, trans): element (r, k) = trans ? X[k + r*ld] : X[r + k*ld].
-__global__ void split_rowexp_kernel(const double *__restrict__ X, long long ld, int trans, long long R,
-                                    long long K, int *__restrict__ e) {
-  // one warp per row for trans (k contiguous); one thread per row otherwise (r contiguous)
-  if (trans) {
-    const long long r = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
-    if (r >= R) return;
-    double m = 0.0;
-    for (long long k = lane; k < K; k += 32) m = fmax(m, fabs(X[k + r * ld]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
-  } else {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    double m = 0.0;
-    for (long long k = 0; k < K; ++k) m = fmax(m, fabs(X[r + k * ld]));
-    e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
-  }
-}
-
-// Slices: out[s][r][k] (bf16, row length Kp, zero padded), 64 x 64 tiles through
-// shared memory so that both the read and the write are coalesced.
-__global__ void __launch_bounds__(256) split_slice_kernel(const double *__restrict__ X, long long ld, int trans,
-                                                          long long R, long long K, long long Kp,
-                                                          const int *__restrict__ e, int S, int w, int plain,
-                                                          __nv_bfloat16 *__restrict__ out) {
-  __shared__ double t[64][65];
-  const long long r0 = (long long)blockIdx.y * 64, k0 = (long long)blockIdx.x * 64;
-  for (int q = threadIdx.x; q < 64 * 64; q += 256) {
-    int rr, kk;
-    if (trans) { kk = q & 63; rr = q >> 6; } else { rr = q & 63; kk = q >> 6; }
-    const long long r = r0 + rr, k = k0 + kk;
-    double v = 0.0;
-    if (r < R && k < K) v = trans ? X[k + r * ld] : X[r + k * ld];
-    t[rr][kk] = v;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 64 * 64; q += 256) {
-    const int kk = q & 63, rr = q >> 6;
-    const long long r = r0 + rr, k = k0 + kk;
-    if (r >= R || k >= Kp) continue;
-    double x = t[rr][kk];
-    if (plain) {
-      out[r * Kp + k] = __double2bfloat16(x);
-      continue;
-    }
-    x = ldexp(x, -e[r]);  // |x| < 1, exact
-    for (int s = 0; s < S; ++s) {
-      const double v = ldexp(x, w);
-      const double n = trunc(v);
-      out[((long long)s * R + r) * Kp + k] = __double2bfloat16(n);  // |n| < 2^w <= 256: exact
-      x = v - n;                                                      // exact
-    }
-  }
-}
-
 // ---------------------------------------------------------------- GEMM kernel
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
@@ -121,6 +61,128 @@ __device__ __forceinline__ double sp_glob_a(const SplitParams &p, long long i, l
 template <bool TA, bool TB>
 __device__ __forceinline__ double sp_glob_b(const SplitParams &p, long long k, long long j) {
   return TB ? p.B[j + k * p.ldb] : p.B[k + j * p.ldb];
+}
+
+// The end of a tile shared by the split kernels, run by 256 threads: sC holds
+// the tile's unscaled FP64 accumulators (column-major, 128 x 128); scale to
+// the output, verify with the FP64 checksums (CK 2), recompute the flagged
+// elements from the original operands (CK >= 1; s_fr / s_fc / cnt[0..1] hold
+// the rows / columns flagged so far), report, store.
+template <bool TA, bool TB, int CK>
+__device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *sC, int *s_fr, int *s_fc, int *cnt,
+                                                  int tile, int I, int J) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = I * SP_BM, j0 = J * SP_BN;
+  const int mI = (int)min((long long)SP_BM, p.M - i0), nJt = (int)min((long long)SP_BN, p.N - j0);
+  // scale to the output: out = alpha * 2^(eA_i + eB_j) * acc + beta * C  (C read only if beta != 0)
+  const bool use_c = p.beta != 0.0;
+  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
+    const int il = e & 127, jl = e >> 7;
+    if (il < mI && jl < nJt) {
+      const long long gi = i0 + il, gj = j0 + jl;
+      const double v = ldexp(sC[e], p.eA[gi] + p.eB[gj]);
+      sC[e] = use_c ? fma(p.alpha, v, p.beta * p.C[gi + gj * p.ldc]) : p.alpha * v;
+    }
+  }
+  __syncthreads();
+  if (CK == 2) {
+    // FP64 checksums: reference sums of the scaled output tile against
+    // alpha * (acs x op(B) or op(A) x bcs) + beta * (sums of C_in)
+    const int idx = tid & 127;
+    const bool col = tid < 128;
+    const bool valid = col ? (idx < nJt) : (idx < mI);
+    if (valid) {
+      double ref = 0.0, cs = 0.0, ca = 0.0, sig = 0.0;
+      if (col) {
+        const long long gj = j0 + idx;
+        for (int i = 0; i < mI; ++i) {
+          ref += sC[idx * SP_BM + i];
+          sig += ldexp(1.0, p.eA[i0 + i]);
+          if (use_c) { const double c = p.C[(i0 + i) + gj * p.ldc]; cs += c; ca += fabs(c); }
+        }
+        sig *= ldexp(1.0, p.eB[gj]);
+      } else {
+        const long long gi = i0 + idx;
+        for (int j = 0; j < nJt; ++j) {
+          ref += sC[j * SP_BM + idx];
+          sig += ldexp(1.0, p.eB[j0 + j]);
+          if (use_c) { const double c = p.C[gi + (long long)(j0 + j) * p.ldc]; cs += c; ca += fabs(c); }
+        }
+        sig *= ldexp(1.0, p.eA[gi]);
+      }
+      const double P = col ? p.P1[(long long)I + (long long)(j0 + idx) * p.ldp1]
+                           : p.P2[(long long)(i0 + idx) + (long long)J * p.ldp2];
+      const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
+      const double S64 = col ? p.bcolabs[j0 + idx] * p.aabsmax[I] : p.arowabs[i0 + idx] * p.babsmax[J];
+      const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
+      const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
+      const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) +
+                         split_err + n * 0x1p-1021;
+      if (!isfinite(pred) || !isfinite(tau)) atomicAdd(&cnt[4], 1);
+      else if (!(fabs(ref - pred) <= tau)) {
+        if (col) s_fc[atomicAdd(&cnt[1], 1)] = idx;
+        else s_fr[atomicAdd(&cnt[0], 1)] = idx;
+      }
+    }
+    __syncthreads();
+  }
+  if (CK >= 1) {
+    const int nr = cnt[0], nc = cnt[1];
+    // flagged intersections (or whole flagged segments when one side is empty
+    // or there are more than 64): recompute in FP64 from the original operands
+    const int ncand = (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) ? nr * nc
+                      : (nr + nc > 0) ? (nr * nJt + nc * mI) : 0;
+    for (int e = warp; e < ncand; e += 8) {
+      int il, jl;
+      if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) { il = s_fr[e / nc]; jl = s_fc[e % nc]; }
+      else if (e < nr * nJt) { il = s_fr[e / nJt]; jl = e % nJt; }
+      else { il = (e - nr * nJt) % mI; jl = s_fc[(e - nr * nJt) / mI]; }
+      const long long gi = i0 + il, gj = j0 + jl;
+      double dot = 0.0, ab = 0.0;
+      for (long long k = lane; k < p.K; k += 32) {
+        const double av = sp_glob_a<TA, TB>(p, gi, k), bv = sp_glob_b<TA, TB>(p, k, gj);
+        dot = fma(av, bv, dot);
+        ab = fma(fabs(av), fabs(bv), ab);
+      }
+      dot = warp_sum(dot);
+      ab = warp_sum(ab);
+      if (lane == 0) {
+        const double c = use_c ? p.C[gi + gj * p.ldc] : 0.0;
+        const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
+        // the emulated value may differ from the FP64 one by the splitting error
+        // (plain BF16: the input rounding) plus FP64 roundings
+        const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
+        const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
+                                           : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
+        const double te = fabs(p.alpha) * split_err +
+                          2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
+        const double old = sC[jl * SP_BM + il];
+        if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
+          atomicAdd(&cnt[2], 1);
+          const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
+          if ((long long)q < p.loc_cap) {
+            DevLoc L;
+            L.row = gi; L.col = gj; L.tile = tile; L.kind = 0; L.delta = old - nv;
+            p.loc[q] = L;
+          }
+        }
+        sC[jl * SP_BM + il] = nv;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      DevReport *r = p.rep;
+      if (cnt[0]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[0]);
+      if (cnt[1]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[1]);
+      if (cnt[2]) { atomicAdd(&r->detected, (unsigned long long)cnt[2]); atomicAdd(&r->corrected, (unsigned long long)cnt[2]); }
+      if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
+    }
+  }
+  // store (plain coalesced stores: rows of the tile are contiguous in C)
+  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
+    const int il = e & 127, jl = e >> 7;
+    if (il < mI && jl < nJt) p.C[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldc] = sC[e];
+  }
 }
 
 // One CTA per 128 x 128 tile; 8 warps as 2 (rows) x 4 (columns), warp tile
@@ -365,7 +427,6 @@ __global__ void __launch_bounds__(256, 1)
         sC[cj * SP_BM + ri] = acc64[a][b][c];
       }
   __syncthreads();
-  double *s_ref = s_r, *s_pred = s_r + 128, *s_tau = s_r + 256;
   if (FT) {
     // reference sums of the accumulators, one per thread: column (tid < 128) or row
     double ref = 0.0;
@@ -392,115 +453,7 @@ __global__ void __launch_bounds__(256, 1)
     }
   }
   __syncthreads();
-  // scale to the output: out = alpha * 2^(eA_i + eB_j) * acc + beta * C  (C read only if beta != 0)
-  const bool use_c = p.beta != 0.0;
-  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
-    const int il = e & 127, jl = e >> 7;
-    if (il < mI && jl < nJt) {
-      const long long gi = i0 + il, gj = j0 + jl;
-      const double v = ldexp(sC[e], p.eA[gi] + p.eB[gj]);
-      sC[e] = use_c ? fma(p.alpha, v, p.beta * p.C[gi + gj * p.ldc]) : p.alpha * v;
-    }
-  }
-  __syncthreads();
-  if (CK == 2) {
-    // FP64 checksums: reference sums of the scaled output tile against
-    // alpha * (acs x op(B) or op(A) x bcs) + beta * (sums of C_in)
-    const int idx = tid & 127;
-    const bool col = tid < 128;
-    const bool valid = col ? (idx < nJt) : (idx < mI);
-    if (valid) {
-      double ref = 0.0, cs = 0.0, ca = 0.0, sig = 0.0;
-      if (col) {
-        const long long gj = j0 + idx;
-        for (int i = 0; i < mI; ++i) {
-          ref += sC[idx * SP_BM + i];
-          sig += ldexp(1.0, p.eA[i0 + i]);
-          if (use_c) { const double c = p.C[(i0 + i) + gj * p.ldc]; cs += c; ca += fabs(c); }
-        }
-        sig *= ldexp(1.0, p.eB[gj]);
-      } else {
-        const long long gi = i0 + idx;
-        for (int j = 0; j < nJt; ++j) {
-          ref += sC[j * SP_BM + idx];
-          sig += ldexp(1.0, p.eB[j0 + j]);
-          if (use_c) { const double c = p.C[gi + (long long)(j0 + j) * p.ldc]; cs += c; ca += fabs(c); }
-        }
-        sig *= ldexp(1.0, p.eA[gi]);
-      }
-      const double P = col ? p.P1[(long long)I + (long long)(j0 + idx) * p.ldp1]
-                           : p.P2[(long long)(i0 + idx) + (long long)J * p.ldp2];
-      const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
-      const double S64 = col ? p.bcolabs[j0 + idx] * p.aabsmax[I] : p.arowabs[i0 + idx] * p.babsmax[J];
-      const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
-      const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
-      const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) +
-                         split_err + n * 0x1p-1021;
-      if (!isfinite(pred) || !isfinite(tau)) atomicAdd(&cnt[4], 1);
-      else if (!(fabs(ref - pred) <= tau)) {
-        if (col) s_fc[atomicAdd(&cnt[1], 1)] = idx;
-        else s_fr[atomicAdd(&cnt[0], 1)] = idx;
-      }
-    }
-    __syncthreads();
-  }
-  if (CK >= 1) {
-    const int nr = cnt[0], nc = cnt[1];
-    // flagged intersections (or whole flagged segments when one side is empty
-    // or there are more than 64): recompute in FP64 from the original operands
-    const int ncand = (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) ? nr * nc
-                      : (nr + nc > 0) ? (nr * nJt + nc * mI) : 0;
-    for (int e = warp; e < ncand; e += 8) {
-      int il, jl;
-      if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) { il = s_fr[e / nc]; jl = s_fc[e % nc]; }
-      else if (e < nr * nJt) { il = s_fr[e / nJt]; jl = e % nJt; }
-      else { il = (e - nr * nJt) % mI; jl = s_fc[(e - nr * nJt) / mI]; }
-      const long long gi = i0 + il, gj = j0 + jl;
-      double dot = 0.0, ab = 0.0;
-      for (long long k = lane; k < p.K; k += 32) {
-        const double av = sp_glob_a<TA, TB>(p, gi, k), bv = sp_glob_b<TA, TB>(p, k, gj);
-        dot = fma(av, bv, dot);
-        ab = fma(fabs(av), fabs(bv), ab);
-      }
-      dot = warp_sum(dot);
-      ab = warp_sum(ab);
-      if (lane == 0) {
-        const double c = use_c ? p.C[gi + gj * p.ldc] : 0.0;
-        const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
-        // the emulated value may differ from the FP64 one by the splitting error
-        // (plain BF16: the input rounding) plus FP64 roundings
-        const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
-        const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
-                                           : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
-        const double te = fabs(p.alpha) * split_err +
-                          2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
-        const double old = sC[jl * SP_BM + il];
-        if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
-          atomicAdd(&cnt[2], 1);
-          const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
-          if ((long long)q < p.loc_cap) {
-            DevLoc L;
-            L.row = gi; L.col = gj; L.tile = tile; L.kind = 0; L.delta = old - nv;
-            p.loc[q] = L;
-          }
-        }
-        sC[jl * SP_BM + il] = nv;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      DevReport *r = p.rep;
-      if (cnt[0]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[0]);
-      if (cnt[1]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[1]);
-      if (cnt[2]) { atomicAdd(&r->detected, (unsigned long long)cnt[2]); atomicAdd(&r->corrected, (unsigned long long)cnt[2]); }
-      if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
-    }
-  }
-  // store (plain coalesced stores: rows of the tile are contiguous in C)
-  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
-    const int il = e & 127, jl = e >> 7;
-    if (il < mI && jl < nJt) p.C[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldc] = sC[e];
-  }
+  split_tile_finish<TA, TB, CK>(p, sC, s_fr, s_fc, cnt, tile, I, J);
 }
 
 }  // namespace ftg

@@ -84,6 +84,8 @@ def lib():
         L.ftgemm_set_panel_check.restype = ctypes.c_int
         L.ftgemm_set_splitk.argtypes = [ctypes.c_int]
         L.ftgemm_set_splitk.restype = ctypes.c_int
+        L.ftgemm_set_split_engine.argtypes = [ctypes.c_int]
+        L.ftgemm_set_split_engine.restype = ctypes.c_int
         L.ftgemm_timing.argtypes = [ctypes.c_int]
         L.ftgemm_timing.restype = ctypes.c_int
         L.ftgemm_timing_read.argtypes = [ctypes.POINTER(_dbl), ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]
@@ -275,6 +277,11 @@ def ftgemm_set_panel_check(kslabs: int) -> int:
 def ftgemm_set_splitk(nsplit: int) -> int:
     """0 automatic k-splitting, 1 never, n >= 2 force n splits."""
     return lib().ftgemm_set_splitk(nsplit)
+
+
+def ftgemm_set_split_engine(engine: int) -> int:
+    """Split precision: 0 tcgen05 tensor cores (mma.sync for ft=1), 1 mma.sync."""
+    return lib().ftgemm_set_split_engine(engine)
 
 
 def ftgemm_launch_count() -> int:

@@ -29,8 +29,10 @@ def ft():
     from paper_2305_02444_gb300 import ftgemm
     ftgemm.lib()
     ftgemm.ftgemm_set_injection(mode=0)
+    ftgemm.ftgemm_set_split_engine(0)
     yield ftgemm
     ftgemm.ftgemm_set_injection(mode=0)
+    ftgemm.ftgemm_set_split_engine(0)
 
 
 def wbits(K):
@@ -185,3 +187,85 @@ def test_fp64_checksums_see_what_fp32_checksums_miss(ft, orc):
             assert sorted(l[:2] for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)
     assert detected[2] == len(flips)
     assert detected[1] < len(flips) // 2
+
+
+def run_engine(ft, engine, *a, **kw):
+    assert ft.ftgemm_set_split_engine(engine) == 0
+    try:
+        return run(ft, *a, **kw)
+    finally:
+        ft.ftgemm_set_split_engine(0)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")])
+@pytest.mark.parametrize("M,N,K,S,ck", [(300, 260, 200, 7, 0), (130, 258, 1000, 8, 2), (256, 384, 640, 3, 2),
+                                        (1, 129, 65, 4, 0), (2, 130, 5000, 11, 2)])
+def test_tcgen05_and_mma_sync_give_the_same_bits(ft, orc, ta, tb, M, N, K, S, ck):
+    """The emulated pair products are exact integers in FP32 on both engines and
+    the FP64 fold has the same order and arithmetic: identical outputs.  (FP64
+    checksums need even leading dimensions: those shapes are even.)"""
+    A, B, C, ar, br = problem(ta, tb, M, N, K, seed=M + N + K)
+    g_tc, rep_tc = run_engine(ft, 0, ta, tb, M, N, K, 1.5, 0.5, A, B, C, ar, br, S, ftflag=ck)
+    g_mm, rep_mm = run_engine(ft, 1, ta, tb, M, N, K, 1.5, 0.5, A, B, C, ar, br, S, ftflag=ck)
+    np.testing.assert_array_equal(g_tc, g_mm)
+    assert rep_tc["flagged_rows"] == rep_mm["flagged_rows"] == 0
+    assert rep_tc["flagged_cols"] == rep_mm["flagged_cols"] == 0
+    ref, E = orc.gemm(ta, tb, 1.5, A[:, :ar].T.numpy(), B[:, :br].T.numpy(), 0.5, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales(ta, tb, A, B, ar, br)
+    split = 1.5 * np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    assert np.all(np.abs(g_tc - ref) <= orc.parity_tol(K, E) + split)
+
+
+def test_tcgen05_several_k_chunks(ft, orc):
+    """K = 18000 > 17408 products per exact FP32 chunk at w = 5: every pair is
+    folded in two chunks, through both tensor-memory accumulators."""
+    M, N, K, S = 130, 140, 18000, 3
+    A, B, C, ar, br = problem("N", "N", M, N, K, seed=5)
+    g_tc, _ = run_engine(ft, 0, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
+    g_mm, _ = run_engine(ft, 1, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
+    np.testing.assert_array_equal(g_tc, g_mm)
+    ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 1.0, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales("N", "N", A, B, ar, br)
+    split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    assert np.all(np.abs(g_tc - ref) <= orc.parity_tol(K, E) + split)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
+def test_tcgen05_plain_bf16(ft, orc, ta, tb):
+    M, N, K = 300, 200, 700
+    A, B, C, ar, br = problem(ta, tb, M, N, K, seed=41)
+    got, rep = run_engine(ft, 0, ta, tb, M, N, K, 1.0, 1.0, A, B, C, ar, br, 0, ftflag=0)
+    ref, E = orc.gemm(ta, tb, 1.0, A[:, :ar].T.numpy(), B[:, :br].T.numpy(), 1.0, C.T.numpy(), want_E=True)
+    opA, opB, _, _ = scales(ta, tb, A, B, ar, br)
+    absab = np.abs(opA) @ np.abs(opB)
+    tol = (2.0 ** -7 + 2.01 * (K + 2) * 2.0 ** -24) * absab + orc.parity_tol(K, E)
+    assert np.all(np.abs(got - ref) <= tol)
+    rel = np.abs(got - ref).max() / np.abs(ref).max()
+    assert 1e-6 < rel < 1e-2
+
+
+def test_tcgen05_injection_log_and_correction(ft, orc):
+    """Flips of the tensor-memory FP64 accumulators after chosen slice pairs
+    (first, middle, last of 36; one element in each lane quadrant): logged
+    with the value they changed, detected by the FP64 checksums, located and
+    corrected."""
+    M, N, K, S = 256, 256, 512, 8
+    A, B, C, ar, br = problem("N", "N", M, N, K, seed=19)
+    flips = [(5, 6, 0, 62), (100, 200, 20, 62), (250, 3, 35, 62), (70, 129, 35, 52)]
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        got, rep = run_engine(ft, 0, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
+        log = ft.ftgemm_injection_log()
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    assert [L["applied"] for L in log] == [1] * len(flips)
+    for L, (i, j, q, bit) in zip(log, flips):
+        assert (L["row"], L["col"], L["kstep"], L["bit"]) == (i, j, q, bit)
+        before, after = np.float64(L["before"]), np.float64(L["after"])
+        assert before.view(np.int64) ^ after.view(np.int64) == np.int64(1) << bit
+    ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 1.0, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales("N", "N", A, B, ar, br)
+    split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+    assert rep["detected"] == len(flips)
+    assert sorted(l[:2] for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)

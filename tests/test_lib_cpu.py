@@ -80,3 +80,10 @@ def test_host_settings_and_strings(ft):
     assert "timeout" in ft.ftgemm_strerror(ft.ERR_TIMEOUT) or "wait" in ft.ftgemm_strerror(ft.ERR_TIMEOUT)
     assert ft.ftgemm_strerror(0) == "success"
     assert ft.ftgemm_launch_count() == 0
+
+
+def test_split_engine_knob_codes(ft):
+    assert ft.ftgemm_set_split_engine(2) == -1
+    assert ft.ftgemm_set_split_engine(-1) == -1
+    assert ft.ftgemm_set_split_engine(1) == 0
+    assert ft.ftgemm_set_split_engine(0) == 0
