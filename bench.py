@@ -401,6 +401,9 @@ def split(args):
         forms += [(f"bf16_plain{sfx}", 0, 0, eng)]
     forms += [(f"emulated_S{S}_fp32ck_mma", S, 1, "mma") for S in args.split_slices] + \
         [("bf16_plain_fp32ck_mma", 0, 1, "mma")]
+    if args.split_forms:
+        keep = set(x for x in args.split_forms.split(",") if x)
+        forms = [f for f in forms if f[0] in keep]
     peaks = measured_peaks()
     for name, S, ck, eng in forms:
         if eng is not None:
@@ -453,7 +456,7 @@ def split(args):
             res[name]["kernel_bf16_tflops"] = tf
             res[name]["kernel_frac_of_bf16_peak"] = tf / peaks["bf16_tflops"]
         print(json.dumps({name: res[name]}), flush=True)
-    base = res["fp64_dfma"]["tflops_fp64_equiv"]
+    base = res["fp64_dfma"]["tflops_fp64_equiv"] if "fp64_dfma" in res else float("nan")
     line = {"metric": "split-precision FT-GEMM TFLOP/s (FP64-equivalent, 2MNK) and max error vs FP64 oracle",
             "config": {"workload": f"split_{n}cubed_loguniform1e-3to1e3_flips1per64tiles", "rows_checked": len(rows)},
             "results": res, "speedup_vs_fp64_dfma": {k: v["tflops_fp64_equiv"] / base for k, v in res.items()},
@@ -481,6 +484,7 @@ def main():
     ap.add_argument("--split-slices", default="7,9,11", help="slice counts for --split")
     ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
     ap.add_argument("--split-engine", default="tc,mma", help="split engines: tc (tcgen05), mma (mma.sync)")
+    ap.add_argument("--split-forms", default="", help="comma list of form names to run (default: all)")
     args = ap.parse_args()
     set_size(args.size)
     if args.sweep:

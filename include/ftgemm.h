@@ -313,11 +313,13 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
 int ftgemm_set_splitk(int nsplit);
 
 /* Engine of ftgemm_d_split (results: the same bits for the emulated forms,
- * within the same bound for the plain BF16 form): 0 (default) runs the slice
+ * within the same bound for the plain BF16 form).  0 (default): the slice
  * products on the tcgen05 tensor cores (FP32 accumulators and the FP64 fold
- * in tensor memory) when ft is 0 or 2 and on the mma.sync kernel when ft is 1
- * (its FP32 checksums are summed from the staged slices on the CUDA cores);
- * 1 runs every call on the mma.sync kernel.  Returns -1 for another value. */
+ * in tensor memory) in 2 x 2 thread-block clusters that share each A and B
+ * slab through TMA multicast, when ft is 0 or 2; 2: the same kernel with one
+ * CTA per tile and no cluster; 1: every call on the mma.sync kernel.  ft = 1
+ * (FP32 checksums summed from the staged slices on the CUDA cores) always
+ * runs on the mma.sync kernel.  Returns -1 for another value. */
 int ftgemm_set_split_engine(int engine);
 
 /* Per-k-panel verification (FT-BLAS style; FT-GEMM blocks K by K_C, §2.1):

@@ -116,6 +116,10 @@ struct SplitParams {
   const double *P1, *P2;        // nI x N (ld ldp1), M x nJ (ld ldp2)
   long long ldp1, ldp2;
   const double *arowabs, *aabsmax, *bcolabs, *babsmax;
+  // P1 / P2 computed by the same emulated product (else null): the
+  // power-of-two scales of the checksum operands' rows (tile rows I of the
+  // column sums of op(A), tile columns J of the row sums of op(B))
+  const int *ePA, *ePB;
 };
 
 

@@ -42,8 +42,8 @@ cudaError_t launch_panel_tt(bool, const CUtensorMap &, const CUtensorMap &, cons
                             cudaStream_t);
 cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s);
-cudaError_t launch_split_tc(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
-                            const SplitParams &p, cudaStream_t s);
+cudaError_t launch_split_tc(bool ta, bool tb, int ck, int cluster, const CUtensorMap &a, const CUtensorMap &b,
+                            const CUtensorMap &b2, const SplitParams &p, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
                            int S, int w, int plain, void *out, cudaStream_t s);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
@@ -81,6 +81,7 @@ struct Workspace {
   Buf W, wpc, wpr;          // split-K partial tiles and predicted-checksum partials
   Buf uC, uccs, uccsa, ucrs, ucrsa, uP1, uP2;  // unfused ablation: copy of C, C sums, skinny GEMMs
   Buf spA, spB, spEA, spEB;  // split precision: bf16 slices and row/column exponents
+  Buf spPA, spPB, spEPA, spEPB;  // slices / exponents of the checksum operands (tcgen05 engine, ft = 2)
   int nsm = 0;              // SM count
   Buf pin;                  // pinned host staging (report, loc, injection upload)
   // the last injected call, for ftgemm_injection_log
@@ -214,7 +215,9 @@ bool tma_ok(const void *p, long long ld) {
 
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
-int g_split_engine = 0;  // split precision: 0 tcgen05 (FP32 checksums: mma.sync), 1 mma.sync
+// split precision: 0 tcgen05 (default cluster shape), 1 mma.sync, 2 / 3 / 4 tcgen05 in clusters of 1 / 2 / 4 CTAs
+int g_split_engine = 0;
+constexpr int SPLIT_DEFAULT_CLUSTER = 1;
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
 int g_panel = 0;   // verify the accumulators every g_panel k-slabs (0: only at the end of the tile)
 
@@ -802,7 +805,7 @@ int ftgemm_set_panel_check(int kslabs) {
 
 int ftgemm_set_split_engine(int engine) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (engine < 0 || engine > 1) return -1;
+  if (engine < 0 || engine > 4) return -1;
   g_split_engine = engine;
   return 0;
 }
@@ -1498,12 +1501,12 @@ int ftgemm_batched(int64_t count, const char *transA, const char *transB, const 
 // Split-precision FT-GEMM (BF16 tensor cores; see ftgemm_split.cuh).
 namespace {
 
-int make_map_slices(CUtensorMap *m, const void *ptr, long long Kp, long long R, long long S) {
+int make_map_slices(CUtensorMap *m, const void *ptr, long long Kp, long long R, long long S, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return FTGEMM_ERR_TENSORMAP;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)S};
   cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)SP_BK, (cuuint32_t)SP_BM, 1};
+  cuuint32_t box[3] = {(cuuint32_t)SP_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1555,8 +1558,15 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
       launch_slicing(B, ldb, tb_t ? 0 : 1, N, K, Kp, (int *)w.spEB.p, S, wbits, plain, w.spB.p, s) != cudaSuccess)
     return FTGEMM_ERR_CUDA;
   g_launches += plain ? 2 : 4;
-  CUtensorMap mA, mB;
-  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S))) return rc;
+  // tcgen05 kernel (ft 0 / 2): 2 x 2 clusters load 64-row halves; otherwise whole 128-row slabs
+  const bool tc = g_split_engine != 1 && ft != 1;
+  const int cl = !tc ? 1 : g_split_engine == 0 ? SPLIT_DEFAULT_CLUSTER : g_split_engine == 3 ? 2
+                 : g_split_engine == 4 ? 4 : 1;
+  const int boxA = cl == 1 ? SP_BM : SP_BM / 2, boxB = cl == 4 ? SP_BM / 2 : SP_BM;
+  CUtensorMap mA, mB, mB2;
+  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S, boxA)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S, boxB)))
+    return rc;
+  mB2 = mB;
 
   SplitParams p;
   memset(&p, 0, sizeof(p));
@@ -1573,6 +1583,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   p.rep = (DevReport *)w.rep.p; p.loc = (DevLoc *)w.loc.p; p.loc_cap = LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
   p.verify = ft;
+  cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   if (ft == 2) {
     // FP64 predicted checksums of the 128 x 128 tiles from the original operands
     const long long Kq = (K + BK - 1) / BK * BK, ldp1 = (nI + 1) & ~1LL, ldp2 = (M + 1) & ~1LL;
@@ -1586,17 +1597,46 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
                          (double *)w.arowabs.p, (double *)w.bcs.p, (double *)w.babsmax.p, (double *)w.bcolabs.p,
                          w, s)))
       return rc;
-    if ((rc = gemm_impl('T', transB, nI, N, K, 1.0, (const double *)w.acs.p, Kq, B, ldb, 0.0, (double *)w.uP1.p,
-                        ldp1, nullptr, s, false)))
-      return rc;
-    if ((rc = gemm_impl(transA, 'N', M, nJ, K, 1.0, A, lda, (const double *)w.bcs.p, Kq, 0.0, (double *)w.uP2.p,
-                        ldp2, nullptr, s, false)))
-      return rc;
     p.P1 = (const double *)w.uP1.p; p.ldp1 = ldp1; p.P2 = (const double *)w.uP2.p; p.ldp2 = ldp2;
+    if (tc) {
+      // P1 = acs^T op(B) and P2 = op(A) bcs by the same emulated product on the
+      // tensor cores: slice the checksum operands (rows I of acs^T, columns J
+      // of bcs), reuse op(B)'s and op(A)'s slices
+      if (ensure(w.spPA, (size_t)S * nI * Kp * 2) || ensure(w.spPB, (size_t)S * nJ * Kp * 2) ||
+          ensure(w.spEPA, sizeof(int) * nI) || ensure(w.spEPB, sizeof(int) * nJ))
+        return FTGEMM_ERR_NOMEM;
+      if (launch_slicing((const double *)w.acs.p, Kq, 1, nI, K, Kp, (int *)w.spEPA.p, S, wbits, 0, w.spPA.p, s) !=
+              cudaSuccess ||
+          launch_slicing((const double *)w.bcs.p, Kq, 1, nJ, K, Kp, (int *)w.spEPB.p, S, wbits, 0, w.spPB.p, s) !=
+              cudaSuccess)
+        return FTGEMM_ERR_CUDA;
+      g_launches += 4;
+      CUtensorMap mPA, mPB;
+      if ((rc = make_map_slices(&mPA, w.spPA.p, Kp, nI, S, boxA)) ||
+          (rc = make_map_slices(&mPB, w.spPB.p, Kp, nJ, S, boxB)))
+        return rc;
+      SplitParams q1 = p, q2 = p;
+      q1.M = nI; q1.nI = (int)((nI + SP_BM - 1) / SP_BM);
+      q1.eA = (const int *)w.spEPA.p; q1.C = (double *)w.uP1.p; q1.ldc = ldp1;
+      q2.N = nJ; q2.nJ = (int)((nJ + SP_BN - 1) / SP_BN);
+      q2.eB = (const int *)w.spEPB.p; q2.C = (double *)w.uP2.p; q2.ldc = ldp2;
+      for (SplitParams *q : {&q1, &q2}) { q->alpha = 1.0; q->beta = 0.0; q->verify = 0; q->inj = 0; }
+      if (launch_split_tc(false, false, 0, cl, mPA, mB, mB, q1, s) != cudaSuccess ||
+          launch_split_tc(false, false, 0, cl, mA, mPB, mPB, q2, s) != cudaSuccess)
+        return FTGEMM_ERR_CUDA;
+      g_launches += 2;
+      p.ePA = (const int *)w.spEPA.p; p.ePB = (const int *)w.spEPB.p;
+    } else {
+      if ((rc = gemm_impl('T', transB, nI, N, K, 1.0, (const double *)w.acs.p, Kq, B, ldb, 0.0, (double *)w.uP1.p,
+                          ldp1, nullptr, s, false)))
+        return rc;
+      if ((rc = gemm_impl(transA, 'N', M, nJ, K, 1.0, A, lda, (const double *)w.bcs.p, Kq, 0.0,
+                          (double *)w.uP2.p, ldp2, nullptr, s, false)))
+        return rc;
+    }
     p.arowabs = (const double *)w.arowabs.p; p.aabsmax = (const double *)w.aabsmax.p;
     p.bcolabs = (const double *)w.bcolabs.p; p.babsmax = (const double *)w.babsmax.p;
   }
-  cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   bool inj = false;
   if (ft) {
     Params tmp;
@@ -1609,8 +1649,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  const bool tc = g_split_engine == 0 && ft != 1;
-  if ((tc ? launch_split_tc(ta_t, tb_t, ft, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
+  if ((tc ? launch_split_tc(ta_t, tb_t, ft, cl, mA, mB, mB2, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
       cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);

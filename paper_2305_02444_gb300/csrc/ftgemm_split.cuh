@@ -115,6 +115,9 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
       const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
       const double S64 = col ? p.bcolabs[j0 + idx] * p.aabsmax[I] : p.arowabs[i0 + idx] * p.babsmax[J];
       const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
+      // splitting error of the reference sum, plus that of the predicted
+      // checksum when it is an emulated product as well
+      if (p.ePA) sig += col ? ldexp(1.0, p.ePA[I] + p.eB[j0 + idx]) : ldexp(1.0, p.eA[i0 + idx] + p.ePB[J]);
       const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
       const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) +
                          split_err + n * 0x1p-1021;

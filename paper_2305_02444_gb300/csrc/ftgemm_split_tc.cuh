@@ -9,11 +9,17 @@
 //   warp 1   MMA issuer: 4 tcgen05.mma (M 128, N 128, K 16) per slab into
 //            one of two FP32 accumulators (tensor-memory columns 0..255),
 //            a commit per slab frees the ring stage, a commit per pair (or
-//            k-chunk) hands the accumulator to the folders;
+//            k-chunk) hands the accumulator to the folders.  It never polls
+//            memory (a poll waits behind its queued MMAs and drains the
+//            tensor pipe: measured 64 -> ~130 cycles per MMA);
 //   warp 2   allocates / frees the 512 tensor-memory columns;
+//   warp 3   waiter: polls the ring's full barriers and the accumulators'
+//            release, and hands each slab to warp 1 at a named barrier;
 //   warps 4-7 folders: thread = tile row; acc64 += 2^-w(s+t+2) * acc32 with
 //            the FP64 accumulators in columns 256..511 (two 32-bit columns
-//            per element), overlapped with the next pair's MMAs.
+//            per element), overlapped with the next pair's MMAs; the scaled
+//            FP32 value is built with integer operations, so that a fold
+//            costs one FP64 add per element.
 // The fold order, weights and FP64 arithmetic are those of the mma.sync
 // kernel (the pair products are exact integers in FP32), so both kernels
 // produce the same bits for the emulated forms.  The end of the tile (scale,
@@ -28,19 +34,51 @@
 
 namespace ftg {
 
-constexpr int TC_STAGES = 6;
+#ifndef FTG_TC_STAGES
+#define FTG_TC_STAGES 7  // ring depth (a build-time tuning knob; 7 x 32 KiB is what fits)
+#endif
+#ifndef FTG_TC_GROUP
+#define FTG_TC_GROUP 8  // tile rows per rasterization group
+#endif
+constexpr int TC_STAGES = FTG_TC_STAGES;
+constexpr int TC_GROUP = FTG_TC_GROUP;
 constexpr int TC_TMEM_COLS = 512;
 constexpr int TC_ACC64_COL = 256;
+constexpr int TC_HANDOFF_BAR = 3;  // named barrier of the waiter -> MMA-issuer handoff (warps 1 and 3)
 constexpr uint32_t TC_IDESC = tc_idesc_bf16_f32(SP_BM, SP_BN);
 constexpr int TC_SMEM_BYTES = TC_STAGES * SP_STAGE_BYTES + 2 * 128 * 4 + 64 * 4 + (2 * TC_STAGES + 5) * 8 + 16 +
                               1024;
 static_assert(TC_STAGES * SP_STAGE_BYTES >= SP_BM * SP_BN * 8, "the ring holds the FP64 tile at the end");
 
-template <bool TA, bool TB, int CK>
+// 2^-sh * f as a double, for f an integer-valued float (the exact FP32 result
+// of a slice-pair product) and 0 <= sh < 800: f's sign, exponent - sh and
+// mantissa moved into the FP64 fields with integer operations (exact, and
+// off the FP64 pipe).
+__device__ __forceinline__ double scaled_exact_f32(uint32_t fb, int sh) {
+  const uint32_t ef = (fb >> 23) & 0xFFu;
+  const uint32_t keep = ef ? 0xFFFFFFFFu : 0u;  // +-0 stays +-0
+  const uint32_t hi = (fb & 0x80000000u) | (keep & (((ef + (1023u - 127u) - (uint32_t)sh) << 20) |
+                                                    ((fb & 0x7FFFFFu) >> 3)));
+  return tc_pack_f64((fb & 7u) << 29, hi);
+}
+
+// CL = 1: one CTA per tile, each loading its own slabs (tmA / tmB with
+// 128-row boxes).  CL = 2: 1 x 2 clusters (tiles (I, J0 + rank)); each CTA
+// loads one 64-row half of the shared A slab (tmA with 64-row boxes) and
+// multicasts it to both, and its whole B slab (tmB2, 128-row boxes): a
+// quarter fewer L2 reads; empty barriers count the two CTAs.  CL = 4: 2 x 2 clusters of tiles (I0 + a, J0 + b), rank
+// a + 2b; the A slab of a tile row is fetched once for the two CTAs that
+// share it (each loads one 64-row half and multicasts it to both), the B slab
+// likewise (tmA / tmB with 64-row boxes): half the L2 reads per CTA.  A ring
+// stage may then be refilled only when the CTA and the two partners writing
+// into it have consumed it: the MMA commits arrive at the empty barriers of
+// all three (count 3).
+template <bool TA, bool TB, int CK, int CL>
 __global__ void __launch_bounds__(256, 1)
     ftsplit_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const __grid_constant__ SplitParams p) {
+                      const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ SplitParams p) {
   static_assert(CK == 0 || CK == 2, "FP32 checksums are taken by the mma.sync kernel");
+  static_assert(CL == 1 || CL == 2 || CL == 4, "clusters of 1, 1 x 2 or 2 x 2 tiles");
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -53,7 +91,33 @@ __global__ void __launch_bounds__(256, 1)
   const uint32_t accf0 = empty0 + 8 * TC_STAGES, acce0 = accf0 + 16, done_bar = acce0 + 16;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x, I = tile % p.nI, J = tile / p.nI;
+  // grouped rasterization: consecutive CTAs sweep TC_GROUP tile rows column
+  // by column, so that the CTAs resident at one time cover a compact block of
+  // tiles and share the slices' slabs in L2
+  int I, J;
+  uint32_t rank = 0;
+  if (CL == 1) {
+    const int b = blockIdx.x, per = TC_GROUP * p.nJ, g = b / per, r = b % per;
+    const int rows = min(TC_GROUP, p.nI - g * TC_GROUP);
+    I = g * TC_GROUP + r % rows;
+    J = r / rows;
+  } else if (CL == 2) {  // 1 x 2 blocks: the two tiles of a pair of columns share the A slab
+    rank = cluster_rank();
+    const int nCJ = (p.nJ + 1) / 2;
+    const int b = blockIdx.x / 2, per = TC_GROUP * nCJ, g = b / per, r = b % per;
+    const int rows = min(TC_GROUP, p.nI - g * TC_GROUP);
+    I = g * TC_GROUP + r % rows;
+    J = 2 * (r / rows) + (int)rank;
+  } else {  // the same order over 2 x 2 blocks of tiles (the grid is padded to even tile counts)
+    rank = cluster_rank();
+    const int nCI = (p.nI + 1) / 2, nCJ = (p.nJ + 1) / 2, G2 = max(1, TC_GROUP / 2);
+    const int b = blockIdx.x / 4, per = G2 * nCJ, g = b / per, r = b % per;
+    const int rows = min(G2, nCI - g * G2);
+    I = 2 * (g * G2 + r % rows) + (int)(rank & 1);
+    J = 2 * (r / rows) + (int)(rank >> 1);
+  }
+  const bool valid = I < p.nI && J < p.nJ;  // padding tiles of a cluster only help load
+  const int tile = valid ? I + J * p.nI : 0;  // injection and location records number tiles column-major
   const int i0 = I * SP_BM, j0 = J * SP_BN;
   int *err = &p.rep->err;
   const unsigned long long limit = p.wait_limit_ns;
@@ -62,7 +126,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int c = 0; c < 8; ++c) cnt[c] = 0;
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, CL == 1 ? 1 : CL == 2 ? 2 : 3);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
@@ -72,13 +136,15 @@ __global__ void __launch_bounds__(256, 1)
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
+    if (CL == 2) prefetch_tmap(&tmB2);
   }
   if (warp == 2) {
     tmem_alloc(smem_u32(s_tmem), TC_TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  if (CL > 1) cluster_sync();  // the partners' barriers exist before anything is multicast to them
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *s_tmem;
 
@@ -102,6 +168,29 @@ __global__ void __launch_bounds__(256, 1)
         if (*(volatile int *)&cnt[3]) break;
         const uint32_t sb = smem_u32(smem + st * SP_STAGE_BYTES), fb = full0 + 8 * st;
         mbar_arrive_expect_tx(fb, SP_STAGE_BYTES);
+        if (CL == 2) {
+          // my half of the A slab to both CTAs, my whole B slab to myself
+          tma_load_3d_mc(sb + (int)rank * (SP_A_BYTES / 2), &tmA, fb, slab * SP_BK, i0 + (int)rank * (SP_BM / 2),
+                         p.pair_s[pq], (uint16_t)3u);
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb + SP_A_BYTES),
+              "l"(reinterpret_cast<uint64_t>(&tmB2)), "r"(fb), "r"(slab * SP_BK), "r"(j0), "r"(p.pair_t[pq])
+              : "memory");
+          issued = step + 1;
+          continue;
+        }
+        if (CL == 4) {
+          // my half of the A slab to the CTAs of my tile row, my half of the
+          // B slab to those of my tile column
+          const int ha = (int)(rank >> 1), hb = (int)(rank & 1);
+          tma_load_3d_mc(sb + ha * (SP_A_BYTES / 2), &tmA, fb, slab * SP_BK, i0 + ha * (SP_BM / 2), p.pair_s[pq],
+                         (uint16_t)((1u << (rank & 1)) | (1u << ((rank & 1) + 2))));
+          tma_load_3d_mc(sb + SP_A_BYTES + hb * (SP_B_BYTES / 2), &tmB, fb, slab * SP_BK, j0 + hb * (SP_BN / 2),
+                         p.pair_t[pq], (uint16_t)(3u << (2 * (rank >> 1))));
+          issued = step + 1;
+          continue;
+        }
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb),
@@ -121,39 +210,64 @@ __global__ void __launch_bounds__(256, 1)
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      int step = 0, item = 0;
-      for (int pq = 0; pq < p.npairs && ok; ++pq) {
-        for (int c = 0; c < nchunks && ok; ++c, ++item) {
-          const int b = item & 1;
-          if (item >= 2 && !mbar_wait_bounded(acce0 + 8 * b, ((item >> 1) - 1) & 1, limit, err)) {
-            ok = false;
-            break;
-          }
+    // never waits on memory: every slab starts with the rendezvous with the
+    // waiter warp, which carries "stop" after a wait that gave up
+    int step = 0, item = 0;
+    bool stop = false;
+    for (int pq = 0; pq < p.npairs && !stop; ++pq) {
+      for (int c = 0; c < nchunks && !stop; ++c, ++item) {
+        const int b = item & 1;
+        const uint32_t dt = tbase + (uint32_t)(b * SP_BN);
+        const int s0 = c * chunk_slabs, s1 = min(nslab, s0 + chunk_slabs);
+        for (int slab = s0; slab < s1; ++slab, ++step) {
+          if (bar_red_or(TC_HANDOFF_BAR, 64, false)) { stop = true; break; }
           tc_fence_after();
-          const uint32_t dt = tbase + (uint32_t)(b * SP_BN);
-          const int s0 = c * chunk_slabs, s1 = min(nslab, s0 + chunk_slabs);
-          for (int slab = s0; slab < s1; ++slab, ++step) {
-            const int st = step % TC_STAGES;
-            if (!mbar_wait_bounded(full0 + 8 * st, (step / TC_STAGES) & 1, limit, err)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
+          const int st = step % TC_STAGES;
+          if (elect_one()) {
             const uint32_t a0 = smem_u32(smem + st * SP_STAGE_BYTES), b0 = a0 + SP_A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < SP_BK / 16; ++kk)
               tc_mma_bf16(dt, tc_desc_k128(a0 + 32 * kk), tc_desc_k128(b0 + 32 * kk), TC_IDESC,
                           (slab > s0 || kk > 0) ? 1u : 0u);
-            tc_commit(empty0 + 8 * st);
+            if (CL == 2) tc_commit_mc(empty0 + 8 * st, (uint16_t)3u);
+            else if (CL == 4)
+              tc_commit_mc(empty0 + 8 * st, (uint16_t)((1u << rank) | (1u << (rank ^ 1)) | (1u << (rank ^ 2))));
+            else tc_commit(empty0 + 8 * st);
+            if (slab + 1 == s1) tc_commit(accf0 + 8 * b);
           }
-          if (ok) tc_commit(accf0 + 8 * b);
+          __syncwarp();
         }
       }
-      if (!ok) atomicExch(&cnt[3], 1);
-      // every MMA issued above has completed before the tensor memory is freed
-      tc_commit(done_bar);
+    }
+    // every MMA issued above has completed before the tensor memory is freed
+    if (elect_one()) tc_commit(done_bar);
+    __syncwarp();
+    if (lane == 0) {
+      if (stop) atomicExch(&cnt[3], 1);
       mbar_wait_bounded(done_bar, 0, limit, err);
+    }
+  } else if (warp == 3) {
+    // ---------------------------------------------------------------- waiter
+    // waits (bounded) for each slab's data and, at an item's first slab, for
+    // the folders to have released the accumulator, then hands over
+    int step = 0, item = 0;
+    bool bad = false;
+    for (int pq = 0; pq < p.npairs && !bad; ++pq) {
+      for (int c = 0; c < nchunks && !bad; ++c, ++item) {
+        const int b = item & 1;
+        const int s0 = c * chunk_slabs, s1 = min(nslab, s0 + chunk_slabs);
+        for (int slab = s0; slab < s1; ++slab, ++step) {
+          int fail = 0;
+          if (lane == 0) {
+            if (slab == s0 && item >= 2 && !mbar_wait_bounded(acce0 + 8 * b, ((item >> 1) - 1) & 1, limit, err))
+              fail = 1;
+            const int st = step % TC_STAGES;
+            if (!fail && !mbar_wait_bounded(full0 + 8 * st, (step / TC_STAGES) & 1, limit, err)) fail = 1;
+          }
+          fail = __shfl_sync(0xffffffffu, fail, 0);
+          if (bar_red_or(TC_HANDOFF_BAR, 64, fail != 0)) { bad = true; break; }
+        }
+      }
     }
   } else if (warp >= 4) {
     // ---------------------------------------------------------------- folders
@@ -161,10 +275,11 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t trow = tbase + ((uint32_t)(fw * 32) << 16);
     const uint32_t t64 = trow + TC_ACC64_COL;
     int fptr = 0, fend = 0;
-    if (CK >= 1 && p.inj) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+    if (CK >= 1 && p.inj && valid) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
     int item = 0;
+    const bool plain = p.S == 0;
     for (int pq = 0; pq < p.npairs && ok; ++pq) {
-      const double wgt = ldexp(1.0, -p.w * (p.pair_s[pq] + p.pair_t[pq] + 2));
+      const int sh = p.w * (p.pair_s[pq] + p.pair_t[pq] + 2);  // the pair's weight is 2^-sh
       for (int c = 0; c < nchunks; ++c, ++item) {
         const int b = item & 1;
         int got = 1;
@@ -182,11 +297,22 @@ __global__ void __launch_bounds__(256, 1)
           } else {
             tmem_ld_x64(t64 + (uint32_t)(ch * 64), d);
           }
+          // acc64 += 2^-sh * acc32: one FP64 add (the same rounding as an FMA
+          // with the exact product); the plain BF16 form converts its FP32 sum
+          if (plain) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const double a = fma(wgt, (double)__uint_as_float(f[j]), tc_pack_f64(d[2 * j], d[2 * j + 1]));
-            d[2 * j] = tc_lo(a);
-            d[2 * j + 1] = tc_hi(a);
+            for (int j = 0; j < 32; ++j) {
+              const double a = tc_pack_f64(d[2 * j], d[2 * j + 1]) + (double)__uint_as_float(f[j]);
+              d[2 * j] = tc_lo(a);
+              d[2 * j + 1] = tc_hi(a);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const double a = tc_pack_f64(d[2 * j], d[2 * j + 1]) + scaled_exact_f32(f[j], sh);
+              d[2 * j] = tc_lo(a);
+              d[2 * j + 1] = tc_hi(a);
+            }
           }
           tmem_st_x64(t64 + (uint32_t)(ch * 64), d);
         }
@@ -228,6 +354,7 @@ __global__ void __launch_bounds__(256, 1)
   tc_fence_after();
   if (cnt[3]) {
     if (warp == 2) tmem_dealloc(tbase, TC_TMEM_COLS);
+    if (CL > 1) cluster_sync();  // no CTA leaves while a partner may still write into it
     return;
   }
   // the ring is free: stage the FP64 accumulators as a column-major tile
@@ -250,7 +377,8 @@ __global__ void __launch_bounds__(256, 1)
     tc_fence_after();
     tmem_dealloc(tbase, TC_TMEM_COLS);
   }
-  split_tile_finish<TA, TB, CK>(p, sC, s_fr, s_fc, cnt, tile, I, J);
+  if (valid) split_tile_finish<TA, TB, CK>(p, sC, s_fr, s_fc, cnt, tile, I, J);
+  if (CL > 1) cluster_sync();
 }
 
 }  // namespace ftg

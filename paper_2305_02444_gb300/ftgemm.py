@@ -280,7 +280,7 @@ def ftgemm_set_splitk(nsplit: int) -> int:
 
 
 def ftgemm_set_split_engine(engine: int) -> int:
-    """Split precision: 0 tcgen05 tensor cores (mma.sync for ft=1), 1 mma.sync."""
+    """Split precision: 0 tcgen05 in 2x2 clusters, 2 tcgen05 single CTAs (ft=1: mma.sync), 1 mma.sync."""
     return lib().ftgemm_set_split_engine(engine)
 
 

@@ -189,6 +189,9 @@ def test_fp64_checksums_see_what_fp32_checksums_miss(ft, orc):
     assert detected[1] < len(flips) // 2
 
 
+ENGINES = (0, 1, 2, 3, 4)   # default, mma.sync, tcgen05 in clusters of 1, 2, 4 CTAs
+
+
 def run_engine(ft, engine, *a, **kw):
     assert ft.ftgemm_set_split_engine(engine) == 0
     try:
@@ -205,11 +208,11 @@ def test_tcgen05_and_mma_sync_give_the_same_bits(ft, orc, ta, tb, M, N, K, S, ck
     the FP64 fold has the same order and arithmetic: identical outputs.  (FP64
     checksums need even leading dimensions: those shapes are even.)"""
     A, B, C, ar, br = problem(ta, tb, M, N, K, seed=M + N + K)
-    g_tc, rep_tc = run_engine(ft, 0, ta, tb, M, N, K, 1.5, 0.5, A, B, C, ar, br, S, ftflag=ck)
-    g_mm, rep_mm = run_engine(ft, 1, ta, tb, M, N, K, 1.5, 0.5, A, B, C, ar, br, S, ftflag=ck)
-    np.testing.assert_array_equal(g_tc, g_mm)
-    assert rep_tc["flagged_rows"] == rep_mm["flagged_rows"] == 0
-    assert rep_tc["flagged_cols"] == rep_mm["flagged_cols"] == 0
+    outs = {e: run_engine(ft, e, ta, tb, M, N, K, 1.5, 0.5, A, B, C, ar, br, S, ftflag=ck) for e in ENGINES}
+    g_tc = outs[0][0]
+    for e, (g, r) in outs.items():   # tcgen05 single CTAs / 1x2 / 2x2 clusters, mma.sync
+        np.testing.assert_array_equal(g, g_tc)
+        assert r["flagged_rows"] == 0 and r["flagged_cols"] == 0
     ref, E = orc.gemm(ta, tb, 1.5, A[:, :ar].T.numpy(), B[:, :br].T.numpy(), 0.5, C.T.numpy(), want_E=True)
     _, _, sa, sb = scales(ta, tb, A, B, ar, br)
     split = 1.5 * np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
@@ -218,12 +221,14 @@ def test_tcgen05_and_mma_sync_give_the_same_bits(ft, orc, ta, tb, M, N, K, S, ck
 
 def test_tcgen05_several_k_chunks(ft, orc):
     """K = 18000 > 17408 products per exact FP32 chunk at w = 5: every pair is
-    folded in two chunks, through both tensor-memory accumulators."""
+    folded in two chunks, through both tensor-memory accumulators; 130 x 140
+    is a 2 x 2 tile grid that the cluster form covers without padding."""
     M, N, K, S = 130, 140, 18000, 3
     A, B, C, ar, br = problem("N", "N", M, N, K, seed=5)
-    g_tc, _ = run_engine(ft, 0, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
-    g_mm, _ = run_engine(ft, 1, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
-    np.testing.assert_array_equal(g_tc, g_mm)
+    outs = {e: run_engine(ft, e, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)[0] for e in ENGINES}
+    g_tc = outs[0]
+    for g in outs.values():
+        np.testing.assert_array_equal(g, g_tc)
     ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 1.0, C.T.numpy(), want_E=True)
     _, _, sa, sb = scales("N", "N", A, B, ar, br)
     split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
@@ -244,7 +249,8 @@ def test_tcgen05_plain_bf16(ft, orc, ta, tb):
     assert 1e-6 < rel < 1e-2
 
 
-def test_tcgen05_injection_log_and_correction(ft, orc):
+@pytest.mark.parametrize("engine", [2, 3, 4])
+def test_tcgen05_injection_log_and_correction(ft, orc, engine):
     """Flips of the tensor-memory FP64 accumulators after chosen slice pairs
     (first, middle, last of 36; one element in each lane quadrant): logged
     with the value they changed, detected by the FP64 checksums, located and
@@ -254,7 +260,7 @@ def test_tcgen05_injection_log_and_correction(ft, orc):
     flips = [(5, 6, 0, 62), (100, 200, 20, 62), (250, 3, 35, 62), (70, 129, 35, 52)]
     assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
     try:
-        got, rep = run_engine(ft, 0, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
+        got, rep = run_engine(ft, engine, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
         log = ft.ftgemm_injection_log()
     finally:
         ft.ftgemm_set_injection(mode=0)
