@@ -16,8 +16,7 @@
 
 namespace ftg {
 
-constexpr int ENC_CW = 256;  // SEG: columns per block
-constexpr int ENC_RW = 256;  // STR: rows per block
+constexpr int ENC_CHUNK = 64;  // unit of the chunked dimension; a block takes 1, 2 or 4 units
 
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
@@ -25,10 +24,11 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// grid (nG, ceil(S / ENC_CW)), 256 threads
+// grid (nG, ceil(S / cw)), 256 threads; block (G, c) covers columns c*cw ..
 __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
-                                                      double *__restrict__ part_rabs, double *__restrict__ part_max) {
+                                                      double *__restrict__ part_rabs, double *__restrict__ part_max,
+                                                      int cw) {
   __shared__ double sh[8][128];
   __shared__ double smx[8];
   const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
   const long long r0 = (long long)G * 128;
   double rabs[4] = {0.0, 0.0, 0.0, 0.0};
   double mx = 0.0;
-  const long long s1 = min(S, (long long)(c + 1) * ENC_CW);
-  for (long long s = (long long)c * ENC_CW + w; s < s1; s += 8) {
+  const long long s1 = min(S, (long long)(c + 1) * cw);
+  for (long long s = (long long)c * cw + w; s < s1; s += 8) {
     double v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -70,40 +70,75 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
   }
 }
 
-// grid (nG, ceil(R / ENC_RW)), 256 threads
+// grid (nG, ceil(R / (64 nsub))), 256 threads: a block covers nsub chunks of
+// 64 rows of one 128-column group; warp w takes the group's columns
+// 16w..16w+15, lane l the rows l and l + 32 of a chunk, so that a column's
+// absolute sum costs one warp reduction per 64 entries.
 __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
-                                                      double *__restrict__ part_cabs, double *__restrict__ part_max) {
-  __shared__ double sh[8][128];
-  __shared__ double smx[8];
+                                                      double *__restrict__ part_cabs, double *__restrict__ part_max,
+                                                      int nsub) {
+  static_assert(ENC_CHUNK == 64, "two rows per lane");
+  __shared__ double srs[8][64], sra[8][64];
+  __shared__ double smx[2];
   const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long r = (long long)c * ENC_RW + threadIdx.x;
   const long long s0 = (long long)G * 128;
   const int ns = (int)min(128LL, S - s0);
-  double sum = 0.0, ab = 0.0;
-  for (int s = 0; s < ns; ++s) {
-    const double v = (r < R) ? X[r + (s0 + s) * ld] : 0.0;
-    sum += v;
-    ab += fabs(v);
-    const double wa = warp_sum(fabs(v));
-    if (lane == 0) sh[w][s] = wa;
-  }
-  if (r < R) gsum[(long long)G * gstride + r] = sum;
-  const double m = warp_max(ab);
-  if (lane == 0) smx[w] = m;
-  __syncthreads();
-  if (threadIdx.x < ns) {
-    double t = 0.0;
+  double cab[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
-    part_cabs[(long long)c * S + s0 + threadIdx.x] = t;
+  for (int q = 0; q < 16; ++q) cab[q] = 0.0;
+  double mloc = 0.0;  // largest row absolute sum seen by this thread (threads < 64)
+  for (int sub = 0; sub < nsub; ++sub) {
+    const long long r0 = ((long long)c * nsub + sub) * 64, ra = r0 + lane, rb = ra + 32;
+    if (r0 >= R) break;
+    double rs_a = 0.0, rs_b = 0.0, ab_a = 0.0, ab_b = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int sl = w * 16 + q;
+      double va = 0.0, vb = 0.0;
+      if (sl < ns) {
+        const double *col = X + (s0 + sl) * ld;
+        if (ra < R) va = col[ra];
+        if (rb < R) vb = col[rb];
+      }
+      rs_a += va;
+      rs_b += vb;
+      ab_a += fabs(va);
+      ab_b += fabs(vb);
+      cab[q] += warp_sum(fabs(va) + fabs(vb));
+    }
+    srs[w][lane] = rs_a;
+    srs[w][lane + 32] = rs_b;
+    sra[w][lane] = ab_a;
+    sra[w][lane + 32] = ab_b;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const long long r = r0 + threadIdx.x;
+      double t = 0.0, ta = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        t += srs[q][threadIdx.x];
+        ta += sra[q][threadIdx.x];
+      }
+      if (r < R) {
+        gsum[(long long)G * gstride + r] = t;
+        mloc = fmax(mloc, ta);
+      }
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double mm = 0.0;
-    for (int q = 0; q < 8; ++q) mm = fmax(mm, smx[q]);
-    part_max[(long long)c * nG + G] = mm;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (w * 16 + q < ns) part_cabs[(long long)c * S + s0 + w * 16 + q] = cab[q];
   }
+  if (threadIdx.x < 64) {
+    const double m = warp_max(mloc);
+    if (lane == 0) smx[w] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) part_max[(long long)c * nG + G] = fmax(smx[0], smx[1]);
 }
 
 // abs[x] = sum_c part_abs[c][x] (x < L), gmax[G] = max_c part_max[c][G] (G < nG)

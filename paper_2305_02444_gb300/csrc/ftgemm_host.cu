@@ -276,53 +276,90 @@ uint64_t splitmix64(uint64_t seed, uint64_t n) {
 
 // Encode the operand checksum vectors (see ftgemm_encode.cuh).  Writes
 // acs (nI x Kp), aabsmax, arowabs, bcs (nJ x Kp), babsmax, bcolabs.
+// Chunking of the operand checksum pass for one operand: a SEG pass (column
+// sums of 128-row groups, over stored R x S with the S columns chunked) or a
+// STR pass (row sums of 128-column groups, rows chunked).  A block takes
+// `sub` chunks of ENC_CHUNK: the largest of 4, 2, 1 that still gives two
+// blocks per SM, so that small operands spread over the SMs and large ones
+// keep the partial buffers small.
+struct EncOp {
+  bool seg;
+  long long R, S, nG, nch;
+  int sub;
+  long long part_len() const { return nch * (seg ? R : S); }
+  long long max_len() const { return nch * nG; }
+};
+
+EncOp enc_op(bool seg, long long R, long long S, int nsm) {
+  EncOp o;
+  o.seg = seg;
+  o.R = R;
+  o.S = S;
+  o.nG = seg ? (R + 127) / 128 : (S + 127) / 128;
+  const long long L = seg ? S : R;
+  o.sub = 1;
+  for (int sub : {4, 2})
+    if (o.nG * ((L + ENC_CHUNK * sub - 1) / (ENC_CHUNK * sub)) >= 2LL * nsm) {
+      o.sub = sub;
+      break;
+    }
+  o.nch = (L + ENC_CHUNK * o.sub - 1) / (ENC_CHUNK * o.sub);
+  return o;
+}
+
+// The passes of op(A) and op(B): op(A) is SEG over stored A (M x K) for 'N',
+// STR over stored A (K x M) for 'T'; op(B) is STR over stored B (K x N) for
+// 'N', SEG over stored B (N x K) for 'T'.
+void enc_ops(bool ta_t, bool tb_t, long long M, long long N, long long K, int nsm, EncOp &oa, EncOp &ob) {
+  oa = ta_t ? enc_op(false, K, M, nsm) : enc_op(true, M, K, nsm);
+  ob = tb_t ? enc_op(true, N, K, nsm) : enc_op(false, K, N, nsm);
+}
+
+// One operand's pass and its finish: gsum = group sums (stride gstride),
+// absv = row (SEG) / column (STR) absolute sums, gmax = per group maximum.
+void launch_enc(const EncOp &o, const double *X, long long ld, double *gsum, long long gstride, double *part_abs,
+                double *part_max, double *absv, double *gmax, cudaStream_t s) {
+  const dim3 grid((unsigned)o.nG, (unsigned)o.nch);
+  if (o.seg) enc_seg_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, ENC_CHUNK * o.sub);
+  else enc_str_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, o.sub);
+  const long long L = o.seg ? o.R : o.S;
+  enc_finish_kernel<<<grid_for(std::max(L, o.nG)), 256, 0, s>>>(part_abs, (int)o.nch, L, absv, part_max, (int)o.nG,
+                                                                gmax);
+}
+
+int device_sms(int dev) {
+  static int cached[MAX_DEV] = {0};
+  if (dev < 0 || dev >= MAX_DEV) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// Encode the operand checksum vectors (see ftgemm_encode.cuh).  Writes
+// acs (nI x Kp), aabsmax, arowabs, bcs (nJ x Kp), babsmax, bcolabs.
 int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, const double *A, long long lda,
                const double *B, long long ldb, long long Kp, double *acs, double *aabsmax, double *arowabs,
                double *bcs, double *babsmax, double *bcolabs, Workspace &w, cudaStream_t s) {
   const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN;
-  // partial buffers: worst case over the two operands
-  auto part_need = [&](long long R, long long S, bool seg) -> long long {
-    const long long nch = seg ? (S + ENC_CW - 1) / ENC_CW : (R + ENC_RW - 1) / ENC_RW;
-    return nch * (seg ? R : S);
-  };
-  auto max_need = [&](long long R, long long S, bool seg) -> long long {
-    const long long nch = seg ? (S + ENC_CW - 1) / ENC_CW : (R + ENC_RW - 1) / ENC_RW;
-    return nch * (seg ? (R + 127) / 128 : (S + 127) / 128);
-  };
-  const long long pa = std::max(ta_t ? part_need(K, M, false) : part_need(M, K, true),
-                                tb_t ? part_need(N, K, true) : part_need(K, N, false));
-  const long long pm = std::max(ta_t ? max_need(K, M, false) : max_need(M, K, true),
-                                tb_t ? max_need(N, K, true) : max_need(K, N, false));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  EncOp oa, ob;
+  enc_ops(ta_t, tb_t, M, N, K, device_sms(dev), oa, ob);
+  const long long pa = std::max(oa.part_len(), ob.part_len()), pm = std::max(oa.max_len(), ob.max_len());
   if (ensure(w.part_abs, sizeof(double) * pa) || ensure(w.part_max, sizeof(double) * pm)) return FTGEMM_ERR_NOMEM;
   double *part_abs = (double *)w.part_abs.p, *part_max = (double *)w.part_max.p;
   if (Kp != K) {
     cudaMemsetAsync(acs, 0, sizeof(double) * nI * Kp, s);
     cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
   }
-  // op(A): SEG over stored A (M x K) for 'N', STR over stored A (K x M) for 'T'
-  if (!ta_t) {
-    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
-    enc_seg_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, M, K, lda, acs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
-                                                                 aabsmax);
-  } else {
-    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
-    enc_str_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, K, M, lda, acs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
-                                                                 aabsmax);
-  }
-  // op(B): STR over stored B (K x N) for 'N', SEG over stored B (N x K) for 'T'
-  if (!tb_t) {
-    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
-    enc_str_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, K, N, ldb, bcs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
-                                                                 babsmax);
-  } else {
-    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
-    enc_seg_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, N, K, ldb, bcs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
-                                                                 babsmax);
-  }
+  launch_enc(oa, A, lda, acs, Kp, part_abs, part_max, arowabs, aabsmax, s);
+  launch_enc(ob, B, ldb, bcs, Kp, part_abs, part_max, bcolabs, babsmax, s);
   g_launches += 4;
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
@@ -917,13 +954,12 @@ struct NoallocLayout {
   size_t rep, loc, acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max, total;
 };
 
-NoallocLayout noalloc_layout(bool ta_t, bool tb_t, long long M, long long N, long long K) {
+NoallocLayout noalloc_layout(bool ta_t, bool tb_t, long long M, long long N, long long K, int nsm) {
   const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN, Kp = (K + BK - 1) / BK * BK;
-  auto nch_seg = [](long long S) { return (S + ENC_CW - 1) / ENC_CW; };
-  auto nch_str = [](long long R) { return (R + ENC_RW - 1) / ENC_RW; };
   // partial buffers of the checksum pass: worst case over the two operands
-  const long long pa = std::max(ta_t ? nch_str(K) * M : nch_seg(K) * M, tb_t ? nch_seg(K) * N : nch_str(K) * N);
-  const long long pm = std::max(ta_t ? nch_str(K) * nI : nch_seg(K) * nI, tb_t ? nch_seg(K) * nJ : nch_str(K) * nJ);
+  EncOp oa, ob;
+  enc_ops(ta_t, tb_t, M, N, K, nsm, oa, ob);
+  const long long pa = std::max(oa.part_len(), ob.part_len()), pm = std::max(oa.max_len(), ob.max_len());
   NoallocLayout L;
   size_t o = 0;
   L.rep = o; o = align256(o + sizeof(DevReport));
@@ -960,15 +996,16 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
     return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
   }
   const bool ta_t = is_t(transA), tb_t = is_t(transB);
-  const NoallocLayout L = noalloc_layout(ta_t, tb_t, M, N, K);
-  if (L.total > (size_t)FTGEMM_NOALLOC_SCRATCH_BYTES) return FTGEMM_ERR_SCRATCH;
-  if (!tma_ok(A, lda) || !tma_ok(B, ldb) || !tma_ok(C, ldc)) return FTGEMM_ERR_UNALIGNED;
-
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) {
     cudaGetLastError();
     return FTGEMM_ERR_NODEVICE;
   }
+  const int nsm = device_sms(dev);
+  const NoallocLayout L = noalloc_layout(ta_t, tb_t, M, N, K, nsm);
+  if (L.total > (size_t)FTGEMM_NOALLOC_SCRATCH_BYTES) return FTGEMM_ERR_SCRATCH;
+  if (!tma_ok(A, lda) || !tma_ok(B, ldb) || !tma_ok(C, ldc)) return FTGEMM_ERR_UNALIGNED;
+
   if (!g_noalloc_ptr[dev]) {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
@@ -995,27 +1032,11 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
     cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
   }
   // operand checksum pass (same kernels as ftgemm_d), partials in the array
-  if (!ta_t) {
-    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
-    enc_seg_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, M, K, lda, acs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max<long long>(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
-                                                                 aabsmax);
-  } else {
-    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
-    enc_str_kernel<<<dim3((unsigned)nI, nch), 256, 0, s>>>(A, K, M, lda, acs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max<long long>(M, nI)), 256, 0, s>>>(part_abs, nch, M, arowabs, part_max, (int)nI,
-                                                                 aabsmax);
-  }
-  if (!tb_t) {
-    const int nch = (int)((K + ENC_RW - 1) / ENC_RW);
-    enc_str_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, K, N, ldb, bcs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max<long long>(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
-                                                                 babsmax);
-  } else {
-    const int nch = (int)((K + ENC_CW - 1) / ENC_CW);
-    enc_seg_kernel<<<dim3((unsigned)nJ, nch), 256, 0, s>>>(B, N, K, ldb, bcs, Kp, part_abs, part_max);
-    enc_finish_kernel<<<grid_for(std::max<long long>(N, nJ)), 256, 0, s>>>(part_abs, nch, N, bcolabs, part_max, (int)nJ,
-                                                                 babsmax);
+  {
+    EncOp oa, ob;
+    enc_ops(ta_t, tb_t, M, N, K, nsm, oa, ob);
+    launch_enc(oa, A, lda, acs, Kp, part_abs, part_max, arowabs, aabsmax, s);
+    launch_enc(ob, B, ldb, bcs, Kp, part_abs, part_max, bcolabs, babsmax, s);
   }
   g_launches += 4;
 

@@ -142,7 +142,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
       prefetch_tmap(tmA);
       prefetch_tmap(tmB);
     }
-    prefetch_tmap(MODE == 1 ? tmW : tmC);
+    prefetch_tmap(MODE == 1 || MODE == 2 ? tmW : tmC);
   }
   if (tid < 128) { s_rfail[tid] = 0; s_cfail[tid] = 0; }
   // a previous tile of a persistent CTA read and wrote the ring with generic
@@ -395,16 +395,24 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     return;
   }
   if (MODE == 2) {
-    // split-K reduction: acc = sum over splits of the partial tiles (ascending split)
+    // split-K reduction: acc = sum over splits of the partial tiles (ascending
+    // split).  Each partial tile comes in as one TMA bulk load into the staged
+    // tile buffer (the ring is idle: no k-slabs here), then is summed from
+    // shared memory; the rows / columns outside the matrix load as zeros.
     for (int sp = 0; sp < p.nsplit; ++sp) {
-      const double *Ws = p.W + (long long)sp * p.ldw * p.N;
+      if (tid == 0) {
+        mbar_arrive_expect_tx(full0, CTILE_BYTES);
+        tma_load_3d(smem_u32(sC), tmW, full0, i0, j0, sp);
+      }
+      if (!mbar_wait_bounded(full0, sp & 1, limit, err)) atomicExch(&cnt[C_ABORT], 1);
+      compute_sync();  // every thread leaves together if a partial never landed
+      if (*reinterpret_cast<volatile int *>(&cnt[C_ABORT])) return;
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp)
 #pragma unroll
-        for (int qq = 0; qq < 8; ++qq) {
-          const int il = tx + 16 * pp, jl = ty + 16 * qq;
-          if (il < mI && jl < nJt) acc[pp][qq] += Ws[(long long)(i0 + il) + (long long)(j0 + jl) * p.ldw];
-        }
+        for (int qq = 0; qq < 8; ++qq) acc[pp][qq] += sC[(ty + 16 * qq) * BM + tx + 16 * pp];
+      fence_proxy_async_smem();  // these generic reads precede the next async write (next partial or C)
+      compute_sync();
       if (FT) {
         if (tid < 128) {
           if (tid < nJt) csacc += p.wpc[((long long)sp * p.nI + I) * p.N + j0 + tid];
