@@ -87,8 +87,9 @@ constexpr int SP_STAGES = 4;
 constexpr int SP_A_BYTES = SP_BM * SP_BK * 2, SP_B_BYTES = SP_BN * SP_BK * 2;  // 16 KiB each
 constexpr int SP_STAGE_BYTES = SP_A_BYTES + SP_B_BYTES;
 constexpr int SP_MAX_PAIRS = 128;
+constexpr int SP_RED_DOUBLES = (4 + 2) * 3 * 128 + 8;  // epilogue scratch of the split kernels
 constexpr int SP_SMEM_BYTES = SP_STAGES * SP_STAGE_BYTES + 4 * SP_BK * 4 + 4 * 128 * 8 + 2 * 128 * 4 + 256 +
-                              2 * SP_STAGES * 8 + 1024;
+                              2 * SP_STAGES * 8 + SP_RED_DOUBLES * 8 + 1024;
 
 struct SplitParams {
   long long M, N, K, Kp;        // Kp: K rounded up to SP_BK (slices are zero padded)

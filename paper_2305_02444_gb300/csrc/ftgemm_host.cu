@@ -82,6 +82,8 @@ struct Workspace {
   Buf uC, uccs, uccsa, ucrs, ucrsa, uP1, uP2;  // unfused ablation: copy of C, C sums, skinny GEMMs
   Buf spA, spB, spEA, spEB;  // split precision: bf16 slices and row/column exponents
   Buf spPA, spPB, spEPA, spEPB;  // slices / exponents of the checksum operands (tcgen05 engine, ft = 2)
+  cudaStream_t side = nullptr;   // second stream for independent work inside one call (fork / join)
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int nsm = 0;              // SM count
   Buf pin;                  // pinned host staging (report, loc, injection upload)
   // the last injected call, for ftgemm_injection_log
@@ -913,7 +915,7 @@ int ftgemm_finalize(void) {
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
                   &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
-                  &w.spA, &w.spB, &w.spEA, &w.spEB};
+                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -921,6 +923,11 @@ int ftgemm_finalize(void) {
   }
   if (w.pin.p) cudaFreeHost(w.pin.p);
   w.pin.p = nullptr;
+  if (w.side) cudaStreamDestroy(w.side);
+  if (w.fork_ev) cudaEventDestroy(w.fork_ev);
+  if (w.join_ev) cudaEventDestroy(w.join_ev);
+  w.side = nullptr;
+  w.fork_ev = w.join_ev = nullptr;
   w.pin.cap = 0;
   w.init = false;
   w.last_nflips = 0;
@@ -1642,9 +1649,18 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
       q2.N = nJ; q2.nJ = (int)((nJ + SP_BN - 1) / SP_BN);
       q2.eB = (const int *)w.spEPB.p; q2.C = (double *)w.uP2.p; q2.ldc = ldp2;
       for (SplitParams *q : {&q1, &q2}) { q->alpha = 1.0; q->beta = 0.0; q->verify = 0; q->inj = 0; }
-      if (launch_split_tc(false, false, 0, cl, mPA, mB, mB, q1, s) != cudaSuccess ||
-          launch_split_tc(false, false, 0, cl, mA, mPB, mPB, q2, s) != cudaSuccess)
+      // P1 and P2 are independent one-wave grids: P2 runs on a second stream
+      if (!w.side && (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&w.join_ev, cudaEventDisableTiming) != cudaSuccess))
         return FTGEMM_ERR_CUDA;
+      cudaEventRecord(w.fork_ev, s);
+      cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+      if (launch_split_tc(false, false, 0, cl, mPA, mB, mB, q1, s) != cudaSuccess ||
+          launch_split_tc(false, false, 0, cl, mA, mPB, mPB, q2, w.side) != cudaSuccess)
+        return FTGEMM_ERR_CUDA;
+      cudaEventRecord(w.join_ev, w.side);
+      cudaStreamWaitEvent(s, w.join_ev, 0);
       g_launches += 2;
       p.ePA = (const int *)w.spEPA.p; p.ePB = (const int *)w.spEPB.p;
     } else {

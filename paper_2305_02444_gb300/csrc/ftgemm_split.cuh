@@ -63,26 +63,79 @@ __device__ __forceinline__ double sp_glob_b(const SplitParams &p, long long k, l
   return TB ? p.B[j + k * p.ldb] : p.B[k + j * p.ldb];
 }
 
+// x * 2^e, exactly as ldexp (one correctly rounded multiply when 2^e is a
+// normal double, ldexp otherwise).
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(x, e);
+}
+__device__ __forceinline__ double pow2_or_ldexp(int e) { return scale_pow2(1.0, e); }
+
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+
 // The end of a tile shared by the split kernels, run by 256 threads: sC holds
 // the tile's unscaled FP64 accumulators (column-major, 128 x 128); scale to
 // the output, verify with the FP64 checksums (CK 2), recompute the flagged
 // elements from the original operands (CK >= 1; s_fr / s_fc / cnt[0..1] hold
-// the rows / columns flagged so far), report, store.
+// the rows / columns flagged so far), report, store.  `red` is shared-memory
+// scratch of SP_RED_DOUBLES doubles.  Thread t scales row t mod 128 over the
+// columns of parity t / 128 (C read coalesced); with CK 2 it also takes that
+// row's partial sums (output, C, |C|) and, by warp reductions, its warp's
+// 32-row partial sums of each column it visits.
 template <bool TA, bool TB, int CK>
-__device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *sC, int *s_fr, int *s_fc, int *cnt,
-                                                  int tile, int I, int J) {
+__device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *sC, double *red, int *s_fr,
+                                                  int *s_fc, int *cnt, int tile, int I, int J) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = I * SP_BM, j0 = J * SP_BN;
   const int mI = (int)min((long long)SP_BM, p.M - i0), nJt = (int)min((long long)SP_BN, p.N - j0);
-  // scale to the output: out = alpha * 2^(eA_i + eB_j) * acc + beta * C  (C read only if beta != 0)
+  // out = alpha * 2^(eA_i + eB_j) * acc + beta * C  (C read only if beta != 0)
   const bool use_c = p.beta != 0.0;
-  for (int e = tid; e < SP_BM * SP_BN; e += 256) {
-    const int il = e & 127, jl = e >> 7;
+  const int il = tid & 127, h = tid >> 7, wq = warp & 3;
+  double *colp = red;                 // [4 row quarters][128 columns][3]: output, C, |C| (FP32 ru)
+  double *rowp = red + 4 * 128 * 3;   // [2 column halves][128 rows][3]
+  double *sigp = rowp + 2 * 128 * 3;  // [0..3] sum of 2^eA over a row quarter, [4..5] of 2^eB over a column half
+  double rref = 0.0, rcs = 0.0, sb = 0.0;
+  float rca = 0.0f;
+  const int eAi = il < mI ? p.eA[i0 + il] : 0;
+  for (int jl = h; jl < SP_BN; jl += 2) {
+    double out = 0.0, c = 0.0;
     if (il < mI && jl < nJt) {
       const long long gi = i0 + il, gj = j0 + jl;
-      const double v = ldexp(sC[e], p.eA[gi] + p.eB[gj]);
-      sC[e] = use_c ? fma(p.alpha, v, p.beta * p.C[gi + gj * p.ldc]) : p.alpha * v;
+      const int eBj = p.eB[gj];
+      const double v = scale_pow2(sC[jl * SP_BM + il], eAi + eBj);
+      if (use_c) c = p.C[gi + gj * p.ldc];
+      out = use_c ? fma(p.alpha, v, p.beta * c) : p.alpha * v;
+      sC[jl * SP_BM + il] = out;
     }
+    if (CK == 2) {
+      rref += out;
+      rcs += c;
+      const float fa = __double2float_ru(fabs(c));
+      rca = __fadd_ru(rca, fa);
+      if (il == 0 && jl < nJt) sb += pow2_or_ldexp(p.eB[j0 + jl]);  // lane 0 of quarter 0: the half's 2^eB sum
+      const double wr = warp_sum(out), wc = warp_sum(c);
+      const float wa = warp_sum_ru(fa);
+      if (lane == 0) {
+        double *q = colp + (wq * 128 + jl) * 3;
+        q[0] = wr;
+        q[1] = wc;
+        q[2] = (double)wa;
+      }
+    }
+  }
+  if (CK == 2) {
+    double *q = rowp + (h * 128 + il) * 3;
+    q[0] = rref;
+    q[1] = rcs;
+    q[2] = (double)rca;
+    const double sa = warp_sum(il < mI ? pow2_or_ldexp(eAi) : 0.0);
+    if (lane == 0 && h == 0) sigp[wq] = sa;
+    if (il == 0) sigp[4 + h] = sb;
   }
   __syncthreads();
   if (CK == 2) {
@@ -92,23 +145,19 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
     const bool col = tid < 128;
     const bool valid = col ? (idx < nJt) : (idx < mI);
     if (valid) {
-      double ref = 0.0, cs = 0.0, ca = 0.0, sig = 0.0;
+      double ref, cs, ca, sig;
       if (col) {
-        const long long gj = j0 + idx;
-        for (int i = 0; i < mI; ++i) {
-          ref += sC[idx * SP_BM + i];
-          sig += ldexp(1.0, p.eA[i0 + i]);
-          if (use_c) { const double c = p.C[(i0 + i) + gj * p.ldc]; cs += c; ca += fabs(c); }
-        }
-        sig *= ldexp(1.0, p.eB[gj]);
+        const double *q = colp + idx * 3;
+        ref = (q[0] + q[384]) + (q[768] + q[1152]);
+        cs = (q[1] + q[385]) + (q[769] + q[1153]);
+        ca = (double)__fadd_ru(__fadd_ru((float)q[2], (float)q[386]), __fadd_ru((float)q[770], (float)q[1154]));
+        sig = ((sigp[0] + sigp[1]) + (sigp[2] + sigp[3])) * pow2_or_ldexp(p.eB[j0 + idx]);
       } else {
-        const long long gi = i0 + idx;
-        for (int j = 0; j < nJt; ++j) {
-          ref += sC[j * SP_BM + idx];
-          sig += ldexp(1.0, p.eB[j0 + j]);
-          if (use_c) { const double c = p.C[gi + (long long)(j0 + j) * p.ldc]; cs += c; ca += fabs(c); }
-        }
-        sig *= ldexp(1.0, p.eA[gi]);
+        const double *q = rowp + idx * 3;
+        ref = q[0] + q[384];
+        cs = q[1] + q[385];
+        ca = (double)__fadd_ru((float)q[2], (float)q[386]);
+        sig = (sigp[4] + sigp[5]) * pow2_or_ldexp(p.eA[i0 + idx]);
       }
       const double P = col ? p.P1[(long long)I + (long long)(j0 + idx) * p.ldp1]
                            : p.P2[(long long)(i0 + idx) + (long long)J * p.ldp2];
@@ -207,6 +256,7 @@ __global__ void __launch_bounds__(256, 1)
   int *s_fc = s_fr + 128;
   int *cnt = s_fc + 128;  // [0] nr [1] nc [2] det [3] abort [4] unverifiable
   uint64_t *bars = reinterpret_cast<uint64_t *>(cnt + 64);
+  double *s_red = reinterpret_cast<double *>(bars + 2 * SP_STAGES);  // epilogue scratch
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + SP_STAGES);
 
   constexpr bool FT = CK == 1;  // FP32 checksum work in the mainloop
@@ -456,7 +506,7 @@ __global__ void __launch_bounds__(256, 1)
     }
   }
   __syncthreads();
-  split_tile_finish<TA, TB, CK>(p, sC, s_fr, s_fc, cnt, tile, I, J);
+  split_tile_finish<TA, TB, CK>(p, sC, s_red, s_fr, s_fc, cnt, tile, I, J);
 }
 
 }  // namespace ftg

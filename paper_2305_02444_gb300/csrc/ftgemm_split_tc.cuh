@@ -48,7 +48,8 @@ constexpr int TC_HANDOFF_BAR = 3;  // named barrier of the waiter -> MMA-issuer 
 constexpr uint32_t TC_IDESC = tc_idesc_bf16_f32(SP_BM, SP_BN);
 constexpr int TC_SMEM_BYTES = TC_STAGES * SP_STAGE_BYTES + 2 * 128 * 4 + 64 * 4 + (2 * TC_STAGES + 5) * 8 + 16 +
                               1024;
-static_assert(TC_STAGES * SP_STAGE_BYTES >= SP_BM * SP_BN * 8, "the ring holds the FP64 tile at the end");
+static_assert(TC_STAGES * SP_STAGE_BYTES >= SP_BM * SP_BN * 8 + SP_RED_DOUBLES * 8,
+              "the ring holds the FP64 tile and the epilogue scratch at the end");
 
 // 2^-sh * f as a double, for f an integer-valued float (the exact FP32 result
 // of a slice-pair product) and 0 <= sh < 800: f's sign, exponent - sh and
@@ -377,7 +378,8 @@ __global__ void __launch_bounds__(256, 1)
     tc_fence_after();
     tmem_dealloc(tbase, TC_TMEM_COLS);
   }
-  if (valid) split_tile_finish<TA, TB, CK>(p, sC, s_fr, s_fc, cnt, tile, I, J);
+  if (valid) split_tile_finish<TA, TB, CK>(p, sC, reinterpret_cast<double *>(smem + SP_BM * SP_BN * 8), s_fr,
+                                            s_fc, cnt, tile, I, J);
   if (CL > 1) cluster_sync();
 }
 
