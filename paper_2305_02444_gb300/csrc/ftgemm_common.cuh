@@ -67,10 +67,13 @@ struct Params {
   DevFlip *flips;                // injection table (INJ kernels only)
   const int *tile_off;           // ntiles + 1 offsets into flips
   unsigned long long wait_limit_ns;
+  // grids over a range of tiles: CTA b takes tile tile_base + b (MODE 1:
+  // tile_base + b mod tile_count, split b / tile_count); tile_count 0 means
+  // all nI x nJ tiles
+  int tile_base, tile_count;
   // split-K (MODE 1 / 2 kernels)
   int nsplit, ks_slabs;          // number of k-splits, k-slabs per split
-  double *W;                     // nsplit partial tiles, [split][N][ldw]
-  long long ldw;
+  double *W;                     // partial tiles, 128 x 128 each, slot split * tile_count + (tile - tile_base)
   double *wpc, *wpr;             // predicted-checksum partials [split][nI][N], [split][nJ][M]
   // unfused ablation (MODE 3): predicted checksums and C sums from separate passes
   const double *P1, *P2;         // nI x N (ld ldp1) and M x nJ (ld ldp2), column-major

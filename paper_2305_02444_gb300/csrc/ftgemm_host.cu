@@ -248,6 +248,27 @@ int choose_splits(long long ntiles, long long nks, int nsm) {
   return bestS;
 }
 
+// K-splits for the tail of a large grid (ntiles >= 4 x nsm, which
+// choose_splits never splits): when the last wave holds rem = ntiles mod nsm
+// tiles, splitting K of those tiles over S x rem CTAs costs ceil(S rem / nsm)
+// waves of 1/S of a tile instead of one whole wave.  Returns the best S
+// (1: leave the tail whole) when it saves at least 0.15 of a tile's time.
+int choose_tail_splits(long long ntiles, long long nks, int nsm) {
+  if (g_splitk != 0 || ntiles < 4LL * nsm) return 1;
+  const long long rem = ntiles % nsm;
+  if (rem == 0) return 1;
+  double best = 1.0;
+  int bestS = 1;
+  for (int S = 2; S <= 16 && S <= nks / 8; ++S) {
+    const long long ks = (nks + S - 1) / S;
+    if ((nks + ks - 1) / ks != S) continue;
+    const double waves = (double)((rem * S + nsm - 1) / nsm);
+    const double T = waves * ((double)ks + 0.07) / (double)nks + (0.03 * S + 0.3) / (double)nks;
+    if (T < best - 1e-9) { best = T; bestS = S; }
+  }
+  return best <= 0.85 ? bestS : 1;
+}
+
 // 3-D fp64 tensor map over nz column-major matrices of rows x cols (ld), stacked.
 int make_map3(CUtensorMap *m, const double *ptr, long long rows, long long cols, long long nz, long long ld) {
   auto fn = encode_fn();
@@ -565,7 +586,18 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     }
   }
   const bool panel = ft && g_panel > 0 && nks > g_panel;
-  const int S = panel ? 1 : choose_splits(ntiles, nks, w.nsm);
+  int S = panel ? 1 : choose_splits(ntiles, nks, w.nsm);
+  // Large grids whose last wave is partly empty: the full waves take whole
+  // tiles, the tail tiles split K over the idle SMs (then a verifying reduction).
+  long long tail_base = 0, tail_count = ntiles;
+  if (!panel && S <= 1) {
+    const int St = choose_tail_splits(ntiles, nks, w.nsm);
+    if (St > 1) {
+      S = St;
+      tail_count = ntiles % w.nsm;
+      tail_base = ntiles - tail_count;
+    }
+  }
   p.panel_slabs = panel ? g_panel : 0;
   cudaError_t e;
   auto launch = [&](int mode, const CUtensorMap &mW) {
@@ -584,20 +616,28 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     e = launch(0, mC);
     g_launches++;
   } else {
-    // split-K: partial tiles into workspace, then the verifying reduction
-    const long long ldw = (M + 1) & ~1LL;
-    if (ensure(w.W, sizeof(double) * ldw * N * S) || ensure(w.wpc, sizeof(double) * S * nI * N) ||
+    e = cudaSuccess;
+    if (tail_base > 0) {  // whole tiles first
+      p.tile_base = 0;
+      p.tile_count = (int)tail_base;
+      e = launch(0, mC);
+      g_launches++;
+    }
+    // split-K over tiles [tail_base, tail_base + tail_count): partial tiles
+    // (128 x 128 slots) into workspace, then the verifying reduction
+    if (ensure(w.W, sizeof(double) * BM * BN * S * tail_count) || ensure(w.wpc, sizeof(double) * S * nI * N) ||
         ensure(w.wpr, sizeof(double) * S * nJ * M))
       return FTGEMM_ERR_NOMEM;
     CUtensorMap mW;
-    if ((rc = make_map3(&mW, (const double *)w.W.p, M, N, S, ldw))) return rc;
+    if ((rc = make_map3(&mW, (const double *)w.W.p, BM, BN, S * tail_count, BM))) return rc;
+    p.tile_base = (int)tail_base;
+    p.tile_count = (int)tail_count;
     p.nsplit = S;
     p.ks_slabs = (int)((nks + S - 1) / S);
     p.W = (double *)w.W.p;
-    p.ldw = ldw;
     p.wpc = (double *)w.wpc.p;
     p.wpr = (double *)w.wpr.p;
-    e = launch(1, mW);
+    if (e == cudaSuccess) e = launch(1, mW);
     if (e == cudaSuccess) e = launch(2, mW);
     g_launches += 2;
   }

@@ -12,7 +12,8 @@ static cudaError_t launch_variant_tt(const CUtensorMap &a, const CUtensorMap &b,
   auto k = ftdgemm_kernel<true, true, FT, INJ, MODE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)p.nI * (unsigned)p.nJ * (MODE == 1 ? (unsigned)p.nsplit : 1u);
+  const unsigned count = p.tile_count ? (unsigned)p.tile_count : (unsigned)p.nI * (unsigned)p.nJ;
+  const unsigned grid = count * (MODE == 1 ? (unsigned)p.nsplit : 1u);
   k<<<grid, NTHREADS, SMEM_BYTES, s>>>(a, b, c, w, p);
   return cudaGetLastError();
 }

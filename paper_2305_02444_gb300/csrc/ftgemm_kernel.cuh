@@ -117,6 +117,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), cbar = smem_u32(bars + 2 * STAGES);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wcount = p.tile_count ? p.tile_count : p.nI * p.nJ;          // split-K partial slots per split
   const int s_begin = (MODE == 1) ? split * p.ks_slabs : 0;              // first k-slab (global)
   const int s_end = (MODE == 1) ? min(p.nks, s_begin + p.ks_slabs) : p.nks;
   const int I = tile % p.nI, J = tile / p.nI;
@@ -388,7 +389,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     fence_proxy_async_smem();
     compute_sync();
     if (tid == 0) {
-      tma_store_3d(tmW, smem_u32(sC), i0, j0, split);
+      tma_store_3d(tmW, smem_u32(sC), 0, 0, split * wcount + (tile - p.tile_base));
       bulk_commit();
       bulk_wait_all();
     }
@@ -402,7 +403,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     for (int sp = 0; sp < p.nsplit; ++sp) {
       if (tid == 0) {
         mbar_arrive_expect_tx(full0, CTILE_BYTES);
-        tma_load_3d(smem_u32(sC), tmW, full0, i0, j0, sp);
+        tma_load_3d(smem_u32(sC), tmW, full0, 0, 0, sp * wcount + (tile - p.tile_base));
       }
       if (!mbar_wait_bounded(full0, sp & 1, limit, err)) atomicExch(&cnt[C_ABORT], 1);
       compute_sync();  // every thread leaves together if a partial never landed
@@ -655,9 +656,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int ntiles = p.nI * p.nJ;
-  const int tile = (MODE == 1) ? (int)(blockIdx.x % ntiles) : (int)blockIdx.x;
-  const int split = (MODE == 1) ? (int)(blockIdx.x / ntiles) : 0;
+  const int count = p.tile_count ? p.tile_count : p.nI * p.nJ;
+  const int tile = p.tile_base + ((MODE == 1) ? (int)(blockIdx.x % count) : (int)blockIdx.x);
+  const int split = (MODE == 1) ? (int)(blockIdx.x / count) : 0;
   ftd_tile<TA, TB, FT, INJ, MODE, PANEL>(&tmA, &tmB, &tmC, &tmW, p, tile, split, smem);
 }
 
