@@ -181,7 +181,8 @@ __device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b
   return lo;
 }
 
-// SEG over groups of 128 rows, all columns of the item in one block.
+// SEG over groups of 128 rows, all columns of the item in one block; each
+// warp takes 4 columns per step so that their warp reductions overlap.
 __global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__restrict__ items, int nitems) {
   __shared__ double sh[8][128];
   __shared__ double smx[8];
@@ -192,19 +193,36 @@ __global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__r
   const long long r0 = (long long)G * 128;
   double rabs[4] = {0.0, 0.0, 0.0, 0.0};
   double mx = 0.0;
-  for (long long s = w; s < E.S; s += 8) {
-    double v[4];
+  for (long long sb = 4 * w; sb < E.S; sb += 32) {
+    double v[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long r = r0 + lane + 32 * q;
-      v[q] = (r < E.R) ? E.X[r + s * E.ld] : 0.0;
-      rabs[q] += fabs(v[q]);
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long r = r0 + lane + 32 * q, s = sb + c;
+        v[c][q] = (r < E.R && s < E.S) ? E.X[r + s * E.ld] : 0.0;
+        rabs[q] += fabs(v[c][q]);
+      }
+    double sum[4], ab[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      sum[c] = (v[c][0] + v[c][1]) + (v[c][2] + v[c][3]);
+      ab[c] = (fabs(v[c][0]) + fabs(v[c][1])) + (fabs(v[c][2]) + fabs(v[c][3]));
     }
-    const double sum = warp_sum((v[0] + v[1]) + (v[2] + v[3]));
-    const double ab = warp_sum((fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
+        ab[c] += __shfl_xor_sync(0xffffffffu, ab[c], o);
+      }
     if (lane == 0) {
-      E.gsum[(long long)G * E.gstride + s] = sum;
-      mx = fmax(mx, ab);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (sb + c < E.S) {
+          E.gsum[(long long)G * E.gstride + sb + c] = sum[c];
+          mx = fmax(mx, ab[c]);
+        }
     }
   }
 #pragma unroll
@@ -225,48 +243,73 @@ __global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__r
   }
 }
 
-// STR over groups of 128 columns, all rows of the item in one block.
+// STR over groups of 128 columns, all rows of the item in one block, in
+// chunks of 64 rows: warp w takes the group's columns 16w..16w+15, lane l the
+// rows l and l + 32 of a chunk; the columns' absolute sums stay in registers
+// (one warp reduction per column per chunk), the rows' sums go through
+// shared memory once per chunk.
 __global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__restrict__ items, int nitems) {
-  __shared__ double sh[8][128];
-  __shared__ double smx[8];
+  __shared__ double srs[8][64], sra[8][64];
+  __shared__ double smx[2];
   const int it = find_item(items, nitems, blockIdx.x);
   const EncItem &E = items[it];
   const int G = blockIdx.x - E.first_block;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long s0 = (long long)G * 128;
   const int ns = (int)min(128LL, E.S - s0);
-  for (int s = threadIdx.x; s < 128; s += 256) {
-    for (int q = 0; q < 8; ++q) sh[q][s] = 0.0;
-  }
-  __syncthreads();
-  double mx = 0.0;
-  for (long long rb = 0; rb < E.R; rb += 256) {
-    const long long r = rb + threadIdx.x;
-    double sum = 0.0, ab = 0.0;
-    for (int s = 0; s < ns; ++s) {
-      const double v = (r < E.R) ? E.X[r + (s0 + s) * E.ld] : 0.0;
-      sum += v;
-      ab += fabs(v);
-      const double wa = warp_sum(fabs(v));
-      if (lane == 0) sh[w][s] += wa;
-    }
-    if (r < E.R) E.gsum[(long long)G * E.gstride + r] = sum;
-    mx = fmax(mx, ab);
-  }
-  const double m = warp_max(mx);
-  if (lane == 0) smx[w] = m;
-  __syncthreads();
-  if (threadIdx.x < ns) {
-    double t = 0.0;
+  double cab[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
-    E.absv[s0 + threadIdx.x] = t;
+  for (int q = 0; q < 16; ++q) cab[q] = 0.0;
+  double mloc = 0.0;
+  for (long long r0 = 0; r0 < E.R; r0 += 64) {
+    const long long ra = r0 + lane, rb = ra + 32;
+    double rs_a = 0.0, rs_b = 0.0, ab_a = 0.0, ab_b = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int sl = w * 16 + q;
+      double va = 0.0, vb = 0.0;
+      if (sl < ns) {
+        const double *col = E.X + (s0 + sl) * E.ld;
+        if (ra < E.R) va = col[ra];
+        if (rb < E.R) vb = col[rb];
+      }
+      rs_a += va;
+      rs_b += vb;
+      ab_a += fabs(va);
+      ab_b += fabs(vb);
+      cab[q] += warp_sum(fabs(va) + fabs(vb));
+    }
+    srs[w][lane] = rs_a;
+    srs[w][lane + 32] = rs_b;
+    sra[w][lane] = ab_a;
+    sra[w][lane + 32] = ab_b;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      const long long r = r0 + threadIdx.x;
+      double t = 0.0, ta = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        t += srs[q][threadIdx.x];
+        ta += sra[q][threadIdx.x];
+      }
+      if (r < E.R) {
+        E.gsum[(long long)G * E.gstride + r] = t;
+        mloc = fmax(mloc, ta);
+      }
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double mm = 0.0;
-    for (int q = 0; q < 8; ++q) mm = fmax(mm, smx[q]);
-    E.gmax[G] = mm;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (w * 16 + q < ns) E.absv[s0 + w * 16 + q] = cab[q];
   }
+  if (threadIdx.x < 64) {
+    const double m = warp_max(mloc);
+    if (lane == 0) smx[w] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) E.gmax[G] = fmax(smx[0], smx[1]);
 }
 
 // Unfused ablation: one pass over C that keeps a copy of C_in (needed to
