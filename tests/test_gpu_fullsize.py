@@ -153,3 +153,35 @@ def test_full_oracle_small_squares(ft, orc, n):
     ref, E = orc.gemm("N", "N", 1.5, A, B, 0.5, Cin, want_E=True)
     assert np.all(np.abs(out - ref) <= orc.parity_tol(n, E))
     assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
+
+
+def test_wave_tail_split_with_flips(ft, orc):
+    """3200^2 x 256: 625 tiles = 4 waves of 152 + 17, so the 17 tail tiles
+    (I = 8..24 of tile column 24) split K in two and go through the verifying
+    reduction while the others run whole.  Exponent-bit flips in a whole tile
+    and in both k-halves of tail tiles are detected, located and corrected;
+    the whole product matches the oracle."""
+    from paper_2305_02444_gb300 import inputs
+    M = N = 3200
+    K = 256
+    A = inputs.matrix(M, K, 31)
+    B = inputs.matrix(K, N, 32)
+    C = inputs.matrix(M, N, 33)
+    dA, dB, dC = A.cuda(), B.cuda(), C.cuda()
+    flips = [(5, 7, 3, 62), (10 * BM + 5, 24 * BN + 3, 2, 62), (20 * BM + 9, 24 * BN + 28, 12, 62)]
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        rc, rep = ft.ftgemm_d("N", "N", M, N, K, 1.5, dA, M, dB, K, 0.5, dC, M, loc_cap=64)
+        log = ft.ftgemm_injection_log()
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    assert rc == 0, ft.ftgemm_strerror(rc)
+    assert [L["applied"] for L in log] == [1, 1, 1]
+    # tail tiles accumulate each half of K in its own CTA: the flip lands in
+    # the half that holds its k-step
+    assert [L["kfirst"] for L in log] == [0, 0, 128]
+    assert rep["detected"] == 3 and rep["corrected"] == 3 and rep["checksum_only"] == 0
+    assert sorted((l[0], l[1]) for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)
+    out = dC.cpu().T.numpy()
+    ref, E = orc.gemm("N", "N", 1.5, A.T.numpy(), B.T.numpy(), 0.5, C.T.numpy(), want_E=True)
+    assert np.all(np.abs(out - ref) <= orc.parity_tol(K, E))
