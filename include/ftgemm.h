@@ -79,8 +79,11 @@ typedef struct {
                     1: found by the fallback that recomputes whole row/column
                        segments of a tile;
                     2: found by a per-k-panel check (accumulator corrected
-                       before the end of K) */
-  double delta;  /* stored value minus recomputed value (may be Inf/NaN) */
+                       before the end of K);
+                    3: corrected by subtracting the column checksum residual
+                       (ftgemm_set_correction(1)) */
+  double delta;  /* stored value minus recomputed value (may be Inf/NaN); for
+                    kind 3 the subtracted residual */
 } ftgemm_loc;
 
 /* Fault report of one call.  The caller sets cap and loc (loc may be NULL
@@ -331,6 +334,19 @@ int ftgemm_set_split_engine(int engine);
  * The end-of-tile verification still runs.  0 (default) turns it off.  Such
  * calls never split K. */
 int ftgemm_set_panel_check(int kslabs);
+
+/* Correction rule of the FP64 FT-GEMM kernels (ftgemm_d and the calls built
+ * on the same kernels): 0 (default) recomputes every located element from
+ * the original operands (exact to the element's rounding bound, robust to
+ * Inf / NaN faults); 1 is FT-BLAS's rule, kept for comparison: when exactly
+ * one row and one column of a tile are flagged, their intersection is
+ * corrected by subtracting the column's checksum residual (reference minus
+ * predicted column sum), which costs no recomputation but carries the
+ * rounding of the 128-term sums and cancels badly for huge faults; a
+ * non-finite residual, several faults in a tile, or a corrected row / column
+ * that still fails its check fall back to recomputation.  Returns -1 for
+ * another value.  The split-precision path always recomputes. */
+int ftgemm_set_correction(int mode);
 
 /* Number of kernels this library has launched in this process. */
 int64_t ftgemm_launch_count(void);

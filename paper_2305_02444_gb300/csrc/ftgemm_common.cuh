@@ -80,6 +80,7 @@ struct Params {
   long long ldp1, ldp2;
   const double *ccs, *ccsa, *crs, *crsa;  // [I][N] column sums, [J][M] row sums of C (and |C|)
   int panel_slabs;               // PANEL kernels: verify the accumulators every panel_slabs k-slabs
+  int correct_mode;              // 0: recompute located elements; 1: subtract the checksum residual (one fault per tile)
   double *Cout;                  // where the verified tile lives (p.C is the copy of C_in)
   long long ldcout;
 };

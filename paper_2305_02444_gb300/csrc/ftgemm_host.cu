@@ -220,6 +220,7 @@ int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>(
 // split precision: 0 tcgen05 (default cluster shape), 1 mma.sync, 2 / 3 / 4 tcgen05 in clusters of 1 / 2 / 4 CTAs
 int g_split_engine = 0;
 constexpr int SPLIT_DEFAULT_CLUSTER = 1;
+int g_correct = 0;  // correction rule of the FP64 kernels (ftgemm_set_correction)
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
 int g_panel = 0;   // verify the accumulators every g_panel k-slabs (0: only at the end of the tile)
 
@@ -551,6 +552,7 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
   p.loc = (DevLoc *)w.loc.p;
   p.loc_cap = LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
+  p.correct_mode = g_correct;
   cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
 
   cudaEvent_t ea0 = nullptr, ea1 = nullptr, em0 = nullptr, em1 = nullptr;
@@ -777,6 +779,7 @@ int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, 
   p.loc = (DevLoc *)w.loc.p;
   p.loc_cap = LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
+  p.correct_mode = g_correct;
   p.nsplit = 1;
   cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   cudaError_t e;
@@ -886,6 +889,13 @@ int ftgemm_set_split_engine(int engine) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (engine < 0 || engine > 4) return -1;
   g_split_engine = engine;
+  return 0;
+}
+
+int ftgemm_set_correction(int mode) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (mode < 0 || mode > 1) return -1;
+  g_correct = mode;
   return 0;
 }
 
@@ -1107,6 +1117,7 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
   p.loc = dloc;
   p.loc_cap = NOALLOC_LOC_CAP;
   p.wait_limit_ns = wait_limit_ns();
+  p.correct_mode = g_correct;
   cudaError_t e;
   if (!ta_t && !tb_t) e = launch_main_nn(true, false, mA, mB, mC, p, s);
   else if (!ta_t && tb_t) e = launch_main_nt(true, false, mA, mB, mC, p, s);
@@ -1363,6 +1374,7 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
     pp.flips = P->flips;
     pp.tile_off = doff + tile_base[q];
     pp.wait_limit_ns = wait_limit_ns();
+    pp.correct_mode = g_correct;
     pp.nsplit = 1;
   }
   BatchProblem *dprobs = nullptr;

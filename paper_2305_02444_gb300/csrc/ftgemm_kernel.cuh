@@ -56,7 +56,7 @@ __device__ __forceinline__ double glob_b(const Params &p, long long k, long long
 }
 
 // counters in shared memory
-enum { C_NR = 0, C_NC, C_DET, C_CSONLY, C_UNVER, C_RECOMP, C_ABORT, C_FAIL, C_PNR, C_PNC, C_PDET, C_NCNT };
+enum { C_NR = 0, C_NC, C_DET, C_CSONLY, C_UNVER, C_RECOMP, C_ABORT, C_FAIL, C_PNR, C_PNC, C_PDET, C_SUBFAIL, C_NCNT };
 
 // Recompute element (il, jl) of the tile from the original operands with one
 // warp (lanes split k), compare with the staged value and rewrite it.
@@ -550,9 +550,37 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     const int nr = cnt[C_NR], nc = cnt[C_NC];
     if (nr + nc > 0) {
       // locate and correct: flagged row x flagged column intersections
-      if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT)
+      if (p.correct_mode == 1 && nr == 1 && nc == 1) {
+        // FT-BLAS style: subtract the column's checksum residual from the one
+        // located element, when it is finite and agrees with the row's
+        // residual within the row threshold (one fault explains both); else
+        // the element is recomputed.  The subtraction carries the rounding
+        // of the 128-term sums; a huge fault cancels badly and fails the
+        // agreement test.
+        if (tid == 0) {
+          const int il = s_fr[0], jl = s_fc[0];
+          const double old = sC[jl * BM + il], dlt = s_co[jl] - s_pc[jl], nv = old - dlt;
+          const double drow = s_ro[il] - s_pr[il];
+          if (isfinite(dlt) && isfinite(nv) && fabs(drow - dlt) <= s_tr[il]) {
+            sC[jl * BM + il] = nv;
+            cnt[C_DET] += 1;
+            const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
+            if ((long long)q < p.loc_cap) {
+              DevLoc L;
+              L.row = i0 + il; L.col = j0 + jl; L.tile = tile; L.kind = 3; L.delta = dlt;
+              p.loc[q] = L;
+            }
+          } else {
+            cnt[C_SUBFAIL] = 1;
+          }
+        }
+        compute_sync();
+        if (cnt[C_SUBFAIL] && warp == 0)
+          recompute_elem<TA, TB>(p, sC, cnt, tile, i0, j0, s_fr[0], s_fc[0], 0, use_c, lane);
+      } else if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) {
         for (int e = warp; e < nr * nc; e += NCOMPUTE / 32)
           recompute_elem<TA, TB>(p, sC, cnt, tile, i0, j0, s_fr[e / nc], s_fc[e % nc], 0, use_c, lane);
+      }
       compute_sync();
       // re-verify the flagged rows and columns
       for (int e = warp; e < nr + nc; e += NCOMPUTE / 32) {

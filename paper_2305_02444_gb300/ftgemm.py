@@ -84,6 +84,8 @@ def lib():
         L.ftgemm_set_panel_check.restype = ctypes.c_int
         L.ftgemm_set_splitk.argtypes = [ctypes.c_int]
         L.ftgemm_set_splitk.restype = ctypes.c_int
+        L.ftgemm_set_correction.argtypes = [ctypes.c_int]
+        L.ftgemm_set_correction.restype = ctypes.c_int
         L.ftgemm_set_split_engine.argtypes = [ctypes.c_int]
         L.ftgemm_set_split_engine.restype = ctypes.c_int
         L.ftgemm_timing.argtypes = [ctypes.c_int]
@@ -277,6 +279,11 @@ def ftgemm_set_panel_check(kslabs: int) -> int:
 def ftgemm_set_splitk(nsplit: int) -> int:
     """0 automatic k-splitting, 1 never, n >= 2 force n splits."""
     return lib().ftgemm_set_splitk(nsplit)
+
+
+def ftgemm_set_correction(mode: int) -> int:
+    """0 recompute located elements (default), 1 subtract the checksum residual."""
+    return lib().ftgemm_set_correction(mode)
 
 
 def ftgemm_set_split_engine(engine: int) -> int:

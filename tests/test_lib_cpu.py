@@ -89,3 +89,10 @@ def test_split_engine_knob_codes(ft):
     assert ft.ftgemm_set_split_engine(-1) == -1
     assert ft.ftgemm_set_split_engine(1) == 0
     assert ft.ftgemm_set_split_engine(0) == 0
+
+
+def test_correction_knob_codes(ft):
+    assert ft.ftgemm_set_correction(2) == -1
+    assert ft.ftgemm_set_correction(-1) == -1
+    assert ft.ftgemm_set_correction(1) == 0
+    assert ft.ftgemm_set_correction(0) == 0
