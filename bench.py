@@ -464,6 +464,116 @@ def split(args):
     print(json.dumps(line), flush=True)
 
 
+def config5(args):
+    """32768^3, normal(0,1), alpha 1, beta 1: the FP64 FT-DGEMM timed
+    fault-free and unprotected, then one call with flips at a rate of
+    --flip-rate per minute of the fault-free time (seeded positions, k-steps
+    and bits 0..62); the same inputs through the emulated FP64 forms on the
+    tensor cores (S = 7 and 11, FP64 checksums, one exponent-bit flip per 64
+    tiles).  Checked against the FP64 oracle on sampled rows and on every
+    injected element."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2305_02444_gb300 import build, ftgemm, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    n = args.size
+    A = inputs.matrix(n, n, SEED, "normal", device="cuda")
+    B = inputs.matrix(n, n, SEED + 1, "normal", device="cuda")
+    C0 = inputs.matrix(n, n, SEED + 2, "normal", device="cuda")
+    C = C0.clone()
+    flops = 2.0 * n ** 3
+    tiles = (-(-n // 128)) ** 2
+    rng = np.random.default_rng(SEED)
+    rows = np.sort(rng.choice(n, size=args.split_rows, replace=False))
+    Ah, Bh, C0h = A.cpu().T.numpy(), B.cpu().T.numpy(), C0.cpu().T.numpy()
+    refs = []
+    for i in rows:
+        r, E = oracle.gemm("N", "N", 1.0, Ah[i:i + 1], Bh, 1.0, C0h[i:i + 1], want_E=True)
+        refs.append((r[0], E[0]))
+
+    def one(fn):
+        C.copy_(C0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        out = fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    def row_errors(tol_scale):
+        out = C.cpu().T.numpy()
+        worst_rel, within = 0.0, True
+        for i, (r, E) in zip(rows, refs):
+            worst_rel = max(worst_rel, float(np.abs(out[i] - r).max() / np.abs(r).max()))
+            within = within and bool(np.all(np.abs(out[i] - r) <= tol_scale(E)))
+        return out, worst_rel, within
+
+    res = {}
+    # FP64 FT-DGEMM
+    t_no, _ = one(lambda: ftgemm.ftgemm_d_noft("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n))
+    t_ft, _ = one(lambda: ftgemm.ftgemm_d("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, loc_cap=0))
+    nflip = max(1, int(round(args.flip_rate * t_ft / 60.0)))
+    assert ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nflip) == 0
+    try:
+        t_inj, (rc, rep) = one(lambda: ftgemm.ftgemm_d("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n,
+                                                       loc_cap=65536))
+        log = ftgemm.ftgemm_injection_log()
+    finally:
+        ftgemm.ftgemm_set_injection(mode=0)
+    out, rel, within = row_errors(lambda E: oracle.parity_tol(n, E))
+    # every injected element against the oracle (faults below the threshold
+    # stay, within their own effect)
+    inj_ok = 0
+    for L in log:
+        i, j = L["row"], L["col"]
+        r, E = oracle.gemm("N", "N", 1.0, Ah[i:i + 1], Bh[:, j:j + 1], 1.0, C0h[i:i + 1, j:j + 1], want_E=True)
+        d = L["after"] - L["before"]
+        eff = abs(d) if np.isfinite(d) else float("inf")
+        # above-threshold faults are corrected; below-threshold ones stay
+        err = abs(out[i, j] - r[0, 0])
+        if err <= oracle.parity_tol(n, E)[0, 0] or (np.isfinite(eff) and err <= 2 * eff + oracle.parity_tol(n, E)[0, 0]):
+            inj_ok += 1
+    res["fp64_dfma"] = {"tflops": flops / t_ft / 1e12, "unprotected_tflops": flops / t_no / 1e12,
+                        "pct_fp64_peak": 100.0 * flops / t_ft / 1e12 / FP64_PEAK_TFLOPS,
+                        "ft_overhead_pct": 100.0 * (t_ft / t_no - 1.0), "s": t_ft,
+                        "injected_call_tflops": flops / t_inj / 1e12, "flip_rate_per_min": args.flip_rate,
+                        "flips": nflip, "detected": rep["detected"], "corrected": rep["corrected"],
+                        "checksum_only": rep["checksum_only"], "rc": rc,
+                        "injected_elements_within_bound": inj_ok, "sampled_rows_within_parity_bound": within,
+                        "max_rel_err_sampled_rows": rel}
+    print(json.dumps({"fp64_dfma": res["fp64_dfma"]}), flush=True)
+    # emulated FP64 on the tensor cores
+    w = 5  # slice width at this K
+    for S in (7, 11):
+        npairs = S * (S + 1) // 2
+        t_no, _ = one(lambda: ftgemm.ftgemm_d_split("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, nslices=S,
+                                                    ft=0, report=False))
+        t_ft, _ = one(lambda: ftgemm.ftgemm_d_split("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n, nslices=S,
+                                                    ft=2, report=False))
+        nf = math.ceil(tiles / 64)
+        flips = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(npairs)), 62) for _ in range(nf)]
+        assert ftgemm.ftgemm_set_injection(mode=2, flips=flips) == 0
+        try:
+            _, (rc, rep) = one(lambda: ftgemm.ftgemm_d_split("N", "N", n, n, n, 1.0, A, n, B, n, 1.0, C, n,
+                                                             nslices=S, ft=2, loc_cap=0))
+        finally:
+            ftgemm.ftgemm_set_injection(mode=0)
+        _, rel, _ = row_errors(lambda E: oracle.parity_tol(n, E))
+        res[f"emulated_S{S}_fp64ck"] = {"tflops_fp64_equiv": flops / t_ft / 1e12,
+                                        "unprotected_tflops": flops / t_no / 1e12,
+                                        "ft_overhead_pct": 100.0 * (t_ft / t_no - 1.0), "s": t_ft,
+                                        "bits_kept": w * S, "flips": nf, "detected": rep["detected"], "rc": rc,
+                                        "max_rel_err_sampled_rows": rel}
+        print(json.dumps({f"emulated_S{S}_fp64ck": res[f"emulated_S{S}_fp64ck"]}), flush=True)
+    print(json.dumps({"metric": "config 5: FT-GEMM at 32768^3, normal(0,1), beta 1, flips at a rate",
+                      "config": {"workload": f"ftdgemm_{n}cubed_normal_a1_b1_rate{args.flip_rate:g}perminute",
+                                 "rows_checked": len(rows)}, "results": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,8 +595,14 @@ def main():
     ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
     ap.add_argument("--split-engine", default="tc,mma", help="split engines: tc (tcgen05), mma (mma.sync)")
     ap.add_argument("--split-forms", default="", help="comma list of form names to run (default: all)")
+    ap.add_argument("--config5", action="store_true", help="32768^3 normal(0,1), beta 1, flips at a rate")
+    ap.add_argument("--flip-rate", type=float, default=360.0, help="flips per minute for --config5")
     args = ap.parse_args()
+    if args.config5 and args.size == 8192:
+        args.size = 32768
     set_size(args.size)
+    if args.config5:
+        return config5(args)
     if args.sweep:
         return sweep(args)
     if args.split:
