@@ -755,6 +755,9 @@ def main():
                          "ft_tflops": flops * args.steps / t_ft / 1e12,
                          "main_kernel_ft_vs_noft": 100.0 * ((ft_ms / max(1, ft_n)) / (noft_ms / max(1, noft_n)) - 1.0),
                          "unfused_vs_noft": 100.0 * (t_unf / t_noft - 1.0)},
+        "checksum_pass": {"ms": ft_aux / max(1, ft_n), "bytes_read": 8 * (M * K + K * N),
+                          "gbs": 8 * (M * K + K * N) / (max(1e-9, ft_aux / max(1, ft_n)) / 1e3) / 1e9,
+                          "what": "operand checksum vectors (and the report reset) before each fault-free call"},
         "errors": {"injected_per_step": FLIPS, "detected_per_step": det[-1] if det else None,
                    "corrected_per_step": cor[-1] if cor else None,
                    "detected_total": sum(det), "corrected_total": sum(cor),
