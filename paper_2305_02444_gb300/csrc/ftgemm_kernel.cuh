@@ -95,6 +95,25 @@ __device__ __forceinline__ void recompute_elem(const Params &p, double *sC, int 
   }
 }
 
+// One k-slab of the tile product for this thread's PP x QQ accumulator
+// blocks (rows tx + 16 pp, columns ty + 16 qq).
+template <bool TA, bool TB, int PP, int QQ>
+__device__ __forceinline__ void slab_fma(double (&acc)[8][8], const unsigned char *sA, const unsigned char *sB,
+                                         int tx, int ty) {
+#pragma unroll
+  for (int k = 0; k < BK; ++k) {
+    double a[PP], b[QQ];
+#pragma unroll
+    for (int pp = 0; pp < PP; ++pp) a[pp] = stage_a<TA>(sA, tx + 16 * pp, k);
+#pragma unroll
+    for (int qq = 0; qq < QQ; ++qq) b[qq] = stage_b<TB>(sB, k, ty + 16 * qq);
+#pragma unroll
+    for (int pp = 0; pp < PP; ++pp)
+#pragma unroll
+      for (int qq = 0; qq < QQ; ++qq) acc[pp][qq] = fma(a[pp], b[qq], acc[pp][qq]);
+  }
+}
+
 // MODE 0: the whole tile (mainloop + epilogue).
 // MODE 1: split-K partial: one k-range of a tile; stores the raw partial
 //         product and its predicted-checksum partials for MODE 2.
@@ -175,6 +194,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   }
 
   const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16*pp, columns ty + 16*qq
+  const int rblk = mI <= 32 ? 2 : mI <= 64 ? 4 : 8, cblk = nJt <= 32 ? 2 : nJt <= 64 ? 4 : 8;
   double acc[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
@@ -198,18 +218,18 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     if (ok) {
     const unsigned char *sA = smem + st * STAGE_BYTES;
     const unsigned char *sB = sA + A_BYTES;
-#pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      double a[8], b[8];
-#pragma unroll
-      for (int pp = 0; pp < 8; ++pp) a[pp] = stage_a<TA>(sA, tx + 16 * pp, k);
-#pragma unroll
-      for (int qq = 0; qq < 8; ++qq) b[qq] = stage_b<TB>(sB, k, ty + 16 * qq);
-#pragma unroll
-      for (int pp = 0; pp < 8; ++pp)
-#pragma unroll
-        for (int qq = 0; qq < 8; ++qq) acc[pp][qq] = fma(a[pp], b[qq], acc[pp][qq]);
-    }
+    // rows tx + 16 pp >= mI and columns ty + 16 qq >= nJt hold zeros (TMA
+    // zero fill): a tile with at most 64 (32) valid rows or columns skips
+    // those blocks' FMAs, leaving the same bits
+    if (rblk == 8 && cblk == 8) slab_fma<TA, TB, 8, 8>(acc, sA, sB, tx, ty);
+    else if (rblk == 8 && cblk == 4) slab_fma<TA, TB, 8, 4>(acc, sA, sB, tx, ty);
+    else if (rblk == 8) slab_fma<TA, TB, 8, 2>(acc, sA, sB, tx, ty);
+    else if (rblk == 4 && cblk == 8) slab_fma<TA, TB, 4, 8>(acc, sA, sB, tx, ty);
+    else if (rblk == 4 && cblk == 4) slab_fma<TA, TB, 4, 4>(acc, sA, sB, tx, ty);
+    else if (rblk == 4) slab_fma<TA, TB, 4, 2>(acc, sA, sB, tx, ty);
+    else if (cblk == 8) slab_fma<TA, TB, 2, 8>(acc, sA, sB, tx, ty);
+    else if (cblk == 4) slab_fma<TA, TB, 2, 4>(acc, sA, sB, tx, ty);
+    else slab_fma<TA, TB, 2, 2>(acc, sA, sB, tx, ty);
     if (FT) {
       const double *scs = reinterpret_cast<const double *>(sA + A_BYTES + B_BYTES);
       if (tid < 128) {
