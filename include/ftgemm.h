@@ -315,14 +315,20 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
  * 1 never splits, n >= 2 forces n splits (fewer when K is short). */
 int ftgemm_set_splitk(int nsplit);
 
-/* Engine of ftgemm_d_split (results: the same bits for the emulated forms,
- * within the same bound for the plain BF16 form).  0 (default): the slice
- * products on the tcgen05 tensor cores (FP32 accumulators and the FP64 fold
- * in tensor memory) in 2 x 2 thread-block clusters that share each A and B
- * slab through TMA multicast, when ft is 0 or 2; 2: the same kernel with one
- * CTA per tile and no cluster; 1: every call on the mma.sync kernel.  ft = 1
- * (FP32 checksums summed from the staged slices on the CUDA cores) always
- * runs on the mma.sync kernel.  Returns -1 for another value. */
+/* Engine of ftgemm_d_split (results: the same bits for the emulated forms
+ * on every engine, and for the plain BF16 form on the tcgen05 engines).
+ * The tcgen05 engines run the slice products on the 5th-generation tensor
+ * cores with the FP32 accumulators and the FP64 fold in tensor memory, when
+ * ft is 0 or 2:
+ *   2: one CTA per 128 x 128 tile;
+ *   3 / 4: the same kernel in 1 x 2 / 2 x 2 thread-block clusters that
+ *      share each A (and B) slab through TMA multicast;
+ *   5: persistent, one CTA per SM walking its tiles, each tile finished
+ *      from tensor memory while the next one's loads and MMAs run;
+ *   0 (default): engine 5.
+ * 1: every call on the mma.sync kernel.  ft = 1 (FP32 checksums summed from
+ * the staged slices on the CUDA cores) always runs on the mma.sync kernel.
+ * Process-global; returns -1 for another value. */
 int ftgemm_set_split_engine(int engine);
 
 /* Per-k-panel verification (FT-BLAS style; FT-GEMM blocks K by K_C, §2.1):

@@ -125,6 +125,9 @@ struct SplitParams {
   // power-of-two scales of the checksum operands' rows (tile rows I of the
   // column sums of op(A), tile columns J of the row sums of op(B))
   const int *ePA, *ePB;
+  // persistent kernel: one 128 x 128 FP64 tile per CTA, where the flagged
+  // elements of a tile are recomputed before the tile is copied to C
+  double *tscratch;
 };
 
 

@@ -44,8 +44,10 @@ cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const C
                          const SplitParams &p, cudaStream_t s);
 cudaError_t launch_split_tc(bool ta, bool tb, int ck, int cluster, const CUtensorMap &a, const CUtensorMap &b,
                             const CUtensorMap &b2, const SplitParams &p, cudaStream_t s);
+cudaError_t launch_split_tcp(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
+                             const SplitParams &p, int nctas, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
-                           int S, int w, int plain, void *out, cudaStream_t s);
+                           int S, int w, int plain, void *out, unsigned long long *mb, int nsm, cudaStream_t s);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
 cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
                            const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
@@ -82,6 +84,8 @@ struct Workspace {
   Buf uC, uccs, uccsa, ucrs, ucrsa, uP1, uP2;  // unfused ablation: copy of C, C sums, skinny GEMMs
   Buf spA, spB, spEA, spEB;  // split precision: bf16 slices and row/column exponents
   Buf spPA, spPB, spEPA, spEPB;  // slices / exponents of the checksum operands (tcgen05 engine, ft = 2)
+  Buf tscr;                      // persistent split kernel: one FP64 tile per CTA for flagged tiles
+  Buf spMB;                      // row maxima of the slicing passes
   cudaStream_t side = nullptr;   // second stream for independent work inside one call (fork / join)
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int nsm = 0;              // SM count
@@ -217,9 +221,11 @@ bool tma_ok(const void *p, long long ld) {
 
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
-// split precision: 0 tcgen05 (default cluster shape), 1 mma.sync, 2 / 3 / 4 tcgen05 in clusters of 1 / 2 / 4 CTAs
+// split precision: 0 default (persistent tcgen05), 1 mma.sync, 2 / 3 / 4 tcgen05 in clusters of 1 / 2 / 4
+// CTAs, 5 persistent tcgen05
 int g_split_engine = 0;
 constexpr int SPLIT_DEFAULT_CLUSTER = 1;
+constexpr bool SPLIT_DEFAULT_PERSISTENT = true;
 int g_correct = 0;  // correction rule of the FP64 kernels (ftgemm_set_correction)
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
 int g_panel = 0;   // verify the accumulators every g_panel k-slabs (0: only at the end of the tile)
@@ -887,7 +893,7 @@ int ftgemm_set_panel_check(int kslabs) {
 
 int ftgemm_set_split_engine(int engine) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (engine < 0 || engine > 4) return -1;
+  if (engine < 0 || engine > 5) return -1;
   g_split_engine = engine;
   return 0;
 }
@@ -965,7 +971,7 @@ int ftgemm_finalize(void) {
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
                   &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
-                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB};
+                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -1634,14 +1640,27 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     cudaMemsetAsync(w.spEB.p, 0, sizeof(int) * N, s);
   }
   // op(A)(i, k): 'T' has k contiguous; op(B)(k, j) seen as row j: 'N' has k contiguous
-  if (launch_slicing(A, lda, ta_t ? 1 : 0, M, K, Kp, (int *)w.spEA.p, S, wbits, plain, w.spA.p, s) != cudaSuccess ||
-      launch_slicing(B, ldb, tb_t ? 0 : 1, N, K, Kp, (int *)w.spEB.p, S, wbits, plain, w.spB.p, s) != cudaSuccess)
+  const int nsm = device_sms(dev);
+  if (ensure(w.spMB, sizeof(unsigned long long) * (size_t)std::max(M, N))) return FTGEMM_ERR_NOMEM;
+  unsigned long long *mb = (unsigned long long *)w.spMB.p;
+  if (launch_slicing(A, lda, ta_t ? 1 : 0, M, K, Kp, (int *)w.spEA.p, S, wbits, plain, w.spA.p, mb, nsm, s) !=
+          cudaSuccess ||
+      launch_slicing(B, ldb, tb_t ? 0 : 1, N, K, Kp, (int *)w.spEB.p, S, wbits, plain, w.spB.p, mb, nsm, s) !=
+          cudaSuccess)
     return FTGEMM_ERR_CUDA;
   g_launches += plain ? 2 : 4;
   // tcgen05 kernel (ft 0 / 2): 2 x 2 clusters load 64-row halves; otherwise whole 128-row slabs
   const bool tc = g_split_engine != 1 && ft != 1;
   const int cl = !tc ? 1 : g_split_engine == 0 ? SPLIT_DEFAULT_CLUSTER : g_split_engine == 3 ? 2
                  : g_split_engine == 4 ? 4 : 1;
+  const bool persist = tc && (g_split_engine == 5 || (g_split_engine == 0 && SPLIT_DEFAULT_PERSISTENT));
+  // one tcgen05 launch: persistent (at most one CTA per SM) or one CTA per tile
+  auto run_tc = [&](bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &b2,
+                    const SplitParams &q, cudaStream_t st) {
+    if (persist)
+      return launch_split_tcp(ta, tb, ck, a, b, q, (int)std::min<long long>((long long)q.nI * q.nJ, nsm), st);
+    return launch_split_tc(ta, tb, ck, cl, a, b, b2, q, st);
+  };
   const int boxA = cl == 1 ? SP_BM : SP_BM / 2, boxB = cl == 4 ? SP_BM / 2 : SP_BM;
   CUtensorMap mA, mB, mB2;
   if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S, boxA)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S, boxB)))
@@ -1685,10 +1704,10 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
       if (ensure(w.spPA, (size_t)S * nI * Kp * 2) || ensure(w.spPB, (size_t)S * nJ * Kp * 2) ||
           ensure(w.spEPA, sizeof(int) * nI) || ensure(w.spEPB, sizeof(int) * nJ))
         return FTGEMM_ERR_NOMEM;
-      if (launch_slicing((const double *)w.acs.p, Kq, 1, nI, K, Kp, (int *)w.spEPA.p, S, wbits, 0, w.spPA.p, s) !=
-              cudaSuccess ||
-          launch_slicing((const double *)w.bcs.p, Kq, 1, nJ, K, Kp, (int *)w.spEPB.p, S, wbits, 0, w.spPB.p, s) !=
-              cudaSuccess)
+      if (launch_slicing((const double *)w.acs.p, Kq, 1, nI, K, Kp, (int *)w.spEPA.p, S, wbits, 0, w.spPA.p, mb,
+                         nsm, s) != cudaSuccess ||
+          launch_slicing((const double *)w.bcs.p, Kq, 1, nJ, K, Kp, (int *)w.spEPB.p, S, wbits, 0, w.spPB.p, mb,
+                         nsm, s) != cudaSuccess)
         return FTGEMM_ERR_CUDA;
       g_launches += 4;
       CUtensorMap mPA, mPB;
@@ -1708,8 +1727,8 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
         return FTGEMM_ERR_CUDA;
       cudaEventRecord(w.fork_ev, s);
       cudaStreamWaitEvent(w.side, w.fork_ev, 0);
-      if (launch_split_tc(false, false, 0, cl, mPA, mB, mB, q1, s) != cudaSuccess ||
-          launch_split_tc(false, false, 0, cl, mA, mPB, mPB, q2, w.side) != cudaSuccess)
+      if (run_tc(false, false, 0, mPA, mB, mB, q1, s) != cudaSuccess ||
+          run_tc(false, false, 0, mA, mPB, mPB, q2, w.side) != cudaSuccess)
         return FTGEMM_ERR_CUDA;
       cudaEventRecord(w.join_ev, w.side);
       cudaStreamWaitEvent(s, w.join_ev, 0);
@@ -1738,8 +1757,12 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  if ((tc ? launch_split_tc(ta_t, tb_t, ft, cl, mA, mB, mB2, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
-      cudaSuccess)
+  if (persist && ft == 2) {
+    if (ensure(w.tscr, sizeof(double) * SP_BM * SP_BN * (size_t)std::min<long long>(nI * nJ, nsm)))
+      return FTGEMM_ERR_NOMEM;
+    p.tscratch = (double *)w.tscr.p;
+  }
+  if ((tc ? run_tc(ta_t, tb_t, ft, mA, mB, mB2, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) != cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);
   g_launches++;

@@ -1,6 +1,8 @@
 // Split-precision mma.sync kernel instantiations (all operand layouts, with
 // and without the fault tolerance), and the slicing kernels with their
 // launcher.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 
 #include "ftgemm_split.cuh"
@@ -52,99 +54,228 @@ __device__ __forceinline__ int exponent_above(unsigned long long mb) {
   return ilog + 1;
 }
 
-// Row exponent: e(r) with max_k |x(r, k)| < 2^e(r) over the finite entries.
-// X is op(X) given by (ptr, ld, trans): element (r, k) = trans ? X[k + r*ld] : X[r + k*ld].
-__global__ void __launch_bounds__(256) split_rowexp_kernel(const double *__restrict__ X, long long ld, int trans,
-                                                           long long R, long long K, int *__restrict__ e) {
-  if (trans) {  // k contiguous: one warp per row
-    const long long r = (long long)blockIdx.x * 8 + threadIdx.x / 32;
+// Row maxima of |op(X)| over the finite entries, as ordered bits, combined
+// across the k-splits of the grid (blockIdx.y) by atomicMax into mb (zeroed
+// before).  op(X)(r, k) = trans ? X[k + r*ld] : X[r + k*ld].  trans = 0 (r
+// contiguous): a thread per row, a warp reads 32 consecutive rows per k;
+// trans = 1 (k contiguous): a warp per row, lanes along k.  Eight loads in
+// flight per thread.
+__global__ void __launch_bounds__(256) split_rowmax_kernel(const double *__restrict__ X, long long ld, int trans,
+                                                           long long R, long long K, long long kper,
+                                                           unsigned long long *__restrict__ mb) {
+  const long long k0 = (long long)blockIdx.y * kper, k1 = min(K, k0 + kper);
+  unsigned long long m = 0;
+  long long r;
+  if (!trans) {
+    r = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (r >= R) return;
+    const double *x = X + r;
+    long long k = k0;
+    for (; k + 8 <= k1; k += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = x[(k + u) * ld];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) m = max(m, abs_bits_finite(v[u]));
+    }
+    for (; k < k1; ++k) m = max(m, abs_bits_finite(x[k * ld]));
+  } else {
+    r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= R) return;
-    unsigned long long m = 0;
-    for (long long k = lane; k < K; k += 32) m = max(m, abs_bits_finite(X[k + r * ld]));
+    const double *x = X + r * ld;
+    long long k = k0 + lane;
+    for (; k + 7 * 32 < k1; k += 8 * 32) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = x[k + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) m = max(m, abs_bits_finite(v[u]));
+    }
+    for (; k < k1; k += 32) m = max(m, abs_bits_finite(x[k]));
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[r] = exponent_above(m);
-  } else {  // r contiguous: 32 rows x 8 k-groups per block
-    __shared__ unsigned long long part[8][32];
-    const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const long long r = (long long)blockIdx.x * 32 + rl;
-    unsigned long long m = 0;
-    if (r < R) {
-#pragma unroll 4
-      for (long long k = g; k < K; k += 8) m = max(m, abs_bits_finite(X[r + k * ld]));
-    }
-    part[g][rl] = m;
-    __syncthreads();
-    if (g == 0 && r < R) {
-      for (int q = 1; q < 8; ++q) m = max(m, part[q][rl]);
-      e[r] = exponent_above(m);
-    }
+    if (lane != 0) return;
   }
+  if (m) atomicMax(mb + r, m);
 }
 
-// Slice s of x: sign(x) * (floor(|x| 2^(w(s+1) - eR)) mod 2^w), exact, from
-// the bits of x (|x| = m 2^(E' - 1075) with the 53-bit integer m).  This is
-// the error-free splitting x 2^-eR = sum_s n_s 2^-w(s+1) + r, |n_s| < 2^w.
-__device__ __forceinline__ int slice_of(unsigned long long m, int base, int w, int s) {
-  const int t = base + w * (s + 1);
-  unsigned long long q;
-  if (t >= 0) q = (t >= w) ? 0ull : (m << t);
-  else q = (t <= -64) ? 0ull : (m >> (-t));
-  return (int)(q & ((1ull << w) - 1ull));
+// x rounded to bf16, to nearest with ties to even (the result of
+// __double2bfloat16): the fields are rounded with integer operations when the
+// result is a normal bf16 number or overflows, the conversion handles zeros,
+// subnormal results, Inf and NaN.
+__device__ __forceinline__ uint32_t bf16_rn_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF), eb = E - 1023 + 127;
+  if (E != 0x7FF && eb >= 1 && eb <= 254) {
+    const unsigned long long rest = b & ((1ull << 45) - 1ull), half = 1ull << 44;
+    uint32_t v = ((uint32_t)eb << 7) | (uint32_t)((b >> 45) & 0x7Fu);
+    v += (rest > half || (rest == half && (v & 1u))) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
+    return ((uint32_t)(b >> 48) & 0x8000u) | v;
+  }
+  return (uint32_t)__bfloat16_as_ushort(__double2bfloat16(x));
 }
 
-// Slices: out[s][r][k] (bf16, row length Kp, zero padded), 64 x 64 tiles through
-// shared memory so that both the read and the write are coalesced.  A
-// non-finite entry is carried by slice 0 (the product is then not finite).
-__global__ void __launch_bounds__(256) split_slice_kernel(const double *__restrict__ X, long long ld, int trans,
-                                                          long long R, long long K, long long Kp,
-                                                          const int *__restrict__ e, int S, int w, int plain,
+// floor(m 2^t) mod 2^64 for the 53-bit integer m and any t.
+__device__ __forceinline__ unsigned long long shift_trunc(unsigned long long m, int t) {
+  if (t >= 0) return t >= 64 ? 0ull : (m << t);
+  return t <= -64 ? 0ull : (m >> (-t));
+}
+
+// The error-free splitting x 2^-e(r) = sum_s n_s 2^-w(s+1) + r with
+// |n_s| < 2^w: slice s of x is sign(x) (floor(|x| 2^(w(s+1) - e(r))) mod 2^w),
+// taken exactly from the bits of x.
+// One entry prepared for slicing.  With |x| 2^-e(r) = m 2^base (m the 53-bit
+// integer of x), slice s is n_s = floor(m 2^(base + w(s+1))) mod 2^w.  The
+// first S1 = floor(64 / w) slices come from f1 = floor(m 2^(base + w S1)) (an
+// integer below 2^(w S1), as |x| 2^-e(r) < 1), the others from the low 64
+// bits f2 of floor(m 2^(base + w S)); then n_s is a field of f1 or f2 at a
+// shift that is the same for every entry.  nfb: the bf16 bits of a
+// non-finite entry (carried by slice 0), else 0.
+struct SliceIn {
+  unsigned long long f1, f2;
+  uint32_t sg, nfb;
+};
+
+__device__ __forceinline__ SliceIn slice_prep(double x, int er, int w, int S, int S1) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  SliceIn q;
+  q.sg = (uint32_t)(b >> 48) & 0x8000u;
+  q.nfb = E == 0x7FF ? (uint32_t)__bfloat16_as_ushort(__double2bfloat16(x)) : 0u;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+  const int base = (E ? E : 1) - 1075 - er;
+  q.f1 = shift_trunc(m, base + w * S1);
+  q.f2 = S > S1 ? shift_trunc(m, base + w * S) : 0ull;
+  return q;
+}
+
+// bf16 bits of slice s: the w-bit field, converted exactly (n < 2^8 as the
+// FP32 (2^23 + n) - 2^23, whose low 16 bits are zero), with the entry's sign.
+__device__ __forceinline__ uint32_t slice_bits(const SliceIn &q, int w, int S, int S1, int s) {
+  if (q.nfb) return s == 0 ? q.nfb : 0u;
+  const unsigned long long f = s < S1 ? q.f1 : q.f2;
+  const int c = s < S1 ? w * (S1 - 1 - s) : w * (S - 1 - s);
+  const uint32_t n = (uint32_t)(f >> c) & ((1u << w) - 1u);
+  if (!n) return 0u;
+  return q.sg | (__float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | n), 8388608.0f)) >> 16);
+}
+
+// Slices: out[s][r][k] (bf16, row length Kp, zero padded past K); plain: the
+// bf16 rounding of each entry.  The row exponent e(r) (max |op(X)(r, :)| <
+// 2^e(r), 0 for a zero row) comes from the row maxima mb and is written to e
+// by the threads of k-block 0.
+//   trans = 1 (k contiguous): a warp per row; each lane takes two consecutive
+//     k of each of four 64-k spans (bf16x2 stores);
+//   trans = 0 (r contiguous): a thread per row and 8 consecutive k (a 16-byte
+//     store per slice), a warp reads 32 consecutive rows per k; the 8 warps
+//     take the 8 8-k groups of a 64-k block.
+// Eight loads in flight per thread.
+template <int trans, int plain>
+__global__ void __launch_bounds__(256) split_slice_kernel(const double *__restrict__ X, long long ld, long long R,
+                                                          long long K, long long Kp,
+                                                          const unsigned long long *__restrict__ mb,
+                                                          int *__restrict__ e, int S, int w,
                                                           __nv_bfloat16 *__restrict__ out) {
-  __shared__ double t[64][65];
-  const long long r0 = (long long)blockIdx.y * 64, k0 = (long long)blockIdx.x * 64;
-  for (int q = threadIdx.x; q < 64 * 64; q += 256) {
-    int rr, kk;
-    if (trans) { kk = q & 63; rr = q >> 6; } else { rr = q & 63; kk = q >> 6; }
-    const long long r = r0 + rr, k = k0 + kk;
-    double v = 0.0;
-    if (r < R && k < K) v = trans ? X[k + r * ld] : X[r + k * ld];
-    t[rr][kk] = v;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < 64 * 64; q += 256) {
-    const int kk = q & 63, rr = q >> 6;
-    const long long r = r0 + rr, k = k0 + kk;
-    if (r >= R || k >= Kp) continue;
-    const double x = t[rr][kk];
-    if (plain) {
-      out[r * Kp + k] = __double2bfloat16(x);
-      continue;
+  uint16_t *o16 = reinterpret_cast<uint16_t *>(out);
+  const long long RK = R * Kp;
+  const int ns = plain ? 1 : S;
+  if constexpr (trans != 0) {
+    const long long r = (long long)blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= R) return;
+    const int er = plain ? 0 : exponent_above(mb[r]);
+    if (!plain && blockIdx.x == 0 && lane == 0) e[r] = er;
+    const long long kb = (long long)blockIdx.x * 256 + 2 * lane;  // k of span u: kb + 64 u
+    const double *x = X + r * ld;
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long k = kb + 64 * (u >> 1) + (u & 1);
+      v[u] = k < K ? x[k] : 0.0;
     }
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int E = (int)((b >> 52) & 0x7FF);
-    const bool neg = (b >> 63) != 0;
-    if (E == 0x7FF) {  // Inf / NaN
-      out[r * Kp + k] = __double2bfloat16(x);
-      for (int s = 1; s < S; ++s) out[((long long)s * R + r) * Kp + k] = __float2bfloat16(0.0f);
-      continue;
+    if constexpr (plain != 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long k = kb + 64 * u;
+        if (k < Kp)
+          *reinterpret_cast<uint32_t *>(o16 + r * Kp + k) =
+              bf16_rn_bits(v[2 * u]) | (bf16_rn_bits(v[2 * u + 1]) << 16);
+      }
+    } else {
+      const int S1 = min(S, 64 / w);
+      SliceIn q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = slice_prep(v[u], er, w, S, S1);
+      for (int s = 0; s < ns; ++s) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long k = kb + 64 * u;
+          if (k < Kp)
+            *reinterpret_cast<uint32_t *>(o16 + s * RK + r * Kp + k) =
+                slice_bits(q[2 * u], w, S, S1, s) | (slice_bits(q[2 * u + 1], w, S, S1, s) << 16);
+        }
+      }
     }
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
-    const int base = (E ? E : 1) - 1075 - e[r];
-    for (int s = 0; s < S; ++s) {
-      const int n = slice_of(m, base, w, s);                           // 0 <= n < 2^w <= 256
-      out[((long long)s * R + r) * Kp + k] = __float2bfloat16_rn((float)(neg ? -n : n));  // exact
+  } else {
+    const long long r = (long long)blockIdx.y * 32 + (threadIdx.x & 31);
+    const int g = threadIdx.x >> 5;
+    if (r >= R) return;
+    const int er = plain ? 0 : exponent_above(mb[r]);
+    if (!plain && blockIdx.x == 0 && g == 0) e[r] = er;
+    const long long k0 = (long long)blockIdx.x * 64 + 8 * g;
+    const double *x = X + r;
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = k0 + u < K ? x[(k0 + u) * ld] : 0.0;
+    uint4 *dst = reinterpret_cast<uint4 *>(o16 + r * Kp + k0);  // 16-byte aligned (Kp is a multiple of 64)
+    if constexpr (plain != 0) {
+      uint32_t h[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) h[u] = bf16_rn_bits(v[2 * u]) | (bf16_rn_bits(v[2 * u + 1]) << 16);
+      *dst = make_uint4(h[0], h[1], h[2], h[3]);
+    } else {
+      const int S1 = min(S, 64 / w);
+      SliceIn q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = slice_prep(v[u], er, w, S, S1);
+      for (int s = 0; s < ns; ++s) {
+        uint32_t h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          h[u] = slice_bits(q[2 * u], w, S, S1, s) | (slice_bits(q[2 * u + 1], w, S, S1, s) << 16);
+        dst[s * (RK / 8)] = make_uint4(h[0], h[1], h[2], h[3]);
+      }
     }
   }
 }
 
+// Row exponents (unless plain) and slices of op(X) (R x K, padded to Kp);
+// mb: R words of device scratch for the row maxima; nsm: the SM count (sizes
+// the k-split of the maxima pass).
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
-                           int S, int w, int plain, void *out, cudaStream_t s) {
+                           int S, int w, int plain, void *out, unsigned long long *mb, int nsm, cudaStream_t s) {
+  if (R <= 0) return cudaSuccess;
   if (!plain) {
-    if (trans) split_rowexp_kernel<<<(unsigned)((R + 7) / 8), 256, 0, s>>>(X, ld, trans, R, K, e);
-    else split_rowexp_kernel<<<(unsigned)((R + 31) / 32), 256, 0, s>>>(X, ld, trans, R, K, e);
+    cudaError_t err = cudaMemsetAsync(mb, 0, sizeof(unsigned long long) * (size_t)R, s);
+    if (err != cudaSuccess) return err;
+    // enough warps to cover every SM several times over, k-ranges of at least 64
+    const long long rows_per_block = trans ? 8 : 256, bx = (R + rows_per_block - 1) / rows_per_block;
+    const long long want = (long long)nsm * 8, ksplit = std::max(1LL, std::min((K + 63) / 64, (want + bx - 1) / bx));
+    const long long kper = (K + ksplit - 1) / ksplit;
+    split_rowmax_kernel<<<dim3((unsigned)bx, (unsigned)((K + kper - 1) / kper)), 256, 0, s>>>(X, ld, trans, R, K,
+                                                                                             kper, mb);
   }
-  dim3 grid((unsigned)((Kp + 63) / 64), (unsigned)((R + 63) / 64));
-  split_slice_kernel<<<grid, 256, 0, s>>>(X, ld, trans, R, K, Kp, e, S, w, plain, (__nv_bfloat16 *)out);
+  __nv_bfloat16 *o = (__nv_bfloat16 *)out;
+  if (trans) {
+    dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)((R + 7) / 8));
+    if (plain) split_slice_kernel<1, 1><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
+    else split_slice_kernel<1, 0><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
+  } else {
+    dim3 grid((unsigned)(Kp / 64), (unsigned)((R + 31) / 32));
+    if (plain) split_slice_kernel<0, 1><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
+    else split_slice_kernel<0, 0><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
+  }
   return cudaGetLastError();
 }
 

@@ -78,6 +78,72 @@ __device__ __forceinline__ float warp_sum_ru(float v) {
 }
 
 
+// Recompute the flagged elements of a tile from the original FP64 operands:
+// the flagged row x column intersections (or, with one side empty or more
+// than 64 of them, the whole flagged row and column segments).  buf holds the
+// tile's output (column-major 128 x 128, shared or global memory) and takes
+// the recomputed values; a value that differs by more than the element bound
+// counts as detected (cnt[2]) with a location record.  Warp `wid` of `nw`
+// warps takes every nw-th candidate; the caller synchronises.
+template <bool TA, bool TB>
+__device__ __forceinline__ void split_tile_recompute(const SplitParams &p, double *buf, const int *s_fr,
+                                                     const int *s_fc, int *cnt, int tile, int I, int J, int wid,
+                                                     int nw, int lane) {
+  const int i0 = I * SP_BM, j0 = J * SP_BN;
+  const int mI = (int)min((long long)SP_BM, p.M - i0), nJt = (int)min((long long)SP_BN, p.N - j0);
+  const bool use_c = p.beta != 0.0;
+  const int nr = cnt[0], nc = cnt[1];
+  const bool inter = nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT;
+  const int ncand = inter ? nr * nc : (nr + nc > 0) ? (nr * nJt + nc * mI) : 0;
+  for (int e = wid; e < ncand; e += nw) {
+    int il, jl;
+    if (inter) { il = s_fr[e / nc]; jl = s_fc[e % nc]; }
+    else if (e < nr * nJt) { il = s_fr[e / nJt]; jl = e % nJt; }
+    else { il = (e - nr * nJt) % mI; jl = s_fc[(e - nr * nJt) / mI]; }
+    const long long gi = i0 + il, gj = j0 + jl;
+    double dot = 0.0, ab = 0.0;
+    for (long long k = lane; k < p.K; k += 32) {
+      const double av = sp_glob_a<TA, TB>(p, gi, k), bv = sp_glob_b<TA, TB>(p, k, gj);
+      dot = fma(av, bv, dot);
+      ab = fma(fabs(av), fabs(bv), ab);
+    }
+    dot = warp_sum(dot);
+    ab = warp_sum(ab);
+    if (lane == 0) {
+      const double c = use_c ? p.C[gi + gj * p.ldc] : 0.0;
+      const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
+      // the emulated value may differ from the FP64 one by the splitting error
+      // (plain BF16: the input rounding) plus FP64 roundings
+      const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
+      const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
+                                         : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
+      const double te = fabs(p.alpha) * split_err +
+                        2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
+      const double old = buf[jl * SP_BM + il];
+      if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
+        atomicAdd(&cnt[2], 1);
+        const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
+        if ((long long)q < p.loc_cap) {
+          DevLoc L;
+          L.row = gi; L.col = gj; L.tile = tile; L.kind = 0; L.delta = old - nv;
+          p.loc[q] = L;
+        }
+      }
+      buf[jl * SP_BM + il] = nv;
+    }
+  }
+}
+
+// Add a tile's counters (cnt[0] flagged rows, [1] columns, [2] detected,
+// [4] unverifiable) to the call's report; one thread.
+__device__ __forceinline__ void split_tile_report(const SplitParams &p, const int *cnt) {
+  DevReport *r = p.rep;
+  if (cnt[0]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[0]);
+  if (cnt[1]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[1]);
+  if (cnt[2]) { atomicAdd(&r->detected, (unsigned long long)cnt[2]); atomicAdd(&r->corrected, (unsigned long long)cnt[2]); }
+  if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
+}
+
 // The end of a tile shared by the split kernels, run by 256 threads: sC holds
 // the tile's unscaled FP64 accumulators (column-major, 128 x 128); scale to
 // the output, verify with the FP64 checksums (CK 2), recompute the flagged
@@ -179,56 +245,9 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
     __syncthreads();
   }
   if (CK >= 1) {
-    const int nr = cnt[0], nc = cnt[1];
-    // flagged intersections (or whole flagged segments when one side is empty
-    // or there are more than 64): recompute in FP64 from the original operands
-    const int ncand = (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) ? nr * nc
-                      : (nr + nc > 0) ? (nr * nJt + nc * mI) : 0;
-    for (int e = warp; e < ncand; e += 8) {
-      int il, jl;
-      if (nr > 0 && nc > 0 && nr * nc <= MAX_INTERSECT) { il = s_fr[e / nc]; jl = s_fc[e % nc]; }
-      else if (e < nr * nJt) { il = s_fr[e / nJt]; jl = e % nJt; }
-      else { il = (e - nr * nJt) % mI; jl = s_fc[(e - nr * nJt) / mI]; }
-      const long long gi = i0 + il, gj = j0 + jl;
-      double dot = 0.0, ab = 0.0;
-      for (long long k = lane; k < p.K; k += 32) {
-        const double av = sp_glob_a<TA, TB>(p, gi, k), bv = sp_glob_b<TA, TB>(p, k, gj);
-        dot = fma(av, bv, dot);
-        ab = fma(fabs(av), fabs(bv), ab);
-      }
-      dot = warp_sum(dot);
-      ab = warp_sum(ab);
-      if (lane == 0) {
-        const double c = use_c ? p.C[gi + gj * p.ldc] : 0.0;
-        const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
-        // the emulated value may differ from the FP64 one by the splitting error
-        // (plain BF16: the input rounding) plus FP64 roundings
-        const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
-        const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
-                                           : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
-        const double te = fabs(p.alpha) * split_err +
-                          2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
-        const double old = sC[jl * SP_BM + il];
-        if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
-          atomicAdd(&cnt[2], 1);
-          const unsigned long long q = atomicAdd(&p.rep->n_loc, 1ull);
-          if ((long long)q < p.loc_cap) {
-            DevLoc L;
-            L.row = gi; L.col = gj; L.tile = tile; L.kind = 0; L.delta = old - nv;
-            p.loc[q] = L;
-          }
-        }
-        sC[jl * SP_BM + il] = nv;
-      }
-    }
+    split_tile_recompute<TA, TB>(p, sC, s_fr, s_fc, cnt, tile, I, J, warp, 8, lane);
     __syncthreads();
-    if (tid == 0) {
-      DevReport *r = p.rep;
-      if (cnt[0]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[0]);
-      if (cnt[1]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[1]);
-      if (cnt[2]) { atomicAdd(&r->detected, (unsigned long long)cnt[2]); atomicAdd(&r->corrected, (unsigned long long)cnt[2]); }
-      if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
-    }
+    if (tid == 0) split_tile_report(p, cnt);
   }
   // store (plain coalesced stores: rows of the tile are contiguous in C)
   for (int e = tid; e < SP_BM * SP_BN; e += 256) {

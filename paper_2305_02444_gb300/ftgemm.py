@@ -287,7 +287,8 @@ def ftgemm_set_correction(mode: int) -> int:
 
 
 def ftgemm_set_split_engine(engine: int) -> int:
-    """Split precision: 0 tcgen05 in 2x2 clusters, 2 tcgen05 single CTAs (ft=1: mma.sync), 1 mma.sync."""
+    """Split precision: 0 default (= 5), 1 mma.sync, 2 tcgen05 one CTA per tile, 3 / 4 tcgen05 in
+    1x2 / 2x2 clusters, 5 persistent tcgen05 (ft=1 always runs on mma.sync)."""
     return lib().ftgemm_set_split_engine(engine)
 
 

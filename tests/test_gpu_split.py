@@ -189,7 +189,7 @@ def test_fp64_checksums_see_what_fp32_checksums_miss(ft, orc):
     assert detected[1] < len(flips) // 2
 
 
-ENGINES = (0, 1, 2, 3, 4)   # default, mma.sync, tcgen05 in clusters of 1, 2, 4 CTAs
+ENGINES = (0, 1, 2, 3, 4, 5)   # default, mma.sync, tcgen05 in clusters of 1, 2, 4 CTAs, persistent tcgen05
 
 
 def run_engine(ft, engine, *a, **kw):
@@ -249,7 +249,7 @@ def test_tcgen05_plain_bf16(ft, orc, ta, tb):
     assert 1e-6 < rel < 1e-2
 
 
-@pytest.mark.parametrize("engine", [2, 3, 4])
+@pytest.mark.parametrize("engine", [2, 3, 4, 5])
 def test_tcgen05_injection_log_and_correction(ft, orc, engine):
     """Flips of the tensor-memory FP64 accumulators after chosen slice pairs
     (first, middle, last of 36; one element in each lane quadrant): logged
@@ -275,3 +275,101 @@ def test_tcgen05_injection_log_and_correction(ft, orc, engine):
     assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
     assert rep["detected"] == len(flips)
     assert sorted(l[:2] for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)
+
+
+@pytest.mark.parametrize("ck,S", [(0, 0), (0, 4), (2, 4)])
+def test_persistent_many_tiles_per_cta(ft, orc, ck, S):
+    """2560 x 2690: 420 tiles (ragged last tile column), so each CTA of the
+    persistent grid (one per SM) finishes two or three tiles and the ring and
+    accumulators pass between tiles.  Same bits as one CTA per tile, for the
+    plain BF16 form (finished from the FP32 accumulator), the emulated form
+    without checks and with FP64 checksums."""
+    M, N, K = 2560, 2690, 192
+    A, B, C, ar, br = problem("N", "T", M, N, K, seed=77)
+    outs = {e: run_engine(ft, e, "N", "T", M, N, K, 1.5, -0.5, A, B, C, ar, br, S, ftflag=ck) for e in (2, 5)}
+    np.testing.assert_array_equal(outs[5][0], outs[2][0])
+    for g, r in outs.values():
+        assert r["flagged_rows"] == 0 and r["flagged_cols"] == 0 and r["unverifiable"] == 0
+    if S:
+        ref, E = orc.gemm("N", "T", 1.5, A.T.numpy(), B[:, :br].T.numpy(), -0.5, C.T.numpy(), want_E=True)
+        _, _, sa, sb = scales("N", "T", A, B, ar, br)
+        split = 1.5 * np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+        assert np.all(np.abs(outs[5][0] - ref) <= orc.parity_tol(K, E) + split)
+
+
+def test_persistent_flips_in_later_tiles(ft, orc):
+    """Flips in tiles that a persistent CTA reaches first, second and third
+    (tile t goes to CTA t mod grid): each tile with a fault is recomputed in
+    the CTA's scratch tile, the others are stored directly; all are located
+    and corrected, and the report counts each once."""
+    M, N, K, S = 2048, 2560, 256, 5
+    A, B, C, ar, br = problem("N", "N", M, N, K, seed=91)
+    # (row, col, pair, bit): tiles (0,0), (8,3) and (15,19) of the 16 x 20 grid, two faults in one tile
+    flips = [(3, 4, 0, 62), (1030, 400, 7, 62), (1100, 450, 14, 61), (1990, 2500, 14, 62)]
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        got, rep = run_engine(ft, 5, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
+        log = ft.ftgemm_injection_log()
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    assert [L["applied"] for L in log] == [1] * len(flips)
+    ref, E = orc.gemm("N", "N", 1.0, A.T.numpy(), B.T.numpy(), 1.0, C.T.numpy(), want_E=True)
+    _, _, sa, sb = scales("N", "N", A, B, ar, br)
+    split = np.outer(sa, sb) * K * (S + 4) * 2.0 ** (-wbits(K) * S)
+    assert np.all(np.abs(got - ref) <= orc.parity_tol(K, E) + split)
+    assert rep["detected"] == len(flips) and rep["corrected"] == len(flips)
+    assert sorted(l[:2] for l in rep["locs"]) == sorted((i, j) for i, j, _, _ in flips)
+
+
+def bf16_nearest_even(x: float) -> float:
+    """x rounded to bf16 (8 significant bits, exponents of FP32), to nearest
+    with ties to even, from the definition: Python's round() of an exactly
+    scaled double is round-half-even."""
+    if x == 0.0 or not math.isfinite(x):
+        return x
+    f, e = math.frexp(x)                  # x = f 2^e, 1/2 <= |f| < 1
+    if e - 1 < -126:                      # below the normal range: multiples of 2^-133
+        v = round(x * 2.0 ** 133) * 2.0 ** -133
+    else:
+        v = math.ldexp(round(math.ldexp(f, 8)), e - 8)
+    return math.copysign(math.inf, x) if abs(v) >= 2.0 ** 128 else v
+
+
+@pytest.mark.parametrize("side,trans", [("A", "N"), ("A", "T"), ("B", "N"), ("B", "T")])
+def test_plain_bf16_rounding_is_nearest_even(ft, side, trans):
+    """A rank-1 product with K = 1 and a unit other operand returns the bf16
+    rounding of each entry (exact in FP32 and FP64 after it): halfway cases
+    (ties to even, both parities, with carries into the exponent), values just
+    off the halfway points, overflow to Inf, zeros and random magnitudes, in
+    both layouts of both operands (the two slicing paths)."""
+    rng = np.random.default_rng(7)
+    q = rng.integers(0x0080, 0x7F7F, 600).astype(np.uint32) << 16          # normal bf16 values
+    base = q.view(np.float32).astype(np.float64) * rng.choice([-1.0, 1.0], 600)
+    ulp = np.array([math.ldexp(1.0, math.frexp(b)[1] - 8) for b in base])
+    vals = np.concatenate([
+        base + np.sign(base) * ulp / 2,                                      # exact ties
+        base + np.sign(base) * ulp / 2 * (1 + 2.0 ** -40),                   # just above
+        base + np.sign(base) * ulp / 2 * (1 - 2.0 ** -40),                   # just below
+        rng.standard_normal(300) * 10.0 ** rng.integers(-30, 30, 300),
+        [0.0, -0.0, 3.4e38, -3.39e38, 3.3961e38, 1.0, 255.5, 256.5, 1.9921875 + 2 ** -8, 1.99609375],
+    ])
+    n = len(vals)
+    x = torch.tensor(vals, dtype=torch.float64)
+    one = torch.ones(1, dtype=torch.float64)
+    if side == "A":   # op(A) n x 1, op(B) = [1]
+        M, N = n, 1
+        A = x.reshape(1, n) if trans == "N" else x.reshape(n, 1)   # column-major (cols, ld) storage
+        lda = n if trans == "N" else 1
+        B, ldb, tb, ta = one.reshape(1, 1), 1, "N", trans
+    else:             # op(A) = [1], op(B) 1 x n
+        M, N = 1, n
+        B = x.reshape(n, 1) if trans == "N" else x.reshape(1, n)
+        ldb = 1 if trans == "N" else n
+        A, lda, ta, tb = one.reshape(1, 1), 1, "N", trans
+    dC = torch.zeros(N, M, dtype=torch.float64, device="cuda")
+    rc, _ = ft.ftgemm_d_split(ta, tb, M, N, 1, 1.0, A.cuda(), lda, B.cuda(), ldb, 0.0, dC, M, nslices=0, ft=0)
+    torch.cuda.synchronize()
+    assert rc == 0, ft.ftgemm_strerror(rc)
+    got = dC.cpu().numpy().reshape(-1)
+    want = np.array([bf16_nearest_even(float(v)) for v in vals])
+    np.testing.assert_array_equal(got, want)
