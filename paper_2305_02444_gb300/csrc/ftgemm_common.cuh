@@ -256,6 +256,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// v[0..15]: this lane's values of 16 columns.  Returns in lane l the sum of
+// column l mod 16 over the warp's 32 lanes (v is overwritten).
+__device__ __forceinline__ double colsum16(double (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const double send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 __device__ __forceinline__ double flip_bit(double x, int bit) {
   return __longlong_as_double(__double_as_longlong(x) ^ (1ll << bit));
 }

@@ -25,6 +25,11 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // grid (nG, ceil(S / cw)), 256 threads; block (G, c) covers columns c*cw ..
+// c*cw + cw - 1 of the 128-row group G.  Warp w takes batches of 16 columns
+// (16w, 16w + 128, ...), lane l the rows l + 32q (q < 4) of each column; a
+// column's sum and absolute sum are the lanes' 4-row partials reduced by the
+// transposing butterfly (16 shuffled adds per 16 columns, not 5 per column:
+// this pass runs on the FP64 pipe, GB300's scarcest unit).
 __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
                                                       double *__restrict__ part_rabs, double *__restrict__ part_max,
@@ -36,24 +41,32 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
   const long long r0 = (long long)G * 128;
   double rabs[4] = {0.0, 0.0, 0.0, 0.0};
   double mx = 0.0;
-  const long long s1 = min(S, (long long)(c + 1) * cw);
-  for (long long s = (long long)c * cw + w; s < s1; s += 8) {
-    double v[4];
+  const long long c0 = (long long)c * cw, s1 = min(S, c0 + cw);
+  for (long long sb = c0 + 16 * w; sb < s1; sb += 128) {
+    double ps[16], pa[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long r = r0 + lane + 32 * q;
-      v[q] = (r < R) ? X[r + s * ld] : 0.0;
-      rabs[q] += fabs(v[q]);
+    for (int j = 0; j < 16; ++j) {
+      const long long s = sb + j;
+      double v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long r = r0 + lane + 32 * q;
+        v[q] = (s < s1 && r < R) ? X[r + s * ld] : 0.0;
+        rabs[q] += fabs(v[q]);
+      }
+      ps[j] = (v[0] + v[1]) + (v[2] + v[3]);
+      pa[j] = (fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3]));
     }
-    const double sum = warp_sum((v[0] + v[1]) + (v[2] + v[3]));
-    const double ab = warp_sum((fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3])));
-    if (lane == 0) {
+    const double sum = colsum16(ps, lane), ab = colsum16(pa, lane);
+    const long long s = sb + (lane & 15);
+    if (lane < 16 && s < s1) {
       gsum[(long long)G * gstride + s] = sum;
       mx = fmax(mx, ab);
     }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) sh[w][lane + 32 * q] = rabs[q];
+  mx = warp_max(mx);
   if (lane == 0) smx[w] = mx;
   __syncthreads();
   if (threadIdx.x < 128) {
@@ -72,8 +85,9 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
 
 // grid (nG, ceil(R / (64 nsub))), 256 threads: a block covers nsub chunks of
 // 64 rows of one 128-column group; warp w takes the group's columns
-// 16w..16w+15, lane l the rows l and l + 32 of a chunk, so that a column's
-// absolute sum costs one warp reduction per 64 entries.
+// 16w..16w+15, lane l the rows l and l + 32 of a chunk.  A column's absolute
+// sum is kept per lane over the block's rows and reduced once at the end (the
+// transposing butterfly over the warp's 16 columns).
 __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
                                                       double *__restrict__ part_cabs, double *__restrict__ part_max,
@@ -106,7 +120,7 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
       rs_b += vb;
       ab_a += fabs(va);
       ab_b += fabs(vb);
-      cab[q] += warp_sum(fabs(va) + fabs(vb));
+      cab[q] += fabs(va) + fabs(vb);
     }
     srs[w][lane] = rs_a;
     srs[w][lane + 32] = rs_b;
@@ -128,11 +142,8 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
     }
     __syncthreads();
   }
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (w * 16 + q < ns) part_cabs[(long long)c * S + s0 + w * 16 + q] = cab[q];
-  }
+  const double cs = colsum16(cab, lane);
+  if (lane < 16 && w * 16 + lane < ns) part_cabs[(long long)c * S + s0 + w * 16 + lane] = cs;
   if (threadIdx.x < 64) {
     const double m = warp_max(mloc);
     if (lane == 0) smx[w] = m;

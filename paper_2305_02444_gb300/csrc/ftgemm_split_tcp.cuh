@@ -68,21 +68,6 @@ __device__ __forceinline__ double f32_bits_to_f64(uint32_t fb) {
   return (double)__uint_as_float(fb);
 }
 
-// v[0..15]: this lane's values of 16 columns.  Returns in lane l the sum of
-// column l mod 16 over the warp's 32 lanes (v is overwritten).
-__device__ __forceinline__ double colsum16(double (&v)[16], int lane) {
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const double send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
-}
-
 // The same with FP32 adds rounded upward (the |C| sums of the threshold).
 __device__ __forceinline__ float colsum16_ru(float (&v)[16], int lane) {
 #pragma unroll
