@@ -325,6 +325,9 @@ int ftgemm_set_splitk(int nsplit);
  *      share each A (and B) slab through TMA multicast;
  *   5: persistent, one CTA per SM walking its tiles, each tile finished
  *      from tensor memory while the next one's loads and MMAs run;
+ *   6: engine 5 on pairs of CTAs (clusters of 2) whose MMAs run as one
+ *      256 x 128 MMA (cta_group::2), each CTA staging half of the B slab;
+ *      grids of one tile row run engine 5;
  *   0 (default): engine 5.
  * 1: every call on the mma.sync kernel.  ft = 1 (FP32 checksums summed from
  * the staged slices on the CUDA cores) always runs on the mma.sync kernel.

@@ -109,8 +109,8 @@ def test_split_injection_detected_and_corrected(ft, orc):
     value by at least 2 (or to a huge value / Inf / NaN), above the FP32
     checksums' threshold, so each is detected and corrected by the FP64
     recomputation.  (Flips far below that threshold, e.g. low exponent bits of
-    the small early-pair partial sums, are not detectable with FP32
-    checksums: their band is stated with the design.)"""
+    a small partial sum, are not detectable with FP32 checksums: their band is
+    stated with the design.)"""
     M, N, K, S = 256, 256, 512, 8
     A, B, C, ar, br = problem("N", "N", M, N, K, seed=17)
     flips = [(5, 6, 0, 62), (100, 200, 20, 62), (250, 3, 35, 62)]   # kstep = pair index (36 pairs)
@@ -189,7 +189,8 @@ def test_fp64_checksums_see_what_fp32_checksums_miss(ft, orc):
     assert detected[1] < len(flips) // 2
 
 
-ENGINES = (0, 1, 2, 3, 4, 5)   # default, mma.sync, tcgen05 in clusters of 1, 2, 4 CTAs, persistent tcgen05
+# default, mma.sync, tcgen05 in clusters of 1, 2, 4 CTAs, persistent tcgen05, persistent on CTA pairs
+ENGINES = (0, 1, 2, 3, 4, 5, 6)
 
 
 def run_engine(ft, engine, *a, **kw):
@@ -249,7 +250,7 @@ def test_tcgen05_plain_bf16(ft, orc, ta, tb):
     assert 1e-6 < rel < 1e-2
 
 
-@pytest.mark.parametrize("engine", [2, 3, 4, 5])
+@pytest.mark.parametrize("engine", [2, 3, 4, 5, 6])
 def test_tcgen05_injection_log_and_correction(ft, orc, engine):
     """Flips of the tensor-memory FP64 accumulators after chosen slice pairs
     (first, middle, last of 36; one element in each lane quadrant): logged
@@ -286,8 +287,9 @@ def test_persistent_many_tiles_per_cta(ft, orc, ck, S):
     without checks and with FP64 checksums."""
     M, N, K = 2560, 2690, 192
     A, B, C, ar, br = problem("N", "T", M, N, K, seed=77)
-    outs = {e: run_engine(ft, e, "N", "T", M, N, K, 1.5, -0.5, A, B, C, ar, br, S, ftflag=ck) for e in (2, 5)}
+    outs = {e: run_engine(ft, e, "N", "T", M, N, K, 1.5, -0.5, A, B, C, ar, br, S, ftflag=ck) for e in (2, 5, 6)}
     np.testing.assert_array_equal(outs[5][0], outs[2][0])
+    np.testing.assert_array_equal(outs[6][0], outs[2][0])
     for g, r in outs.values():
         assert r["flagged_rows"] == 0 and r["flagged_cols"] == 0 and r["unverifiable"] == 0
     if S:
@@ -297,7 +299,8 @@ def test_persistent_many_tiles_per_cta(ft, orc, ck, S):
         assert np.all(np.abs(outs[5][0] - ref) <= orc.parity_tol(K, E) + split)
 
 
-def test_persistent_flips_in_later_tiles(ft, orc):
+@pytest.mark.parametrize("engine", [5, 6])
+def test_persistent_flips_in_later_tiles(ft, orc, engine):
     """Flips in tiles that a persistent CTA reaches first, second and third
     (tile t goes to CTA t mod grid): each tile with a fault is recomputed in
     the CTA's scratch tile, the others are stored directly; all are located
@@ -308,7 +311,7 @@ def test_persistent_flips_in_later_tiles(ft, orc):
     flips = [(3, 4, 0, 62), (1030, 400, 7, 62), (1100, 450, 14, 61), (1990, 2500, 14, 62)]
     assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
     try:
-        got, rep = run_engine(ft, 5, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
+        got, rep = run_engine(ft, engine, "N", "N", M, N, K, 1.0, 1.0, A, B, C, ar, br, S, ftflag=2)
         log = ft.ftgemm_injection_log()
     finally:
         ft.ftgemm_set_injection(mode=0)

@@ -83,8 +83,8 @@ def test_host_settings_and_strings(ft):
 
 
 def test_split_engine_knob_codes(ft):
-    assert ft.ftgemm_set_split_engine(6) == -1
-    for e in (5, 4, 3, 2):
+    assert ft.ftgemm_set_split_engine(7) == -1
+    for e in (6, 5, 4, 3, 2):
         assert ft.ftgemm_set_split_engine(e) == 0
     assert ft.ftgemm_set_split_engine(-1) == -1
     assert ft.ftgemm_set_split_engine(1) == 0
