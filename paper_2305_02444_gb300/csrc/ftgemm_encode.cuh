@@ -192,8 +192,9 @@ __device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b
   return lo;
 }
 
-// SEG over groups of 128 rows, all columns of the item in one block; each
-// warp takes 4 columns per step so that their warp reductions overlap.
+// SEG over groups of 128 rows, all columns of the item in one block; warp w
+// takes batches of 16 columns (16w, 16w + 128, ...), reduced by the
+// transposing butterfly as in enc_seg_kernel.
 __global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__restrict__ items, int nitems) {
   __shared__ double sh[8][128];
   __shared__ double smx[8];
@@ -204,40 +205,31 @@ __global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__r
   const long long r0 = (long long)G * 128;
   double rabs[4] = {0.0, 0.0, 0.0, 0.0};
   double mx = 0.0;
-  for (long long sb = 4 * w; sb < E.S; sb += 32) {
-    double v[4][4];
+  for (long long sb = 16 * w; sb < E.S; sb += 128) {
+    double ps[16], pa[16];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int j = 0; j < 16; ++j) {
+      const long long s = sb + j;
+      double v[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const long long r = r0 + lane + 32 * q, s = sb + c;
-        v[c][q] = (r < E.R && s < E.S) ? E.X[r + s * E.ld] : 0.0;
-        rabs[q] += fabs(v[c][q]);
+        const long long r = r0 + lane + 32 * q;
+        v[q] = (r < E.R && s < E.S) ? E.X[r + s * E.ld] : 0.0;
+        rabs[q] += fabs(v[q]);
       }
-    double sum[4], ab[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      sum[c] = (v[c][0] + v[c][1]) + (v[c][2] + v[c][3]);
-      ab[c] = (fabs(v[c][0]) + fabs(v[c][1])) + (fabs(v[c][2]) + fabs(v[c][3]));
+      ps[j] = (v[0] + v[1]) + (v[2] + v[3]);
+      pa[j] = (fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3]));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], o);
-        ab[c] += __shfl_xor_sync(0xffffffffu, ab[c], o);
-      }
-    if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (sb + c < E.S) {
-          E.gsum[(long long)G * E.gstride + sb + c] = sum[c];
-          mx = fmax(mx, ab[c]);
-        }
+    const double sum = colsum16(ps, lane), ab = colsum16(pa, lane);
+    const long long s = sb + (lane & 15);
+    if (lane < 16 && s < E.S) {
+      E.gsum[(long long)G * E.gstride + s] = sum;
+      mx = fmax(mx, ab);
     }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) sh[w][lane + 32 * q] = rabs[q];
+  mx = warp_max(mx);
   if (lane == 0) smx[w] = mx;
   __syncthreads();
   if (threadIdx.x < 128) {
@@ -256,9 +248,9 @@ __global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__r
 
 // STR over groups of 128 columns, all rows of the item in one block, in
 // chunks of 64 rows: warp w takes the group's columns 16w..16w+15, lane l the
-// rows l and l + 32 of a chunk; the columns' absolute sums stay in registers
-// (one warp reduction per column per chunk), the rows' sums go through
-// shared memory once per chunk.
+// rows l and l + 32 of a chunk; the columns' absolute sums stay per lane in
+// registers and are reduced once at the end (transposing butterfly), the
+// rows' sums go through shared memory once per chunk.
 __global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__restrict__ items, int nitems) {
   __shared__ double srs[8][64], sra[8][64];
   __shared__ double smx[2];
@@ -288,7 +280,7 @@ __global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__r
       rs_b += vb;
       ab_a += fabs(va);
       ab_b += fabs(vb);
-      cab[q] += warp_sum(fabs(va) + fabs(vb));
+      cab[q] += fabs(va) + fabs(vb);
     }
     srs[w][lane] = rs_a;
     srs[w][lane + 32] = rs_b;
@@ -310,11 +302,8 @@ __global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__r
     }
     __syncthreads();
   }
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      if (w * 16 + q < ns) E.absv[s0 + w * 16 + q] = cab[q];
-  }
+  const double cs = colsum16(cab, lane);
+  if (lane < 16 && w * 16 + lane < ns) E.absv[s0 + w * 16 + lane] = cs;
   if (threadIdx.x < 64) {
     const double m = warp_max(mloc);
     if (lane == 0) smx[w] = m;
