@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -286,6 +287,38 @@ __device__ __forceinline__ double colsum16(double (&v)[16], int lane) {
     }
   }
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// x rounded to bf16, to nearest with ties to even (the result of
+// __double2bfloat16): the fields are rounded with integer operations when the
+// result is a normal bf16 number or overflows, the conversion handles zeros,
+// subnormal results, Inf and NaN.
+__device__ __forceinline__ uint32_t bf16_rn_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF), eb = E - 1023 + 127;
+  if (E != 0x7FF && eb >= 1 && eb <= 254) {
+    const unsigned long long rest = b & ((1ull << 45) - 1ull), half = 1ull << 44;
+    uint32_t v = ((uint32_t)eb << 7) | (uint32_t)((b >> 45) & 0x7Fu);
+    v += (rest > half || (rest == half && (v & 1u))) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
+    return ((uint32_t)(b >> 48) & 0x8000u) | v;
+  }
+  return (uint32_t)__bfloat16_as_ushort(__double2bfloat16(x));
+}
+
+// |x| rounded upward to FP32 (the result of __double2float_ru(fabs(x))): the
+// fields are rounded with integer operations when the result is a normal
+// FP32 number or overflows, the conversion handles zeros, subnormal results,
+// Inf and NaN.  Used for the absolute sums of the detection thresholds, off
+// the FP64 pipe.
+__device__ __forceinline__ float f32_ru_abs(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  const int ef = (int)(b >> 52) - 1023 + 127;
+  if (ef >= 1 && ef <= 254) {
+    uint32_t v = ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
+    v += (b & 0x1FFFFFFFull) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
+    return __uint_as_float(v);
+  }
+  return __double2float_ru(fabs(x));
 }
 
 __device__ __forceinline__ double flip_bit(double x, int bit) {

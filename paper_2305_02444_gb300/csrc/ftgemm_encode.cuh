@@ -1,7 +1,8 @@
 // Operand checksum pass: per-tile checksum vectors of op(A) and op(B) and the
 // absolute sums the detection threshold uses (the A and B checksums of
 // FT-GEMM §2.2/§2.3).  One read of each operand; deterministic (fixed
-// reduction order, partials combined in a second small kernel).
+// reduction order; the partials of a group's chunks are combined by the
+// block that completes the group last).
 //
 // Both operands reduce to the same two shapes on a column-major X (R x S):
 //  SEG: groups of 128 consecutive rows; gsum[G][s] = sum_{r in G} X[r,s],
@@ -24,6 +25,36 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// The finish of a group of the pass, run by the block that completes the
+// group last (the others' partials are visible: each block fences its
+// partials before counting itself done): abs_out[x] = sum over the chunks c
+// of part_abs[c * L + x] for the group's 128 entries x0 .. (ascending c: a
+// fixed order), gmax[G] = max over c of part_max[c * nG + G].  The counter
+// goes back to zero for the next pass.
+__device__ __forceinline__ void enc_group_finish(unsigned int *cnt, int G, int nG, int nch, long long x0,
+                                                 long long L, const double *part_abs, const double *part_max,
+                                                 double *abs_out, double *gmax) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&cnt[G], 1u) == (unsigned)(nch - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < 128 && x0 + threadIdx.x < L) {
+    const long long x = x0 + threadIdx.x;
+    double t = 0.0;
+    for (int c = 0; c < nch; ++c) t += __ldcg(part_abs + (long long)c * L + x);
+    abs_out[x] = t;
+  }
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int c = 0; c < nch; ++c) m = fmax(m, __ldcg(part_max + (long long)c * nG + G));
+    gmax[G] = m;
+    cnt[G] = 0u;
+  }
+}
+
 // grid (nG, ceil(S / cw)), 256 threads; block (G, c) covers columns c*cw ..
 // c*cw + cw - 1 of the 128-row group G.  Warp w takes batches of 16 columns
 // (16w, 16w + 128, ...), lane l the rows l + 32q (q < 4) of each column; a
@@ -33,7 +64,8 @@ __device__ __forceinline__ double warp_max(double v) {
 __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
                                                       double *__restrict__ part_rabs, double *__restrict__ part_max,
-                                                      int cw) {
+                                                      int cw, unsigned int *__restrict__ cnt,
+                                                      double *__restrict__ rabs_out, double *__restrict__ gmax) {
   __shared__ double sh[8][128];
   __shared__ double smx[8];
   const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
@@ -81,6 +113,7 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
     for (int q = 0; q < 8; ++q) m = fmax(m, smx[q]);
     part_max[(long long)c * nG + G] = m;
   }
+  enc_group_finish(cnt, G, nG, (int)gridDim.y, r0, R, part_rabs, part_max, rabs_out, gmax);
 }
 
 // grid (nG, ceil(R / (64 nsub))), 256 threads: a block covers nsub chunks of
@@ -91,7 +124,8 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
 __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
                                                       double *__restrict__ part_cabs, double *__restrict__ part_max,
-                                                      int nsub) {
+                                                      int nsub, unsigned int *__restrict__ cnt,
+                                                      double *__restrict__ cabs_out, double *__restrict__ gmax) {
   static_assert(ENC_CHUNK == 64, "two rows per lane");
   __shared__ double srs[8][64], sra[8][64];
   __shared__ double smx[2];
@@ -150,23 +184,7 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
   }
   __syncthreads();
   if (threadIdx.x == 0) part_max[(long long)c * nG + G] = fmax(smx[0], smx[1]);
-}
-
-// abs[x] = sum_c part_abs[c][x] (x < L), gmax[G] = max_c part_max[c][G] (G < nG)
-__global__ void enc_finish_kernel(const double *__restrict__ part_abs, int nchunk, long long L,
-                                  double *__restrict__ abs_out, const double *__restrict__ part_max, int nG,
-                                  double *__restrict__ gmax) {
-  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < L) {
-    double t = 0.0;
-    for (int c = 0; c < nchunk; ++c) t += part_abs[(long long)c * L + x];
-    abs_out[x] = t;
-  }
-  if (x < nG) {
-    double m = 0.0;
-    for (int c = 0; c < nchunk; ++c) m = fmax(m, part_max[(long long)c * nG + x]);
-    gmax[x] = m;
-  }
+  enc_group_finish(cnt, G, nG, (int)gridDim.y, s0, S, part_cabs, part_max, cabs_out, gmax);
 }
 
 // Batched checksum pass: one item per operand of each problem of a batch;
@@ -345,8 +363,8 @@ __global__ void __launch_bounds__(256) enc_c_kernel(const double *__restrict__ C
     const double vc = tbuf[r * 128 + 64 * h + ((q + r) & 63)];
     rs += vr;
     cs += vc;
-    ra = __fadd_ru(ra, __double2float_ru(fabs(vr)));
-    ca = __fadd_ru(ca, __double2float_ru(fabs(vc)));
+    ra = __fadd_ru(ra, f32_ru_abs(vr));
+    ca = __fadd_ru(ca, f32_ru_abs(vc));
   }
   if (h) { part[0][r] = rs; part[1][r] = cs; part[2][r] = (double)ra; part[3][r] = (double)ca; }
   __syncthreads();

@@ -79,6 +79,7 @@ struct Buf {
 struct Workspace {
   bool init = false;
   Buf acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max;
+  Buf part_abs2, part_max2, enc_cnt;  // op(B)'s partials, group counters of the checksum pass
   Buf rep, loc, flips, tile_off;
   Buf stA, stB, stC;        // aligned copies of unaligned operands
   Buf hA, hB, hC;           // device copies for ftgemm_d_host
@@ -347,16 +348,29 @@ void enc_ops(bool ta_t, bool tb_t, long long M, long long N, long long K, int ns
   ob = tb_t ? enc_op(true, N, K, nsm) : enc_op(false, K, N, nsm);
 }
 
-// One operand's pass and its finish: gsum = group sums (stride gstride),
-// absv = row (SEG) / column (STR) absolute sums, gmax = per group maximum.
+// One operand's pass: gsum = group sums (stride gstride), absv = row (SEG) /
+// column (STR) absolute sums, gmax = per group maximum; part_abs / part_max
+// hold the chunks' partials, cnt (o.nG counters, zero between passes) counts
+// each group's finished chunks.
 void launch_enc(const EncOp &o, const double *X, long long ld, double *gsum, long long gstride, double *part_abs,
-                double *part_max, double *absv, double *gmax, cudaStream_t s) {
+                double *part_max, unsigned int *cnt, double *absv, double *gmax, cudaStream_t s) {
   const dim3 grid((unsigned)o.nG, (unsigned)o.nch);
-  if (o.seg) enc_seg_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, ENC_CHUNK * o.sub);
-  else enc_str_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, o.sub);
-  const long long L = o.seg ? o.R : o.S;
-  enc_finish_kernel<<<grid_for(std::max(L, o.nG)), 256, 0, s>>>(part_abs, (int)o.nch, L, absv, part_max, (int)o.nG,
-                                                                gmax);
+  if (o.seg)
+    enc_seg_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, ENC_CHUNK * o.sub, cnt,
+                                        absv, gmax);
+  else
+    enc_str_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, o.sub, cnt, absv, gmax);
+}
+
+// The second stream of a call (independent work inside one call runs on it
+// between a fork and a join event).
+int ensure_side(Workspace &w) {
+  if (w.side) return 0;
+  if (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&w.join_ev, cudaEventDisableTiming) != cudaSuccess)
+    return FTGEMM_ERR_CUDA;
+  return 0;
 }
 
 int device_sms(int dev) {
@@ -383,16 +397,30 @@ int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, cons
   cudaGetDevice(&dev);
   EncOp oa, ob;
   enc_ops(ta_t, tb_t, M, N, K, device_sms(dev), oa, ob);
-  const long long pa = std::max(oa.part_len(), ob.part_len()), pm = std::max(oa.max_len(), ob.max_len());
-  if (ensure(w.part_abs, sizeof(double) * pa) || ensure(w.part_max, sizeof(double) * pm)) return FTGEMM_ERR_NOMEM;
-  double *part_abs = (double *)w.part_abs.p, *part_max = (double *)w.part_max.p;
+  // op(A)'s pass on s and op(B)'s on the second stream, each with its own
+  // partials and group counters (zeroed when allocated, reset by each pass)
+  const size_t ncnt = (size_t)(oa.nG + ob.nG);
+  if (ensure(w.part_abs, sizeof(double) * oa.part_len()) || ensure(w.part_max, sizeof(double) * oa.max_len()) ||
+      ensure(w.part_abs2, sizeof(double) * ob.part_len()) || ensure(w.part_max2, sizeof(double) * ob.max_len()))
+    return FTGEMM_ERR_NOMEM;
+  if (w.enc_cnt.cap < sizeof(unsigned int) * ncnt) {
+    if (ensure(w.enc_cnt, sizeof(unsigned int) * ncnt)) return FTGEMM_ERR_NOMEM;
+    if (cudaMemset(w.enc_cnt.p, 0, w.enc_cnt.cap) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  }
+  if (int rc = ensure_side(w)) return rc;
+  unsigned int *cnt = (unsigned int *)w.enc_cnt.p;
   if (Kp != K) {
     cudaMemsetAsync(acs, 0, sizeof(double) * nI * Kp, s);
     cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
   }
-  launch_enc(oa, A, lda, acs, Kp, part_abs, part_max, arowabs, aabsmax, s);
-  launch_enc(ob, B, ldb, bcs, Kp, part_abs, part_max, bcolabs, babsmax, s);
-  g_launches += 4;
+  cudaEventRecord(w.fork_ev, s);
+  cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+  launch_enc(oa, A, lda, acs, Kp, (double *)w.part_abs.p, (double *)w.part_max.p, cnt, arowabs, aabsmax, s);
+  launch_enc(ob, B, ldb, bcs, Kp, (double *)w.part_abs2.p, (double *)w.part_max2.p, cnt + oa.nG, bcolabs, babsmax,
+             w.side);
+  cudaEventRecord(w.join_ev, w.side);
+  cudaStreamWaitEvent(s, w.join_ev, 0);
+  g_launches += 2;
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
 
@@ -973,7 +1001,7 @@ int ftgemm_finalize(void) {
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
                   &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
-                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB};
+                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB, &w.part_abs2, &w.part_max2, &w.enc_cnt};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -1016,7 +1044,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Scratch layout for one call; returns the bytes needed.
 struct NoallocLayout {
-  size_t rep, loc, acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max, total;
+  size_t rep, loc, acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max, enc_cnt, total;
 };
 
 NoallocLayout noalloc_layout(bool ta_t, bool tb_t, long long M, long long N, long long K, int nsm) {
@@ -1037,6 +1065,7 @@ NoallocLayout noalloc_layout(bool ta_t, bool tb_t, long long M, long long N, lon
   L.babsmax = o; o = align256(o + sizeof(double) * nJ);
   L.part_abs = o; o = align256(o + sizeof(double) * pa);
   L.part_max = o; o = align256(o + sizeof(double) * pm);
+  L.enc_cnt = o; o = align256(o + sizeof(unsigned int) * std::max(oa.nG, ob.nG));
   L.total = o;
   return L;
 }
@@ -1096,14 +1125,17 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
     cudaMemsetAsync(acs, 0, sizeof(double) * nI * Kp, s);
     cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
   }
-  // operand checksum pass (same kernels as ftgemm_d), partials in the array
+  // operand checksum pass (same kernels as ftgemm_d), partials and group
+  // counters in the array, both operands on the caller's stream
   {
     EncOp oa, ob;
     enc_ops(ta_t, tb_t, M, N, K, nsm, oa, ob);
-    launch_enc(oa, A, lda, acs, Kp, part_abs, part_max, arowabs, aabsmax, s);
-    launch_enc(ob, B, ldb, bcs, Kp, part_abs, part_max, bcolabs, babsmax, s);
+    unsigned int *cnt = (unsigned int *)(base + L.enc_cnt);
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * std::max(oa.nG, ob.nG), s);
+    launch_enc(oa, A, lda, acs, Kp, part_abs, part_max, cnt, arowabs, aabsmax, s);
+    launch_enc(ob, B, ldb, bcs, Kp, part_abs, part_max, cnt, bcolabs, babsmax, s);
   }
-  g_launches += 4;
+  g_launches += 2;
 
   CUtensorMap mA, mB, mC;
   if (ta_t) rc = make_map(&mA, A, K, M, lda, BK, BM, true);
@@ -1731,10 +1763,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
       q2.eB = (const int *)w.spEPB.p; q2.C = (double *)w.uP2.p; q2.ldc = ldp2;
       for (SplitParams *q : {&q1, &q2}) { q->alpha = 1.0; q->beta = 0.0; q->verify = 0; q->inj = 0; }
       // P1 and P2 are independent one-wave grids: P2 runs on a second stream
-      if (!w.side && (cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking) != cudaSuccess ||
-                      cudaEventCreateWithFlags(&w.fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-                      cudaEventCreateWithFlags(&w.join_ev, cudaEventDisableTiming) != cudaSuccess))
-        return FTGEMM_ERR_CUDA;
+      if ((rc = ensure_side(w))) return rc;
       cudaEventRecord(w.fork_ev, s);
       cudaStreamWaitEvent(w.side, w.fork_ev, 0);
       if (run_tc(false, false, 0, mPA, mB, mB, mBh, q1, s) != cudaSuccess ||

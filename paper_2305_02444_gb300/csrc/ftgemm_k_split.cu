@@ -100,22 +100,6 @@ __global__ void __launch_bounds__(256) split_rowmax_kernel(const double *__restr
   if (m) atomicMax(mb + r, m);
 }
 
-// x rounded to bf16, to nearest with ties to even (the result of
-// __double2bfloat16): the fields are rounded with integer operations when the
-// result is a normal bf16 number or overflows, the conversion handles zeros,
-// subnormal results, Inf and NaN.
-__device__ __forceinline__ uint32_t bf16_rn_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((b >> 52) & 0x7FF), eb = E - 1023 + 127;
-  if (E != 0x7FF && eb >= 1 && eb <= 254) {
-    const unsigned long long rest = b & ((1ull << 45) - 1ull), half = 1ull << 44;
-    uint32_t v = ((uint32_t)eb << 7) | (uint32_t)((b >> 45) & 0x7Fu);
-    v += (rest > half || (rest == half && (v & 1u))) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
-    return ((uint32_t)(b >> 48) & 0x8000u) | v;
-  }
-  return (uint32_t)__bfloat16_as_ushort(__double2bfloat16(x));
-}
-
 // floor(m 2^t) mod 2^64 for the 53-bit integer m and any t.
 __device__ __forceinline__ unsigned long long shift_trunc(unsigned long long m, int t) {
   if (t >= 0) return t >= 64 ? 0ull : (m << t);

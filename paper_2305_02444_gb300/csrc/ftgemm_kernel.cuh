@@ -497,8 +497,8 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
       const double vc = sC[r * BM + 64 * h + ((q + r) & 63)];
       rs += vr;
       cs += vc;
-      ra = __fadd_ru(ra, __double2float_ru(fabs(vr)));
-      ca = __fadd_ru(ca, __double2float_ru(fabs(vc)));
+      ra = __fadd_ru(ra, f32_ru_abs(vr));
+      ca = __fadd_ru(ca, f32_ru_abs(vc));
     }
     if (h) { s_ro[r] = rs; s_co[r] = cs; s_pr[r] = (double)ra; s_pc[r] = (double)ca; }
     compute_sync();

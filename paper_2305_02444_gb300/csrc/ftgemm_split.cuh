@@ -181,7 +181,7 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
     if (CK == 2) {
       rref += out;
       rcs += c;
-      const float fa = __double2float_ru(fabs(c));
+      const float fa = f32_ru_abs(c);
       rca = __fadd_ru(rca, fa);
       if (il == 0 && jl < nJt) sb += pow2_or_ldexp(p.eB[j0 + jl]);  // lane 0 of quarter 0: the half's 2^eB sum
       const double wr = warp_sum(out), wc = warp_sum(c);

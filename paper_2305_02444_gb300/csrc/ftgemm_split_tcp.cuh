@@ -263,7 +263,7 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
       ov[j] = o;
       d[2 * j] = tc_lo(o);
       d[2 * j + 1] = tc_hi(o);
-      av[j] = __double2float_ru(fabs(cv[j]));
+      av[j] = f32_ru_abs(cv[j]);
       if (j & 1) { rs1 += o; rc1 += cv[j]; ra1 = __fadd_ru(ra1, av[j]); }
       else { rs0 += o; rc0 += cv[j]; ra0 = __fadd_ru(ra0, av[j]); }
     }

@@ -8,6 +8,9 @@ runs (tests/probes/*.cu):
 - umma_issue.cu: tcgen05.mma issue rate when the issuing thread also polls an
   mbarrier versus when another warp polls and hands over at a named barrier
   (the split kernel's waiter warp).
+- bit_tricks.cu: the integer shortcuts that keep conversions and scalings
+  off the FP64 pipe give the same bits as the CUDA conversions and FP64
+  operations they replace.
 
 The assertions are loose bounds on what the designs rely on; `-s` prints the
 measured figures."""
@@ -57,3 +60,12 @@ def test_tcgen05_issue_with_and_without_polling():
     # 128 x 128 x 16 BF16 MMA = 262144 FMAs at 4096 FMA/clk/SM = 64 cycles
     assert c["plain"] <= 72 and c["handoff"] <= 72
     assert c["poll"] >= 1.3 * c["handoff"]
+
+
+def test_integer_shortcuts_match_the_conversions():
+    """FP32 round-up of |x|, bf16 rounding, power-of-two scaling, FP32 -> FP64
+    and the scaled exact pair products: bit-identical to the conversions and
+    FP64 operations on 2^26 inputs (ties, range edges, subnormals, Inf, NaN)."""
+    d = build_and_run("bit_tricks")
+    assert d["inputs"] == 1 << 26
+    assert all(v == 0 for v in d["mismatch"].values()), d
