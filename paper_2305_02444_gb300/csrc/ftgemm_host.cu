@@ -92,7 +92,10 @@ struct Workspace {
   cudaStream_t side = nullptr;   // second stream for independent work inside one call (fork / join)
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int nsm = 0;              // SM count
-  Buf pin;                  // pinned host staging (report, loc, injection upload)
+  Buf pin;                  // pinned host staging of the report and location copies
+  Buf ipin[2];              // pinned staging of the injection upload, used in turn
+  cudaEvent_t ipin_ev[2] = {nullptr, nullptr};  // recorded after each staging buffer's copies
+  int ipin_next = 0;
   // the last injected call, for ftgemm_injection_log
   long long last_nflips = 0;
   std::vector<long long> last_perm;  // sorted position -> original index
@@ -463,12 +466,18 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
   });
   const size_t fbytes = sizeof(DevFlip) * (size_t)std::max(1LL, nf);
   const size_t obytes = sizeof(int) * (size_t)(ntiles + 1);
-  if (ensure(w.flips, fbytes) || ensure(w.tile_off, obytes) || ensure_pinned(w.pin, fbytes + obytes + 4096))
+  // two pinned staging buffers in turn: the one taken now may still be read
+  // by the copies of the call before the previous one, so wait for its event
+  // (recorded after those copies; long complete when calls follow each other)
+  const int k = w.ipin_next;
+  w.ipin_next ^= 1;
+  if (!w.ipin_ev[k] && cudaEventCreateWithFlags(&w.ipin_ev[k], cudaEventDisableTiming) != cudaSuccess)
+    return FTGEMM_ERR_CUDA;
+  if (cudaEventSynchronize(w.ipin_ev[k]) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  if (ensure(w.flips, fbytes) || ensure(w.tile_off, obytes) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096))
     return FTGEMM_ERR_NOMEM;
-  // the pinned buffer may still be read by an earlier async copy: wait for the stream
-  cudaStreamSynchronize(s);
-  DevFlip *hf = (DevFlip *)w.pin.p;
-  int *ho = (int *)((char *)w.pin.p + fbytes);
+  DevFlip *hf = (DevFlip *)w.ipin[k].p;
+  int *ho = (int *)((char *)w.ipin[k].p + fbytes);
   std::fill(ho, ho + ntiles + 1, 0);
   for (long long q = 0; q < nf; ++q) {
     const ftgemm_flip &f = L[perm[q]];
@@ -479,6 +488,7 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
   for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
   cudaMemcpyAsync(w.flips.p, hf, sizeof(DevFlip) * nf, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(w.tile_off.p, ho, obytes, cudaMemcpyHostToDevice, s);
+  cudaEventRecord(w.ipin_ev[k], s);
   w.last_nflips = nf;
   w.last_perm = perm;
   p.flips = (DevFlip *)w.flips.p;
@@ -1001,7 +1011,8 @@ int ftgemm_finalize(void) {
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
                   &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
-                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB, &w.part_abs2, &w.part_max2, &w.enc_cnt};
+                  &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB,
+                  &w.part_abs2, &w.part_max2, &w.enc_cnt};
   for (Buf *b : dbufs) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
@@ -1009,6 +1020,14 @@ int ftgemm_finalize(void) {
   }
   if (w.pin.p) cudaFreeHost(w.pin.p);
   w.pin.p = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (w.ipin[k].p) cudaFreeHost(w.ipin[k].p);
+    w.ipin[k].p = nullptr;
+    w.ipin[k].cap = 0;
+    if (w.ipin_ev[k]) cudaEventDestroy(w.ipin_ev[k]);
+    w.ipin_ev[k] = nullptr;
+  }
+  w.ipin_next = 0;
   if (w.side) cudaStreamDestroy(w.side);
   if (w.fork_ev) cudaEventDestroy(w.fork_ev);
   if (w.join_ev) cudaEventDestroy(w.join_ev);
