@@ -81,7 +81,7 @@ struct Params {
   long long ldp1, ldp2;
   const double *ccs, *ccsa, *crs, *crsa;  // [I][N] column sums, [J][M] row sums of C (and |C|)
   int panel_slabs;               // PANEL kernels: verify the accumulators every panel_slabs k-slabs
-  int correct_mode;              // 0: recompute located elements; 1: subtract the checksum residual (one fault per tile)
+  int correct_mode;              // 0: recompute located elements; 1: subtract the checksum residual
   double *Cout;                  // where the verified tile lives (p.C is the copy of C_in)
   long long ldcout;
 };
@@ -114,7 +114,6 @@ struct SplitParams {
   unsigned long long wait_limit_ns;
   int verify;                   // 1: fault tolerant
   // injection: flips of the FP64 accumulator of (row, col) after pair `kstep` is folded in
-  const DevFlip *flips_unused;
   DevFlip *flips;
   const int *tile_off;
   int inj;

@@ -1523,11 +1523,10 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
       const int total = (int)grp[gi].prob.size();
       if (!total) continue;
       const int grid = std::min(nsm, (total + chunk - 1) / chunk);
-      cudaError_t e;
-      if (gi == 0) e = launch_batched_nn(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
-      else if (gi == 1) e = launch_batched_nt(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
-      else if (gi == 2) e = launch_batched_tn(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
-      else e = launch_batched_tt(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk, counters + gi, gerr, grid, cs);
+      auto launch = gi == 0 ? launch_batched_nn : gi == 1 ? launch_batched_nt : gi == 2 ? launch_batched_tn
+                                                                                    : launch_batched_tt;
+      const cudaError_t e = launch(P->ft, P->inj, dprobs, dgrp[gi][0], dgrp[gi][1], dgrp[gi][2], total, chunk,
+                                   counters + gi, gerr, grid, cs);
       ok = ok && e == cudaSuccess;
       P->kernels++;
     }

@@ -46,9 +46,12 @@ static cudaError_t launch_split_tc_ck(bool ta, bool tb, const CUtensorMap &a, co
 cudaError_t launch_split_tc(bool ta, bool tb, int ck, int cluster, const CUtensorMap &a, const CUtensorMap &b,
                             const CUtensorMap &b2, const SplitParams &p, cudaStream_t s) {
   if (ck != 0 && ck != 2) return cudaErrorInvalidValue;
-  if (cluster == 4) return ck ? launch_split_tc_ck<2, 4>(ta, tb, a, b, b2, p, s) : launch_split_tc_ck<0, 4>(ta, tb, a, b, b2, p, s);
-  if (cluster == 2) return ck ? launch_split_tc_ck<2, 2>(ta, tb, a, b, b2, p, s) : launch_split_tc_ck<0, 2>(ta, tb, a, b, b2, p, s);
-  if (cluster == 1) return ck ? launch_split_tc_ck<2, 1>(ta, tb, a, b, b2, p, s) : launch_split_tc_ck<0, 1>(ta, tb, a, b, b2, p, s);
+  if (cluster == 4)
+    return ck ? launch_split_tc_ck<2, 4>(ta, tb, a, b, b2, p, s) : launch_split_tc_ck<0, 4>(ta, tb, a, b, b2, p, s);
+  if (cluster == 2)
+    return ck ? launch_split_tc_ck<2, 2>(ta, tb, a, b, b2, p, s) : launch_split_tc_ck<0, 2>(ta, tb, a, b, b2, p, s);
+  if (cluster == 1)
+    return ck ? launch_split_tc_ck<2, 1>(ta, tb, a, b, b2, p, s) : launch_split_tc_ck<0, 1>(ta, tb, a, b, b2, p, s);
   return cudaErrorInvalidValue;
 }
 

@@ -140,7 +140,10 @@ __device__ __forceinline__ void split_tile_report(const SplitParams &p, const in
   DevReport *r = p.rep;
   if (cnt[0]) atomicAdd(&r->flagged_rows, (unsigned long long)cnt[0]);
   if (cnt[1]) atomicAdd(&r->flagged_cols, (unsigned long long)cnt[1]);
-  if (cnt[2]) { atomicAdd(&r->detected, (unsigned long long)cnt[2]); atomicAdd(&r->corrected, (unsigned long long)cnt[2]); }
+  if (cnt[2]) {
+    atomicAdd(&r->detected, (unsigned long long)cnt[2]);
+    atomicAdd(&r->corrected, (unsigned long long)cnt[2]);
+  }
   if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
 }
 
