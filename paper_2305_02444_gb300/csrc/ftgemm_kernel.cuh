@@ -114,6 +114,38 @@ __device__ __forceinline__ void slab_fma(double (&acc)[8][8], const unsigned cha
   }
 }
 
+// slab_fma for rblk x cblk accumulator blocks (each 2, 4 or 8; 6 as well
+// with FINE).
+template <bool TA, bool TB, int PP>
+__device__ __forceinline__ void slab_fma_cols(int cblk, double (&acc)[8][8], const unsigned char *sA,
+                                              const unsigned char *sB, int tx, int ty) {
+  if (cblk == 8) slab_fma<TA, TB, PP, 8>(acc, sA, sB, tx, ty);
+  else if (cblk == 6) slab_fma<TA, TB, PP, 6>(acc, sA, sB, tx, ty);
+  else if (cblk == 4) slab_fma<TA, TB, PP, 4>(acc, sA, sB, tx, ty);
+  else slab_fma<TA, TB, PP, 2>(acc, sA, sB, tx, ty);
+}
+
+template <bool TA, bool TB, bool FINE>
+__device__ __forceinline__ void slab_fma_blocks(int rblk, int cblk, double (&acc)[8][8], const unsigned char *sA,
+                                                const unsigned char *sB, int tx, int ty) {
+  if constexpr (!FINE) {  // 2, 4 or 8 blocks each way
+    if (rblk == 8 && cblk == 8) slab_fma<TA, TB, 8, 8>(acc, sA, sB, tx, ty);
+    else if (rblk == 8 && cblk == 4) slab_fma<TA, TB, 8, 4>(acc, sA, sB, tx, ty);
+    else if (rblk == 8) slab_fma<TA, TB, 8, 2>(acc, sA, sB, tx, ty);
+    else if (rblk == 4 && cblk == 8) slab_fma<TA, TB, 4, 8>(acc, sA, sB, tx, ty);
+    else if (rblk == 4 && cblk == 4) slab_fma<TA, TB, 4, 4>(acc, sA, sB, tx, ty);
+    else if (rblk == 4) slab_fma<TA, TB, 4, 2>(acc, sA, sB, tx, ty);
+    else if (cblk == 8) slab_fma<TA, TB, 2, 8>(acc, sA, sB, tx, ty);
+    else if (cblk == 4) slab_fma<TA, TB, 2, 4>(acc, sA, sB, tx, ty);
+    else slab_fma<TA, TB, 2, 2>(acc, sA, sB, tx, ty);
+  } else {
+    if (rblk == 8) slab_fma_cols<TA, TB, 8>(cblk, acc, sA, sB, tx, ty);
+    else if (rblk == 6) slab_fma_cols<TA, TB, 6>(cblk, acc, sA, sB, tx, ty);
+    else if (rblk == 4) slab_fma_cols<TA, TB, 4>(cblk, acc, sA, sB, tx, ty);
+    else slab_fma_cols<TA, TB, 2>(cblk, acc, sA, sB, tx, ty);
+  }
+}
+
 // MODE 0: the whole tile (mainloop + epilogue).
 // MODE 1: split-K partial: one k-range of a tile; stores the raw partial
 //         product and its predicted-checksum partials for MODE 2.
@@ -121,7 +153,7 @@ __device__ __forceinline__ void slab_fma(double (&acc)[8][8], const unsigned cha
 //         epilogue as MODE 0 (beta*C encode, verify, locate, correct, store).
 // MODE 3: verify-only pass of the unfused ablation: the tile of a finished
 //         GEMM, predicted checksums and C sums computed by separate passes.
-template <bool TA, bool TB, bool FT, bool INJ, int MODE, bool PANEL = false>
+template <bool TA, bool TB, bool FT, bool INJ, int MODE, bool PANEL = false, bool FINE = false>
 __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorMap *tmB, const CUtensorMap *tmC,
                                          const CUtensorMap *tmW, const Params &p, const int tile, const int split,
                                          unsigned char *smem) {
@@ -194,7 +226,11 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   }
 
   const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16*pp, columns ty + 16*qq
-  const int rblk = mI <= 32 ? 2 : mI <= 64 ? 4 : 8, cblk = nJt <= 32 ? 2 : nJt <= 64 ? 4 : 8;
+  // accumulator blocks (16 rows / columns each) that hold valid rows / columns:
+  // 2, 4 or 8, and also 6 in the batched kernel (FINE), whose small problems
+  // often end in partly filled tiles
+  auto blocks = [](int v) { return v <= 32 ? 2 : v <= 64 ? 4 : (FINE && v <= 96) ? 6 : 8; };
+  const int rblk = blocks(mI), cblk = blocks(nJt);
   double acc[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
@@ -219,17 +255,9 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     const unsigned char *sA = smem + st * STAGE_BYTES;
     const unsigned char *sB = sA + A_BYTES;
     // rows tx + 16 pp >= mI and columns ty + 16 qq >= nJt hold zeros (TMA
-    // zero fill): a tile with at most 64 (32) valid rows or columns skips
-    // those blocks' FMAs, leaving the same bits
-    if (rblk == 8 && cblk == 8) slab_fma<TA, TB, 8, 8>(acc, sA, sB, tx, ty);
-    else if (rblk == 8 && cblk == 4) slab_fma<TA, TB, 8, 4>(acc, sA, sB, tx, ty);
-    else if (rblk == 8) slab_fma<TA, TB, 8, 2>(acc, sA, sB, tx, ty);
-    else if (rblk == 4 && cblk == 8) slab_fma<TA, TB, 4, 8>(acc, sA, sB, tx, ty);
-    else if (rblk == 4 && cblk == 4) slab_fma<TA, TB, 4, 4>(acc, sA, sB, tx, ty);
-    else if (rblk == 4) slab_fma<TA, TB, 4, 2>(acc, sA, sB, tx, ty);
-    else if (cblk == 8) slab_fma<TA, TB, 2, 8>(acc, sA, sB, tx, ty);
-    else if (cblk == 4) slab_fma<TA, TB, 2, 4>(acc, sA, sB, tx, ty);
-    else slab_fma<TA, TB, 2, 2>(acc, sA, sB, tx, ty);
+    // zero fill): a tile with at most 96 / 64 / 32 valid rows or columns
+    // skips those blocks' FMAs, leaving the same bits
+    slab_fma_blocks<TA, TB, FINE>(rblk, cblk, acc, sA, sB, tx, ty);
     if (FT) {
       const double *scs = reinterpret_cast<const double *>(sA + A_BYTES + B_BYTES);
       if (tid < 128) {
@@ -735,7 +763,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int c = 0; c < chunk && base + c < total; ++c) {
       const int g = order[base + c];
       const BatchProblem *bp = probs + tile_prob[g];
-      ftd_tile<TA, TB, FT, INJ, 0>(&bp->tmA, &bp->tmB, &bp->tmC, &bp->tmC, bp->p, tile_local[g], 0, smem);
+      ftd_tile<TA, TB, FT, INJ, 0, false, true>(&bp->tmA, &bp->tmB, &bp->tmC, &bp->tmC, bp->p, tile_local[g], 0,
+                                                smem);
       __syncthreads();
       if (threadIdx.x == 0 && *reinterpret_cast<volatile int *>(&bp->p.rep->err) != 0) atomicExch(gerr, ERR_TIMEOUT);
     }
