@@ -380,6 +380,24 @@ __global__ void __launch_bounds__(256) enc_c_kernel(const double *__restrict__ C
   }
 }
 
+// Split-K partial tiles (nsplit x ntile slots of BM x BN doubles, slot
+// split * ntile + tile) summed into slot 0 of each tile in ascending split
+// order, as the reduction kernel adds them (0 + W0 + W1 + ...: the same bits),
+// spread over the whole GPU instead of one CTA per tile.
+__global__ void splitk_sum_kernel(double *__restrict__ W, long long ntile, int nsplit) {
+  const long long total = ntile * BM * BN;  // doubles per split; even
+  for (long long e = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x); e < total;
+       e += 2LL * gridDim.x * blockDim.x) {
+    double x = 0.0, y = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) {
+      const double2 v = *reinterpret_cast<const double2 *>(W + (long long)sp * total + e);
+      x += v.x;
+      y += v.y;
+    }
+    *reinterpret_cast<double2 *>(W + e) = make_double2(x, y);
+  }
+}
+
 // C <- beta*C (beta == 0 writes zeros without reading C)
 __global__ void scale_kernel(double *C, long long M, long long N, long long ldc, double beta) {
   const long long total = M * N;

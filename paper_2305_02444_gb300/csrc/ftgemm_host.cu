@@ -686,6 +686,16 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     p.wpc = (double *)w.wpc.p;
     p.wpr = (double *)w.wpr.p;
     if (e == cudaSuccess) e = launch(1, mW);
+    // fewer tiles than SMs: sum the partial tiles over the whole GPU first
+    // (the reduction has one CTA per tile and is FP64-add bound)
+    p.presummed = tail_count < w.nsm ? 1 : 0;
+    if (e == cudaSuccess && p.presummed) {
+      const long long pairs = BM * BN * tail_count / 2;
+      splitk_sum_kernel<<<(unsigned)std::min<long long>((pairs + 255) / 256, 8LL * w.nsm), 256, 0, s>>>(
+          (double *)w.W.p, tail_count, S);
+      e = cudaGetLastError();
+      g_launches++;
+    }
     if (e == cudaSuccess) e = launch(2, mW);
     g_launches += 2;
   }
@@ -693,10 +703,7 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
   if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
   if (c_staged) launch_copy(Cuse, ldcU, C, ldc, M, N, s);
 
-  if (rep) {
-    if (inj) cudaStreamSynchronize(s);  // the pinned buffer held the injection upload
-    return copy_report(w, rep, s);
-  }
+  if (rep) return copy_report(w, rep, s);
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
 
@@ -1826,9 +1833,6 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);
   g_launches++;
-  if (rep) {
-    if (inj) cudaStreamSynchronize(s);
-    return copy_report(w, rep, s);
-  }
+  if (rep) return copy_report(w, rep, s);
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }

@@ -448,7 +448,11 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     // split).  Each partial tile comes in as one TMA bulk load into the staged
     // tile buffer (the ring is idle: no k-slabs here), then is summed from
     // shared memory; the rows / columns outside the matrix load as zeros.
+    // With p.presummed, slot 0 already holds that sum (splitk_sum_kernel, the
+    // same additions in the same order): one load, the checksum partials of
+    // every split still added here.
     for (int sp = 0; sp < p.nsplit; ++sp) {
+      if (!p.presummed || sp == 0) {
       if (tid == 0) {
         mbar_arrive_expect_tx(full0, CTILE_BYTES);
         tma_load_3d(smem_u32(sC), tmW, full0, 0, 0, sp * wcount + (tile - p.tile_base));
@@ -462,6 +466,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
         for (int qq = 0; qq < 8; ++qq) acc[pp][qq] += sC[(ty + 16 * qq) * BM + tx + 16 * pp];
       fence_proxy_async_smem();  // these generic reads precede the next async write (next partial or C)
       compute_sync();
+      }
       if (FT) {
         if (tid < 128) {
           if (tid < nJt) csacc += p.wpc[((long long)sp * p.nI + I) * p.N + j0 + tid];
