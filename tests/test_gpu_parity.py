@@ -195,8 +195,12 @@ def test_unaligned_operands(ft, orc, pad, offset):
 
 
 @pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
-def test_encode_operands_vs_oracle(ft, orc, ta, tb):
-    M, N, K = 300, 200, 77
+@pytest.mark.parametrize("M,N,K", [(300, 200, 77), (2085, 1103, 3001)])
+def test_encode_operands_vs_oracle(ft, orc, ta, tb, M, N, K):
+    """The operand checksum pass against the oracle's, both operand layouts.
+    The larger shape splits each 128-wide group into several chunks, so the
+    group's finish (the last block to complete sums the chunks' partials)
+    runs over many partials; the ragged sizes leave partial groups."""
     P = make_problem(ta, tb, M, N, K, seed=8)
     nI, nJ = -(-M // BM), -(-N // BN)
     d = dict(acs=(nI, K), aabsmax=(nI,), arowabs=(M,), bcs=(nJ, K), babsmax=(nJ,), bcolabs=(N,))
