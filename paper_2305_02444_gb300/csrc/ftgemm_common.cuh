@@ -75,6 +75,7 @@ struct Params {
   // split-K (MODE 1 / 2 kernels)
   int nsplit, ks_slabs;          // number of k-splits, k-slabs per split
   int presummed;                 // MODE 2: slot 0 of each tile already holds the sum of its partial tiles
+  int csums;                     // MODE 2: the beta-side sums of C come from ccs .. crsa (enc_c_kernel)
   double *W;                     // partial tiles, 128 x 128 each, slot split * tile_count + (tile - tile_base)
   double *wpc, *wpr;             // predicted-checksum partials [split][nI][N], [split][nJ][M]
   // unfused ablation (MODE 3): predicted checksums and C sums from separate passes

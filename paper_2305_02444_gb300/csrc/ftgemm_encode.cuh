@@ -330,11 +330,13 @@ __global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__r
   if (threadIdx.x == 0) E.gmax[G] = fmax(smx[0], smx[1]);
 }
 
-// Unfused ablation: one pass over C that keeps a copy of C_in (needed to
-// recompute an element after the GEMM overwrote C) and takes, per 128x128
-// tile, the column sums over the tile's rows and the row sums over its
-// columns (and the absolute sums, FP32 with upward rounding, as in the fused
-// epilogue).  grid = tiles, 256 threads, 128 KiB dynamic shared memory.
+// One pass over C that takes, per 128x128 tile, the column sums over the
+// tile's rows and the row sums over its columns (and the absolute sums, FP32
+// with upward rounding), with the fused epilogue's thread mapping and order,
+// so the sums have the epilogue's bits.  The unfused ablation also keeps a
+// copy of C_in in Cc (needed to recompute an element after the GEMM overwrote
+// C); the split-K reduction of small grids takes the sums alone (Cc null).
+// grid = tiles, 256 threads, 128 KiB dynamic shared memory.
 __global__ void __launch_bounds__(256) enc_c_kernel(const double *__restrict__ C, long long ldc,
                                                     double *__restrict__ Cc, long long ldcc, long long M,
                                                     long long N, int nI, double *__restrict__ ccs,
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(256) enc_c_kernel(const double *__restrict__ C
     double v = 0.0;
     if (il < mI && jl < nJt) {
       v = C[(i0 + il) + (j0 + jl) * ldc];
-      Cc[(i0 + il) + (j0 + jl) * ldcc] = v;
+      if (Cc) Cc[(i0 + il) + (j0 + jl) * ldcc] = v;
     }
     tbuf[jl * 128 + il] = v;
   }

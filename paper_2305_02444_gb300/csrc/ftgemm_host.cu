@@ -80,7 +80,7 @@ struct Workspace {
   bool init = false;
   Buf acs, bcs, arowabs, aabsmax, bcolabs, babsmax, part_abs, part_max;
   Buf part_abs2, part_max2, enc_cnt;  // op(B)'s partials, group counters of the checksum pass
-  Buf rep, loc, flips, tile_off;
+  Buf rep, loc, flips;              // flips: the injection table, then its per-tile offsets
   Buf stA, stB, stC;        // aligned copies of unaligned operands
   Buf hA, hB, hC;           // device copies for ftgemm_d_host
   Buf W, wpc, wpr;          // split-K partial tiles and predicted-checksum partials
@@ -96,6 +96,7 @@ struct Workspace {
   Buf ipin[2];              // pinned staging of the injection upload, used in turn
   cudaEvent_t ipin_ev[2] = {nullptr, nullptr};  // recorded after each staging buffer's copies
   int ipin_next = 0;
+  bool encc_attr = false;   // enc_c_kernel's shared-memory attribute set on this device
   // the last injected call, for ftgemm_injection_log
   long long last_nflips = 0;
   std::vector<long long> last_perm;  // sorted position -> original index
@@ -464,7 +465,9 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
     const long long ta = tile_of(L[a]), tb = tile_of(L[b]);
     return ta != tb ? ta < tb : L[a].kstep < L[b].kstep;
   });
-  const size_t fbytes = sizeof(DevFlip) * (size_t)std::max(1LL, nf);
+  // the flip table and the per-tile offsets travel in one copy: one staging
+  // buffer, one device buffer (offsets at a 256-byte aligned position)
+  const size_t fbytes = (sizeof(DevFlip) * (size_t)std::max(1LL, nf) + 255) & ~(size_t)255;
   const size_t obytes = sizeof(int) * (size_t)(ntiles + 1);
   // two pinned staging buffers in turn: the one taken now may still be read
   // by the copies of the call before the previous one, so wait for its event
@@ -474,8 +477,7 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
   if (!w.ipin_ev[k] && cudaEventCreateWithFlags(&w.ipin_ev[k], cudaEventDisableTiming) != cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (cudaEventSynchronize(w.ipin_ev[k]) != cudaSuccess) return FTGEMM_ERR_CUDA;
-  if (ensure(w.flips, fbytes) || ensure(w.tile_off, obytes) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096))
-    return FTGEMM_ERR_NOMEM;
+  if (ensure(w.flips, fbytes + obytes) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096)) return FTGEMM_ERR_NOMEM;
   DevFlip *hf = (DevFlip *)w.ipin[k].p;
   int *ho = (int *)((char *)w.ipin[k].p + fbytes);
   std::fill(ho, ho + ntiles + 1, 0);
@@ -486,13 +488,12 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
     ho[tile_of(f) + 1]++;
   }
   for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
-  cudaMemcpyAsync(w.flips.p, hf, sizeof(DevFlip) * nf, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(w.tile_off.p, ho, obytes, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(w.flips.p, hf, fbytes + obytes, cudaMemcpyHostToDevice, s);
   cudaEventRecord(w.ipin_ev[k], s);
   w.last_nflips = nf;
   w.last_perm = perm;
   p.flips = (DevFlip *)w.flips.p;
-  p.tile_off = (const int *)w.tile_off.p;
+  p.tile_off = (const int *)((const char *)w.flips.p + fbytes);
   *inj = true;
   return 0;
 }
@@ -685,7 +686,36 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     p.W = (double *)w.W.p;
     p.wpc = (double *)w.wpc.p;
     p.wpr = (double *)w.wpr.p;
+    // a small split grid (all tiles split, fewer than the SMs): the
+    // reduction's C-side checksum sums come from a pass over C on the second
+    // stream while the partial kernel runs (C is not written before the
+    // reduction), instead of from the reduction's few CTAs
+    const bool csums = ft && beta != 0.0 && tail_base == 0 && tail_count < w.nsm;
+    if (csums) {
+      if (ensure(w.uccs, sizeof(double) * nI * N) || ensure(w.uccsa, sizeof(double) * nI * N) ||
+          ensure(w.ucrs, sizeof(double) * nJ * M) || ensure(w.ucrsa, sizeof(double) * nJ * M))
+        return FTGEMM_ERR_NOMEM;
+      if ((rc = ensure_side(w))) return rc;
+      cudaEventRecord(w.fork_ev, s);
+    }
     if (e == cudaSuccess) e = launch(1, mW);
+    if (csums && e == cudaSuccess) {
+      if (!w.encc_attr) {
+        cudaFuncSetAttribute(enc_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
+        w.encc_attr = true;
+      }
+      cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+      enc_c_kernel<<<(unsigned)ntiles, 256, 128 * 128 * 8, w.side>>>(Cuse, ldcU, nullptr, 0, M, N, (int)nI,
+                                                                      (double *)w.uccs.p, (double *)w.uccsa.p,
+                                                                      (double *)w.ucrs.p, (double *)w.ucrsa.p);
+      e = cudaGetLastError();
+      cudaEventRecord(w.join_ev, w.side);
+      cudaStreamWaitEvent(s, w.join_ev, 0);
+      p.csums = 1;
+      p.ccs = (const double *)w.uccs.p; p.ccsa = (const double *)w.uccsa.p;
+      p.crs = (const double *)w.ucrs.p; p.crsa = (const double *)w.ucrsa.p;
+      g_launches++;
+    }
     // fewer tiles than SMs: sum the partial tiles over the whole GPU first
     // (the reduction has one CTA per tile and is FP64-add bound)
     p.presummed = tail_count < w.nsm ? 1 : 0;
@@ -793,10 +823,9 @@ int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, 
     return rc;
   // pass 2: copy of C_in and its per-tile row/column sums
   if (beta != 0.0) {
-    static bool attr = false;
-    if (!attr) {
+    if (!w.encc_attr) {
       cudaFuncSetAttribute(enc_c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
-      attr = true;
+      w.encc_attr = true;
     }
     enc_c_kernel<<<(unsigned)ntiles, 256, 128 * 128 * 8, s>>>(C, ldc, (double *)w.uC.p, ldcc, M, N, (int)nI,
                                                                (double *)w.uccs.p, (double *)w.uccsa.p,
@@ -1016,7 +1045,7 @@ int ftgemm_finalize(void) {
   Workspace &w = g_ws[dev];
   cudaDeviceSynchronize();
   Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
-                  &w.rep, &w.loc, &w.flips, &w.tile_off, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
+                  &w.rep, &w.loc, &w.flips, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
                   &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
                   &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB,
                   &w.part_abs2, &w.part_max2, &w.enc_cnt};

@@ -511,8 +511,8 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   // FP32 pipe with upward rounding (each partial sum stays an upper bound).
   const int r = tid & 127, h = tid >> 7;
   // beta-side sums of C for the predicted checksums and the thresholds
-  if (MODE == 3 && use_c) {
-    // from the separate pass over C
+  if ((MODE == 3 || (MODE == 2 && FT && p.csums)) && use_c) {
+    // from the separate pass over C (the same sums, same order)
     if (tid < 128) {
       s_cc[tid] = tid < nJt ? p.ccs[(long long)I * p.N + j0 + tid] : 0.0;
       s_cca[tid] = tid < nJt ? p.ccsa[(long long)I * p.N + j0 + tid] : 0.0;

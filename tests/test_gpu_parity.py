@@ -431,8 +431,9 @@ def test_splitk_auto_small_square(ft, orc):
     n0 = ft.ftgemm_launch_count()
     rc, rep, out = run_gpu(ft, P, 1.5, 0.5)
     assert rc == 0
-    # checksum pass (one kernel per operand), partials, their sum over the whole GPU, verifying reduction
-    assert ft.ftgemm_launch_count() - n0 == 2 + 3
+    # checksum pass (one kernel per operand); partials, with the C-side checksum sums beside them;
+    # the partials' sum over the whole GPU; verifying reduction
+    assert ft.ftgemm_launch_count() - n0 == 2 + 4
     assert_parity(orc, P, out, ref, E)
     assert rep["flagged_rows"] == 0 and rep["flagged_cols"] == 0
 
