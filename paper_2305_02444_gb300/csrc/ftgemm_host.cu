@@ -395,14 +395,16 @@ int device_sms(int dev) {
 // acs (nI x Kp), aabsmax, arowabs, bcs (nJ x Kp), babsmax, bcolabs.
 int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, const double *A, long long lda,
                const double *B, long long ldb, long long Kp, double *acs, double *aabsmax, double *arowabs,
-               double *bcs, double *babsmax, double *bcolabs, Workspace &w, cudaStream_t s) {
+               double *bcs, double *babsmax, double *bcolabs, Workspace &w, cudaStream_t s,
+               bool concurrent = true) {
   const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN;
   int dev = 0;
   cudaGetDevice(&dev);
   EncOp oa, ob;
   enc_ops(ta_t, tb_t, M, N, K, device_sms(dev), oa, ob);
-  // op(A)'s pass on s and op(B)'s on the second stream, each with its own
-  // partials and group counters (zeroed when allocated, reset by each pass)
+  // op(A)'s pass on s and op(B)'s on the second stream (concurrent), or both
+  // on s, each with its own partials and group counters (zeroed when
+  // allocated, reset by each pass)
   const size_t ncnt = (size_t)(oa.nG + ob.nG);
   if (ensure(w.part_abs, sizeof(double) * oa.part_len()) || ensure(w.part_max, sizeof(double) * oa.max_len()) ||
       ensure(w.part_abs2, sizeof(double) * ob.part_len()) || ensure(w.part_max2, sizeof(double) * ob.max_len()))
@@ -411,19 +413,25 @@ int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, cons
     if (ensure(w.enc_cnt, sizeof(unsigned int) * ncnt)) return FTGEMM_ERR_NOMEM;
     if (cudaMemset(w.enc_cnt.p, 0, w.enc_cnt.cap) != cudaSuccess) return FTGEMM_ERR_CUDA;
   }
-  if (int rc = ensure_side(w)) return rc;
+  if (concurrent)
+    if (int rc = ensure_side(w)) return rc;
   unsigned int *cnt = (unsigned int *)w.enc_cnt.p;
   if (Kp != K) {
     cudaMemsetAsync(acs, 0, sizeof(double) * nI * Kp, s);
     cudaMemsetAsync(bcs, 0, sizeof(double) * nJ * Kp, s);
   }
-  cudaEventRecord(w.fork_ev, s);
-  cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+  const cudaStream_t sb = concurrent ? w.side : s;
+  if (concurrent) {
+    cudaEventRecord(w.fork_ev, s);
+    cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+  }
   launch_enc(oa, A, lda, acs, Kp, (double *)w.part_abs.p, (double *)w.part_max.p, cnt, arowabs, aabsmax, s);
   launch_enc(ob, B, ldb, bcs, Kp, (double *)w.part_abs2.p, (double *)w.part_max2.p, cnt + oa.nG, bcolabs, babsmax,
-             w.side);
-  cudaEventRecord(w.join_ev, w.side);
-  cudaStreamWaitEvent(s, w.join_ev, 0);
+             sb);
+  if (concurrent) {
+    cudaEventRecord(w.join_ev, w.side);
+    cudaStreamWaitEvent(s, w.join_ev, 0);
+  }
   g_launches += 2;
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
@@ -1727,6 +1735,24 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     cudaMemsetAsync(w.spEA.p, 0, sizeof(int) * M, s);
     cudaMemsetAsync(w.spEB.p, 0, sizeof(int) * N, s);
   }
+  // ft 2: the operand checksum pass (FP64 adds) runs on the second stream
+  // while the slicing passes (integer and memory work) run on s
+  const long long Kq = (K + BK - 1) / BK * BK, ldp1 = (nI + 1) & ~1LL, ldp2 = (M + 1) & ~1LL;
+  if (ft == 2) {
+    if (ensure(w.acs, sizeof(double) * nI * Kq) || ensure(w.bcs, sizeof(double) * nJ * Kq) ||
+        ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
+        ensure(w.bcolabs, sizeof(double) * N) || ensure(w.babsmax, sizeof(double) * nJ) ||
+        ensure(w.uP1, sizeof(double) * ldp1 * N) || ensure(w.uP2, sizeof(double) * ldp2 * nJ))
+      return FTGEMM_ERR_NOMEM;
+    if (!tma_ok(A, lda) || !tma_ok(B, ldb)) return FTGEMM_ERR_UNALIGNED;
+    if ((rc = ensure_side(w))) return rc;
+    cudaEventRecord(w.fork_ev, s);
+    cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+    if ((rc = run_encode(ta_t, tb_t, M, N, K, A, lda, B, ldb, Kq, (double *)w.acs.p, (double *)w.aabsmax.p,
+                         (double *)w.arowabs.p, (double *)w.bcs.p, (double *)w.babsmax.p, (double *)w.bcolabs.p,
+                         w, w.side, false)))
+      return rc;
+  }
   // op(A)(i, k): 'T' has k contiguous; op(B)(k, j) seen as row j: 'N' has k contiguous
   const int nsm = device_sms(dev);
   if (ensure(w.spMB, sizeof(unsigned long long) * (size_t)std::max(M, N))) return FTGEMM_ERR_NOMEM;
@@ -1778,18 +1804,10 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   p.verify = ft;
   cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   if (ft == 2) {
-    // FP64 predicted checksums of the 128 x 128 tiles from the original operands
-    const long long Kq = (K + BK - 1) / BK * BK, ldp1 = (nI + 1) & ~1LL, ldp2 = (M + 1) & ~1LL;
-    if (ensure(w.acs, sizeof(double) * nI * Kq) || ensure(w.bcs, sizeof(double) * nJ * Kq) ||
-        ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
-        ensure(w.bcolabs, sizeof(double) * N) || ensure(w.babsmax, sizeof(double) * nJ) ||
-        ensure(w.uP1, sizeof(double) * ldp1 * N) || ensure(w.uP2, sizeof(double) * ldp2 * nJ))
-      return FTGEMM_ERR_NOMEM;
-    if (!tma_ok(A, lda) || !tma_ok(B, ldb)) return FTGEMM_ERR_UNALIGNED;
-    if ((rc = run_encode(ta_t, tb_t, M, N, K, A, lda, B, ldb, Kq, (double *)w.acs.p, (double *)w.aabsmax.p,
-                         (double *)w.arowabs.p, (double *)w.bcs.p, (double *)w.babsmax.p, (double *)w.bcolabs.p,
-                         w, s)))
-      return rc;
+    // FP64 predicted checksums of the 128 x 128 tiles from the original
+    // operands: the checksum pass (side stream) joins here
+    cudaEventRecord(w.join_ev, w.side);
+    cudaStreamWaitEvent(s, w.join_ev, 0);
     p.P1 = (const double *)w.uP1.p; p.ldp1 = ldp1; p.P2 = (const double *)w.uP2.p; p.ldp2 = ldp2;
     if (tc) {
       // P1 = acs^T op(B) and P2 = op(A) bcs by the same emulated product on the
