@@ -780,11 +780,17 @@ int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
   const size_t abytes = sizeof(double) * (size_t)(lda * acols), bbytes = sizeof(double) * (size_t)(ldb * bcols);
   const size_t cbytes = sizeof(double) * (size_t)(ldc * N);
   if (ensure(w.hA, abytes) || ensure(w.hB, bbytes) || ensure(w.hC, cbytes)) return FTGEMM_ERR_NOMEM;
+  if ((rc = ensure_side(w))) return rc;
+  // op(B) goes up on the second stream, beside op(A) and C (two copy engines)
+  cudaEventRecord(w.fork_ev, s);
+  cudaStreamWaitEvent(w.side, w.fork_ev, 0);
   if (K > 0 && alpha != 0.0) {
     if (abytes) cudaMemcpyAsync(w.hA.p, A, abytes, cudaMemcpyHostToDevice, s);
-    if (bbytes) cudaMemcpyAsync(w.hB.p, B, bbytes, cudaMemcpyHostToDevice, s);
+    if (bbytes) cudaMemcpyAsync(w.hB.p, B, bbytes, cudaMemcpyHostToDevice, w.side);
   }
   if (beta != 0.0) cudaMemcpyAsync(w.hC.p, C, cbytes, cudaMemcpyHostToDevice, s);
+  cudaEventRecord(w.join_ev, w.side);
+  cudaStreamWaitEvent(s, w.join_ev, 0);
   ftgemm_report local;
   memset(&local, 0, sizeof(local));
   ftgemm_report *r = rep ? rep : &local;
