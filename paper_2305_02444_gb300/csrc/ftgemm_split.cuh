@@ -147,6 +147,23 @@ __device__ __forceinline__ void split_tile_report(const SplitParams &p, const in
   if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
 }
 
+// The threshold test of one row or column checksum of the emulated product:
+// ref, the sum of the output; cs / ca, the
+// sums of C and of |C| (FP32 rounded up); P, the predicted checksum of the
+// product; S64, the absolute product bound; sig, the splitting-error scale.
+// Returns 0 verified, 1 flagged, 2 unverifiable.
+__device__ __forceinline__ int split_check(const SplitParams &p, double ref, double cs, double ca, double P, double S64,
+                                           double sig) {
+  const bool use_c = p.beta != 0.0;
+  const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
+  const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
+  const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
+  const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) + split_err +
+                     n * 0x1p-1021;
+  if (!isfinite(pred) || !isfinite(tau)) return 2;
+  return fabs(ref - pred) <= tau ? 0 : 1;
+}
+
 // The end of a tile shared by the split kernels, run by 256 threads: sC holds
 // the tile's unscaled FP64 accumulators (column-major, 128 x 128); scale to
 // the output, verify with the FP64 checksums (CK 2), recompute the flagged
@@ -230,17 +247,13 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
       }
       const double P = col ? p.P1[(long long)I + (long long)(j0 + idx) * p.ldp1]
                            : p.P2[(long long)(i0 + idx) + (long long)J * p.ldp2];
-      const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
       const double S64 = col ? p.bcolabs[j0 + idx] * p.aabsmax[I] : p.arowabs[i0 + idx] * p.babsmax[J];
-      const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
       // splitting error of the reference sum, plus that of the predicted
       // checksum when it is an emulated product as well
       if (p.ePA) sig += col ? ldexp(1.0, p.ePA[I] + p.eB[j0 + idx]) : ldexp(1.0, p.eA[i0 + idx] + p.ePB[J]);
-      const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
-      const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) +
-                         split_err + n * 0x1p-1021;
-      if (!isfinite(pred) || !isfinite(tau)) atomicAdd(&cnt[4], 1);
-      else if (!(fabs(ref - pred) <= tau)) {
+      const int r = split_check(p, ref, cs, ca, P, S64, sig);
+      if (r == 2) atomicAdd(&cnt[4], 1);
+      else if (r == 1) {
         if (col) s_fc[atomicAdd(&cnt[1], 1)] = idx;
         else s_fr[atomicAdd(&cnt[0], 1)] = idx;
       }

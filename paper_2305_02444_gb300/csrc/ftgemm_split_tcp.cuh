@@ -82,23 +82,6 @@ __device__ __forceinline__ float colsum16_ru(float (&v)[16], int lane) {
   return __fadd_ru(v[0], __shfl_xor_sync(0xffffffffu, v[0], 16));
 }
 
-// The threshold test of one row or column checksum of the emulated product
-// (the bound of split_tile_finish): ref, the sum of the output; cs / ca, the
-// sums of C and of |C| (FP32 rounded up); P, the predicted checksum of the
-// product; S64, the absolute product bound; sig, the splitting-error scale.
-// Returns 0 verified, 1 flagged, 2 unverifiable.
-__device__ __forceinline__ int split_check(const SplitParams &p, double ref, double cs, double ca, double P, double S64,
-                                           double sig) {
-  const bool use_c = p.beta != 0.0;
-  const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
-  const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
-  const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
-  const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) + split_err +
-                     n * 0x1p-1021;
-  if (!isfinite(pred) || !isfinite(tau)) return 2;
-  return fabs(ref - pred) <= tau ? 0 : 1;
-}
-
 // The folder warps' work on one tile (4 warps, thread = tile row fw*32 +
 // lane): fold each pair (k-chunk) of the tile into the FP64 accumulators as
 // the MMAs finish it, inject, then finish the tile (see the file comment).
