@@ -73,3 +73,29 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         steps, warmup = 1, 3
     assert bench.reference_arm(A()) is None
     assert not called
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the CPU oracle timed on a row sample of the
+    bench workload) prints one JSON line with the keys the benchmark contract
+    names, on the same metric and configuration as the library's arm."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["config"] == bench.main_config()
+    for k in ("value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data"):
+        assert k in d, k
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["warmup"] >= 3
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
