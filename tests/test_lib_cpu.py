@@ -96,3 +96,28 @@ def test_correction_knob_codes(ft):
     assert ft.ftgemm_set_correction(-1) == -1
     assert ft.ftgemm_set_correction(1) == 0
     assert ft.ftgemm_set_correction(0) == 0
+
+
+def test_autotune_signature_and_cache(tmp_path, monkeypatch):
+    """The batched schedule autotuner's host side: the batch signature is the
+    multiset of (layouts, shape) -- order-free, sensitive to every field --,
+    a missing or corrupt cache reads as empty, and a cached signature returns
+    its schedule without timing anything."""
+    import json
+    from paper_2305_02444_gb300 import autotune
+    monkeypatch.setattr(autotune, "_device_name", lambda: "cpu")
+    shapes = [("N", "N", 100, 200, 300), ("T", "N", 64, 64, 64), ("N", "T", 1024, 32, 77)]
+    sig = autotune.signature(shapes)
+    assert sig == autotune.signature(list(reversed(shapes)))
+    for k in range(5):
+        changed = [list(s) for s in shapes]
+        changed[0][k] = "T" if k < 2 else changed[0][k] + 1
+        assert autotune.signature([tuple(s) for s in changed]) != sig
+    assert len(set(autotune.CANDIDATES)) == len(autotune.CANDIDATES) == 9
+    path = tmp_path / "sched.json"
+    assert autotune.load_cache(str(path)) == {}
+    path.write_text("{not json")
+    assert autotune.load_cache(str(path)) == {}
+    path.write_text(json.dumps({f"cpu:{sig}": {"schedule": 17, "ms": {"17": 1.0}, "n": 3}}))
+    best, ms = autotune.tune_batched(shapes, cache_path=str(path))
+    assert best == 17 and ms == {"17": 1.0}
