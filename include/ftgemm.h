@@ -35,9 +35,11 @@
  *    gives C = beta*C; beta == 0 never reads C (NaN in C does not propagate).
  *  - The library owns a lazily grown per-device workspace (operand checksum
  *    vectors, the device report, the injection table, staging for unaligned
- *    operands and for ftgemm_d_host), released by ftgemm_finalize().  Calls
- *    share it, so calls must not run concurrently on different streams or
- *    host threads.
+ *    operands and for ftgemm_d_host) and a second stream on which a call runs
+ *    independent parts of its work (forked from and joined back into the
+ *    caller's stream by events, so the call stays stream-ordered), released
+ *    by ftgemm_finalize().  Calls share them, so calls must not run
+ *    concurrently on different streams or host threads.
  *  - Operands whose base address is not 16-byte aligned or whose leading
  *    dimension is odd are first copied into aligned workspace (the tensor
  *    memory accelerator needs 16-byte aligned rows); results are the same.
@@ -187,7 +189,9 @@ int ftgemm_d_noft(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
  *  - Every call shares the one array and it keeps the last call's contents;
  *    the call clears what must start at zero.  Calls that overlap on the GPU
  *    (different streams, threads or processes' graphs) race on it.
- * Results equal ftgemm_d's (same kernels).  Returns as ftgemm_d does. */
+ * Same kernels as ftgemm_d, always on whole tiles: where ftgemm_d splits K
+ * (grids of few tiles) the two sum in different orders and agree within the
+ * parity bound; elsewhere their results are equal.  Returns as ftgemm_d does. */
 int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                      const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                      double *C, int64_t ldc, ftgemm_report *rep, void *stream);
