@@ -17,6 +17,11 @@ function cites the passage it follows:
                           with source-level fault injection (§2.2, §3.2).
 * ``partial``          -- the accumulator value after the first kend products.
 * ``random_flips``     -- the seeded fault list (splitmix64, counter based).
+* ``split``            -- the split-precision form (module ``split.py``,
+                          numpy and Python integers): the BF16-slice
+                          emulation of the product evaluated exactly
+                          (``split_gemm``) and the plain BF16 form
+                          (``bf16_round``, ``bf16_gemm``).
 
 Parity of the oracle to numbers printed in the paper is unpinned: the paper
 prints none (its figures are elided and it gives no worked example).  Every
@@ -242,3 +247,6 @@ def parity_tol(K: int, E: np.ndarray) -> np.ndarray:
     """Componentwise parity bound max(4K, 2K+6) * u * E (4Ku as the target
     states; for K < 3 the rigorous two-sided bound (2K+5)u is larger)."""
     return max(4 * K, 2 * K + 6) * U * E
+
+
+from .split import bf16_gemm, bf16_round, row_exponents, slices, split_gemm, split_width  # noqa: E402
