@@ -67,8 +67,11 @@ extern "C" {
 #define FTGEMM_ERR_INJECT 6     /* an explicit fault lies outside the problem */
 #define FTGEMM_ERR_TENSORMAP 7  /* a TMA descriptor could not be encoded */
 #define FTGEMM_ERR_SCRATCH 8    /* ftgemm_d_noalloc: the problem needs more scratch than it holds */
-#define FTGEMM_ERR_UNALIGNED 9  /* ftgemm_d_noalloc / ftgemm_d_unfused: an operand is not
-                                   16-byte aligned or its leading dimension is odd */
+#define FTGEMM_ERR_UNALIGNED 9  /* ftgemm_d_noalloc, ftgemm_d_unfused, the batched calls and
+                                   ftgemm_d_split with ft = 2: an operand is not 16-byte
+                                   aligned or its leading dimension is odd */
+#define FTGEMM_ERR_BATCH 10     /* batched calls: count < 0, or a NULL plan pointer or
+                                   per-problem array (count > 0) */
 
 /* Size of the device array that ftgemm_d_noalloc uses as scratch. */
 #define FTGEMM_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -215,8 +218,11 @@ int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, 
  * one CTA per SM takes (problem, tile) work items from a global counter, in
  * an order fixed by the schedule.  Each problem gets its own report
  * (reps[p], cap/loc set by the caller; up to 64 locations per problem).
- * Argument errors return -(100*p + i) for argument i of problem p; operands
- * must be 16-byte aligned with even leading dimensions (FTGEMM_ERR_UNALIGNED).
+ * Argument errors return -(100*p + i) for argument i of problem p, numbered
+ * as in ftgemm_d (so -(100*p + 8) is a bad lda); count < 0 or a NULL array
+ * (count > 0) returns FTGEMM_ERR_BATCH; all of these are found before any
+ * device work.  Operands must be 16-byte aligned with even leading
+ * dimensions (FTGEMM_ERR_UNALIGNED).
  * Injection (the process-global setting): mode 1 draws `count` faults over
  * the batch, fault f taking splitmix64 outputs 5f..5f+4 as (problem mod count,
  * row, col, kstep, bit) of that problem; mode 2 uses ftgemm_flip.problem.
@@ -291,7 +297,9 @@ int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
  * caller: acs (ceil(M/BM) x K, row stride K), aabsmax (ceil(M/BM)), arowabs
  * (M), bcs (ceil(N/BN) x K, row stride K), babsmax (ceil(N/BN)), bcolabs (N):
  *   acs[I*K+k] = sum_{i in I} op(A)(i,k),   aabsmax[I] = max_k sum_{i in I} |op(A)(i,k)|,
- *   arowabs[i] = sum_k |op(A)(i,k)|,        and symmetrically for op(B). */
+ *   arowabs[i] = sum_k |op(A)(i,k)|,        and symmetrically for op(B).
+ * Returns 0, -i for a bad argument i (this function's numbering: lda is 7,
+ * ldb is 9), or a positive FTGEMM_ERR_* code; M, N or K = 0 does nothing. */
 int ftgemm_encode_operands(char transA, char transB, int64_t M, int64_t N, int64_t K,
                            const double *A, int64_t lda, const double *B, int64_t ldb,
                            double *acs, double *aabsmax, double *arowabs, double *bcs,

@@ -894,7 +894,7 @@ int ftgemm_encode_operands(char transA, char transB, int64_t M, int64_t N, int64
                            double *babsmax, double *bcolabs, void *stream) {
   std::lock_guard<std::mutex> lk(g_mu);
   int rc = check_args(transA, transB, M, N, K, lda, ldb, std::max<int64_t>(1, M));
-  if (rc) return rc;
+  if (rc) return rc == -8 ? -7 : rc == -10 ? -9 : rc;  // lda, ldb are arguments 7 and 9 here
   if (M == 0 || N == 0 || K == 0) return 0;
   int dev = 0;
   Workspace *wp = workspace(&dev);
@@ -1047,7 +1047,8 @@ const char *ftgemm_strerror(int code) {
     case FTGEMM_ERR_INJECT: return "injected fault outside the problem";
     case FTGEMM_ERR_TENSORMAP: return "TMA descriptor encoding failed";
     case FTGEMM_ERR_SCRATCH: return "problem needs more scratch than ftgemm_d_noalloc holds";
-    case FTGEMM_ERR_UNALIGNED: return "operand not 16-byte aligned or leading dimension odd (ftgemm_d_noalloc)";
+    case FTGEMM_ERR_UNALIGNED: return "operand not 16-byte aligned or leading dimension odd";
+    case FTGEMM_ERR_BATCH: return "invalid batch: count < 0, or a NULL plan pointer or per-problem array";
     default: return "unknown error";
   }
 }
@@ -1329,9 +1330,12 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
                                const double *const *B, const int64_t *ldb, const double *beta, double *const *C,
                                const int64_t *ldc, int ft, int schedule, void *stream) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!plan_out) return -1;
+  if (!plan_out) return FTGEMM_ERR_BATCH;
   *plan_out = nullptr;
-  if (count < 0) return -2;
+  if (count < 0) return FTGEMM_ERR_BATCH;
+  if (count > 0 && (!transA || !transB || !M || !N || !K || !alpha || !A || !lda || !B || !ldb || !beta || !C ||
+                    !ldc))
+    return FTGEMM_ERR_BATCH;
   for (long long q = 0; q < count; ++q) {
     const int rc = check_args(transA[q], transB[q], M[q], N[q], K[q], lda[q], ldb[q], ldc[q]);
     if (rc) return (int)(rc - 100 * q);  // -(100*problem + argument)

@@ -121,3 +121,86 @@ def test_autotune_signature_and_cache(tmp_path, monkeypatch):
     path.write_text(json.dumps({f"cpu:{sig}": {"schedule": 17, "ms": {"17": 1.0}, "n": 3}}))
     best, ms = autotune.tune_batched(shapes, cache_path=str(path))
     assert best == 17 and ms == {"17": 1.0}
+
+
+@pytest.mark.parametrize("call", ["d", "noft", "host", "noalloc", "unfused", "split"])
+def test_empty_output_returns_before_the_device(ft, call):
+    """M = 0 or N = 0: nothing to compute, 0 returned before any device work."""
+    for M, N in ((0, 3), (3, 0)):
+        args = ("N", "N", M, N, 4, 1.0, 0, max(1, M), 0, 4, 0.5, 0, max(1, M))
+        if call == "d":
+            rc = ft.ftgemm_d(*args, stream=0)[0]
+        elif call == "noft":
+            rc = ft.ftgemm_d_noft(*args, stream=0)
+        elif call == "host":
+            rc = ft.ftgemm_d_host(*args, stream=0)[0]
+        elif call == "noalloc":
+            rc = ft.ftgemm_d_noalloc(*args, stream=0)[0]
+        elif call == "unfused":
+            rc = ft.ftgemm_d_unfused(*args, stream=0)[0]
+        else:
+            rc = ft.ftgemm_d_split(*args, nslices=7, ft=2, stream=0)[0]
+        assert rc == 0, (call, M, N, rc)
+    assert ft.ftgemm_launch_count() == 0
+
+
+@pytest.mark.parametrize("args,code", [
+    (("X", "N", 2, 2, 2, 2, 2, 2), -1), (("N", "N", -1, 2, 2, 2, 2, 2), -3),
+    (("N", "N", 3, 2, 2, 2, 2, 3), -8), (("N", "T", 2, 3, 2, 2, 2, 2), -10),
+    (("N", "N", 3, 2, 2, 3, 2, 2), -13),
+])
+def test_other_entry_points_number_arguments_as_ftgemm_d(ft, args, code):
+    ta, tb, M, N, K, lda, ldb, ldc = args
+    full = (ta, tb, M, N, K, 1.0, 0, lda, 0, ldb, 0.0, 0, ldc)
+    assert ft.ftgemm_d_noalloc(*full, report=False, stream=0)[0] == code
+    assert ft.ftgemm_d_unfused(*full, report=False, stream=0)[0] == code
+    assert ft.ftgemm_d_split(*full, nslices=3, ft=2, report=False, stream=0)[0] == code
+
+
+def test_split_checksum_form_code(ft):
+    base = ("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4)
+    for nslices, ftflag in ((3, 3), (3, -1), (0, 2)):   # ft 2 needs an emulated form
+        assert ft.ftgemm_d_split(*base, nslices=nslices, ft=ftflag, report=False, stream=0)[0] == -15
+
+
+@pytest.mark.parametrize("args,code", [
+    (("X", "N", 2, 2, 2, 2, 2), -1), (("N", "Q", 2, 2, 2, 2, 2), -2), (("N", "N", -1, 2, 2, 2, 2), -3),
+    (("N", "N", 2, -1, 2, 2, 2), -4), (("N", "N", 2, 2, -1, 2, 2), -5), (("N", "N", 3, 2, 2, 2, 2), -7),
+    (("T", "N", 2, 2, 3, 2, 3), -7), (("N", "N", 2, 2, 3, 2, 2), -9), (("N", "T", 2, 3, 2, 2, 2), -9),
+    (("N", "N", 0, 2, 2, 1, 2), 0), (("N", "N", 2, 2, 0, 2, 1), 0),
+])
+def test_encode_operands_argument_codes(ft, args, code):
+    """ftgemm_encode_operands numbers its own arguments (lda 7, ldb 9); an
+    empty problem returns 0 before the device."""
+    ta, tb, M, N, K, lda, ldb = args
+    z = [0] * 6
+    assert ft.ftgemm_encode_operands(ta, tb, M, N, K, 0, lda, 0, ldb, *z, stream=0) == code
+
+
+def test_batched_argument_codes_before_the_device(ft):
+    """-(100 p + i) for argument i (ftgemm_d's numbering) of problem p; count
+    < 0, a NULL per-problem array or a NULL plan pointer: FTGEMM_ERR_BATCH;
+    the plan calls on a NULL plan: -1.  All found before any device work."""
+    import ctypes
+    L = ft.lib()
+    ok = ("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4)
+    assert ft.ftgemm_batched([ok, ("N", "N", 4, 4, 4, 1.0, 0, 3, 0, 4, 0.0, 0, 4)])[0] == -108
+    assert ft.ftgemm_batched([("N", "Z") + ok[2:], ok])[0] == -2
+    assert ft.ftgemm_batched([ok, ok, ("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 3)])[0] == -213
+    a = ft._BatchArgs([ok])
+    args = list(a.args())
+    assert L.ftgemm_batched(-1, *args[1:], None, None) == ft.ERR_BATCH
+    for k in range(1, len(args)):
+        nulled = list(args)
+        nulled[k] = None
+        assert L.ftgemm_batched(1, *nulled[1:], None, None) == ft.ERR_BATCH, k
+    assert L.ftgemm_batched_plan_create(None, *args, 1, -1, None) == ft.ERR_BATCH
+    h = ctypes.c_void_p()
+    assert L.ftgemm_batched_plan_create(ctypes.byref(h), -3, *args[1:], 1, -1, None) == ft.ERR_BATCH
+    assert not h.value
+    assert L.ftgemm_batched_plan_launch(None, None) == -1
+    assert L.ftgemm_batched_plan_report(None, None, None) == -1
+    assert L.ftgemm_batched_plan_injection_log(None, None, 0) == -1
+    assert L.ftgemm_batched_plan_destroy(None) == -1
+    assert "batch" in ft.ftgemm_strerror(ft.ERR_BATCH)
+    assert ft.ftgemm_launch_count() == 0
