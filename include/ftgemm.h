@@ -123,8 +123,10 @@ typedef struct {
   int32_t problem;  /* batched calls: index of the problem; otherwise ignored */
 } ftgemm_flip;
 
-/* Injection setting, process-global, applied to every later ftgemm_d call
- * (not to ftgemm_d_noft).  mode 0: off.  mode 1: `count` faults per call at
+/* Injection setting, process-global, applied to every later call that checks
+ * its result: ftgemm_d, ftgemm_d_host, ftgemm_d_split with ft != 0, and the
+ * batched calls (a plan takes the setting when it is created); not to
+ * ftgemm_d_noft, ftgemm_d_noalloc or ftgemm_d_unfused.  mode 0: off.  mode 1: `count` faults per call at
  * positions drawn from splitmix64(seed): fault f takes outputs 4f..4f+3 of the
  * generator, n-th output = mix(seed + (n+1) * 0x9E3779B97F4A7C15), as
  * (row mod M, col mod N, kstep mod ceil(K/16), bit mod 63).  mode 2: the
@@ -322,10 +324,24 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
 
 /* K splitting (a tuning knob; results stay within the same bound): 0 picks
  * the number of k-splits automatically (the default: grids with fewer than
- * 4 tiles per SM split K so that every SM gets work, then a reduction kernel
- * sums the partial tiles and runs the verification on the whole tile),
- * 1 never splits, n >= 2 forces n splits (fewer when K is short). */
+ * 4 tiles per SM split K so that every SM gets work; larger grids whose last
+ * wave is partly empty run their full waves whole and split K of the tail
+ * tiles over the idle SMs; a reduction kernel sums the partial tiles and runs
+ * the verification on the whole tile), 1 never splits, n >= 2 forces n
+ * splits of every tile (fewer when K is short).  ftgemm_d_noalloc never
+ * splits; per-k-panel verification (ftgemm_set_panel_check) does not split. */
 int ftgemm_set_splitk(int nsplit);
+
+/* The K split that ftgemm_d (and ftgemm_d_host) would use for an M x N x K
+ * problem on a GPU with nsm SMs under the current settings (host only, no
+ * device work): *splits k-ranges (1: none) for the tiles from
+ * *first_split_tile on, in the kernels' tile order; the tiles before it run
+ * whole (*first_split_tile = 0: every tile split; = the tile count: none).
+ * ftgemm_d_noft plans the same way except that it ignores the per-k-panel
+ * setting.  Returns 0, or -i for a bad argument i (M, N, K < 0, nsm <= 0,
+ * NULL outputs). */
+int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits,
+                        int64_t *first_split_tile);
 
 /* Engine of ftgemm_d_split (results: the same bits for the emulated forms
  * on every engine, and for the plain BF16 form on the tcgen05 engines).

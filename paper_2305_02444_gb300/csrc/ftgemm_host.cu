@@ -283,6 +283,27 @@ int choose_tail_splits(long long ntiles, long long nks, int nsm) {
   return best <= 0.85 ? bestS : 1;
 }
 
+// The k-split plan of one FP64 call: S splits (1: none) of the tiles
+// [tail_base, ntiles), the tiles before tail_base whole.  Per-k-panel
+// verification never splits.
+struct KSplit {
+  int S;
+  long long tail_base;
+};
+KSplit plan_ksplit(long long ntiles, long long nks, int nsm, bool panel) {
+  KSplit k{panel ? 1 : choose_splits(ntiles, nks, nsm), 0};
+  // Large grids whose last wave is partly empty: the full waves take whole
+  // tiles, the tail tiles split K over the idle SMs (then a verifying reduction).
+  if (!panel && k.S <= 1) {
+    const int St = choose_tail_splits(ntiles, nks, nsm);
+    if (St > 1) {
+      k.S = St;
+      k.tail_base = ntiles - ntiles % nsm;
+    }
+  }
+  return k;
+}
+
 // 3-D fp64 tensor map over nz column-major matrices of rows x cols (ld), stacked.
 int make_map3(CUtensorMap *m, const double *ptr, long long rows, long long cols, long long nz, long long ld) {
   auto fn = encode_fn();
@@ -643,18 +664,9 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     }
   }
   const bool panel = ft && g_panel > 0 && nks > g_panel;
-  int S = panel ? 1 : choose_splits(ntiles, nks, w.nsm);
-  // Large grids whose last wave is partly empty: the full waves take whole
-  // tiles, the tail tiles split K over the idle SMs (then a verifying reduction).
-  long long tail_base = 0, tail_count = ntiles;
-  if (!panel && S <= 1) {
-    const int St = choose_tail_splits(ntiles, nks, w.nsm);
-    if (St > 1) {
-      S = St;
-      tail_count = ntiles % w.nsm;
-      tail_base = ntiles - tail_count;
-    }
-  }
+  const KSplit ksp = plan_ksplit(ntiles, nks, w.nsm, panel);
+  int S = ksp.S;
+  const long long tail_base = ksp.tail_base, tail_count = ntiles - ksp.tail_base;
   p.panel_slabs = panel ? g_panel : 0;
   cudaError_t e;
   auto launch = [&](int mode, const CUtensorMap &mW) {
@@ -992,6 +1004,26 @@ int ftgemm_set_correction(int mode) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (mode < 0 || mode > 1) return -1;
   g_correct = mode;
+  return 0;
+}
+
+int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits, int64_t *first_split_tile) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (M < 0) return -1;
+  if (N < 0) return -2;
+  if (K < 0) return -3;
+  if (nsm <= 0) return -4;
+  if (!splits) return -5;
+  if (!first_split_tile) return -6;
+  const long long ntiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN), nks = (K + BK - 1) / BK;
+  if (ntiles == 0 || nks == 0) {  // quick returns: no GEMM kernel
+    *splits = 1;
+    *first_split_tile = ntiles;
+    return 0;
+  }
+  const KSplit k = plan_ksplit(ntiles, nks, nsm, g_panel > 0 && nks > g_panel);
+  *splits = k.S;
+  *first_split_tile = k.S > 1 ? k.tail_base : ntiles;
   return 0;
 }
 

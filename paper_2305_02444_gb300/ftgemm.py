@@ -82,6 +82,9 @@ def lib():
         L.ftgemm_launch_count.restype = _i64
         L.ftgemm_set_panel_check.argtypes = [ctypes.c_int]
         L.ftgemm_set_panel_check.restype = ctypes.c_int
+        L.ftgemm_query_ksplit.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(_i64)]
+        L.ftgemm_query_ksplit.restype = ctypes.c_int
         L.ftgemm_set_splitk.argtypes = [ctypes.c_int]
         L.ftgemm_set_splitk.restype = ctypes.c_int
         L.ftgemm_set_correction.argtypes = [ctypes.c_int]
@@ -291,6 +294,14 @@ def ftgemm_set_split_engine(engine: int) -> int:
     1x2 / 2x2 clusters, 5 persistent tcgen05, 6 persistent tcgen05 on CTA pairs (cta_group::2)
     (ft=1 always runs on mma.sync)."""
     return lib().ftgemm_set_split_engine(engine)
+
+
+def ftgemm_query_ksplit(M, N, K, nsm=152):
+    """(rc, splits, first_split_tile): the K split ftgemm_d would use (host only)."""
+    sp = ctypes.c_int(0)
+    first = _i64(0)
+    rc = lib().ftgemm_query_ksplit(M, N, K, nsm, ctypes.byref(sp), ctypes.byref(first))
+    return rc, sp.value, first.value
 
 
 def ftgemm_launch_count() -> int:

@@ -204,3 +204,71 @@ def test_batched_argument_codes_before_the_device(ft):
     assert L.ftgemm_batched_plan_destroy(None) == -1
     assert "batch" in ft.ftgemm_strerror(ft.ERR_BATCH)
     assert ft.ftgemm_launch_count() == 0
+
+
+def test_ksplit_plan_of_the_measured_shapes(ft):
+    """On 152 SMs: 1024^3 (64 tiles) splits every tile; 4096^3 (1024 tiles,
+    6 waves + 112) runs 912 tiles whole and splits the 112 tail tiles 4 ways;
+    8192^3 (4096 tiles, the last wave 144 of 152) and the rank-256 update do
+    not split."""
+    assert ft.ftgemm_query_ksplit(4096, 4096, 4096) == (0, 4, 912)
+    rc, S, first = ft.ftgemm_query_ksplit(1024, 1024, 1024)
+    assert rc == 0 and S > 1 and first == 0
+    assert ft.ftgemm_query_ksplit(8192, 8192, 8192) == (0, 1, 4096)
+    assert ft.ftgemm_query_ksplit(8192, 8192, 256) == (0, 1, 4096)
+
+
+def test_ksplit_plan_properties(ft):
+    """For any shape: 1 <= S <= 32 k-ranges, none empty; S = 1 exactly when no
+    tile is split; grids under 4 tiles per SM split all tiles or none; larger
+    grids split at most their last, partly empty wave."""
+    import random
+    rng = random.Random(4)
+    for nsm in (152, 148, 7):
+        for _ in range(400):
+            M, N = rng.randint(1, 12000), rng.randint(1, 12000)
+            K = rng.choice([rng.randint(1, 64), rng.randint(1, 40000)])
+            rc, S, first = ft.ftgemm_query_ksplit(M, N, K, nsm)
+            assert rc == 0
+            ntiles = -(-M // 128) * -(-N // 128)
+            nks = -(-K // 16)
+            assert 1 <= S <= min(32, nks)
+            ks = -(-nks // S)
+            assert -(-nks // ks) == S                    # S non-empty k-ranges
+            assert (S == 1) == (first == ntiles)
+            if ntiles < 4 * nsm:
+                assert first in (0, ntiles)
+            else:
+                assert first in (ntiles - ntiles % nsm, ntiles)
+                assert S == 1 or ntiles % nsm != 0
+
+
+def test_ksplit_plan_follows_the_knobs(ft):
+    try:
+        assert ft.ftgemm_set_splitk(1) == 0
+        for n in (256, 1024, 4096):
+            assert ft.ftgemm_query_ksplit(n, n, n) == (0, 1, (n // 128) ** 2)
+        assert ft.ftgemm_set_splitk(4) == 0
+        assert ft.ftgemm_query_ksplit(1024, 1024, 1024) == (0, 4, 0)
+        assert ft.ftgemm_query_ksplit(4096, 4096, 4096) == (0, 4, 0)   # forced: every tile
+        assert ft.ftgemm_query_ksplit(256, 256, 32) == (0, 2, 0)       # 2 k-slabs: 2 splits
+        assert ft.ftgemm_set_splitk(0) == 0
+        assert ft.ftgemm_set_panel_check(16) == 0
+        assert ft.ftgemm_query_ksplit(1024, 1024, 1024) == (0, 1, 64)  # panel checks never split
+        assert ft.ftgemm_query_ksplit(1024, 1024, 160)[1] > 1          # 10 k-slabs: no panel check
+    finally:
+        ft.ftgemm_set_splitk(0)
+        ft.ftgemm_set_panel_check(0)
+
+
+def test_ksplit_query_arguments(ft):
+    import ctypes
+    L = ft.lib()
+    sp, first = ctypes.c_int(0), ctypes.c_int64(0)
+    for args, code in (((-1, 4, 4, 152), -1), ((4, -1, 4, 152), -2), ((4, 4, -1, 152), -3),
+                       ((4, 4, 4, 0), -4)):
+        assert L.ftgemm_query_ksplit(*args, ctypes.byref(sp), ctypes.byref(first)) == code
+    assert L.ftgemm_query_ksplit(4, 4, 4, 152, None, ctypes.byref(first)) == -5
+    assert L.ftgemm_query_ksplit(4, 4, 4, 152, ctypes.byref(sp), None) == -6
+    assert ft.ftgemm_query_ksplit(0, 300, 300) == (0, 1, 0)
+    assert ft.ftgemm_query_ksplit(300, 300, 0) == (0, 1, 9)
