@@ -1,0 +1,106 @@
+"""bench.py's host-side logic on CPU: the clock record of the timed region,
+the DRAM-traffic record that is only used while the kernel source it was
+taken on is unchanged, and the whole-job throughput arithmetic."""
+from __future__ import annotations
+
+import hashlib
+import os
+import shutil
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+pytest.importorskip("torch")
+import bench  # noqa: E402
+
+
+class _Proc:
+    """Stands in for the nvidia-smi sampler process."""
+
+    def __init__(self):
+        self.terminated = False
+
+    def terminate(self):
+        self.terminated = True
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _clocks(tmp_path, lines):
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(lines) + "\n")
+    proc, fh = _Proc(), open(tmp_path / "unused", "w")
+    out = bench.sample_clocks_stop(proc, fh, str(path))
+    assert proc.terminated
+    return out
+
+
+def test_clock_record_median_max_and_reasons(tmp_path):
+    """Median SM clock under load, the maximum clock, and every throttle
+    reason seen Active in any sample (nvidia-smi csv, noheader, nounits);
+    malformed lines are skipped."""
+    row = "0, {sm}, 2070, 1200.5, 0x{act:x}, {hw}, Not Active, Not Active, {pc}"
+    lines = [row.format(sm=s, act=0, hw="Not Active", pc="Not Active") for s in (1900, 1950, 2000)]
+    lines += [row.format(sm=1600, act=4, hw="Not Active", pc="Active"),
+              row.format(sm=1700, act=8, hw="Active", pc="Not Active"),
+              "garbage", "0, [N/A], 2070, 1, 0, Not Active, Not Active, Not Active, Not Active"]
+    out = _clocks(tmp_path, lines)
+    assert out["sm_mhz"] == 1900 and out["sm_max_mhz"] == 2070 and out["samples"] == 5
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    clean = _clocks(tmp_path, [row.format(sm=2070, act=0, hw="Not Active", pc="Not Active")] * 3)
+    assert clean["reasons"] == [] and clean["sm_mhz"] == 2070
+
+
+def test_clock_record_absent_without_sampler(tmp_path):
+    assert bench.sample_clocks_stop(None, None, str(tmp_path / "none.csv")) is None
+    assert _clocks(tmp_path, ["not a sample"]) is None
+
+
+def test_traffic_only_for_the_kernel_source_it_was_taken_on(tmp_path, monkeypatch):
+    """roofline.traffic comes from profiles/traffic.txt only while the
+    recorded hash equals that of the current kernel source; any edit of the
+    kernel, an unknown tag or a missing record gives null."""
+    src_rel = os.path.join("paper_2305_02444_gb300", "csrc", "ftgemm_kernel.cuh")
+    os.makedirs(tmp_path / "profiles")
+    os.makedirs(tmp_path / os.path.dirname(src_rel))
+    shutil.copy(os.path.join(ROOT, src_rel), tmp_path / src_rel)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.read_traffic("k") is None                       # no record
+    h = hashlib.sha256(open(tmp_path / src_rel, "rb").read()).hexdigest()[:16]
+    (tmp_path / "profiles" / "traffic.txt").write_text(f"# header\n\nk {h} 12345\nother {h} 7\n")
+    assert bench.read_traffic("k") == 12345.0
+    assert bench.read_traffic("missing") is None
+    with open(tmp_path / src_rel, "a") as f:
+        f.write("// edited\n")
+    assert bench.read_traffic("k") is None
+
+
+def test_committed_traffic_record_is_well_formed():
+    """Every record line: tag, 16 hex digits of the source hash, a byte count."""
+    for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        tag, h, nbytes = line.split()[:3]
+        assert len(h) == 16 and int(h, 16) >= 0 and int(nbytes) > 0 and tag
+
+
+def test_whole_job_throughput():
+    """value = units of all ranks / the slowest rank's time (weak scaling)."""
+    assert bench.job_tflops(1, 2.0e12, 4, 8.0) == pytest.approx(1.0)
+    assert bench.job_tflops(4, 2.0e12, 4, 8.0) == pytest.approx(4.0)
+
+
+def test_fp64_peak_from_unit_counts():
+    """152 SMs x 2 FP64 FMAs per clock each x 2 flops per FMA x 2070 MHz; the
+    measured peaks (or the stated fallback) carry both roofline denominators."""
+    assert bench.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+    peaks = bench.measured_peaks()
+    assert peaks["source"] in ("measured", "fallback") and peaks["hbm_gbs"] > 0 and peaks["bf16_tflops"] > 0
