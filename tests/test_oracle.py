@@ -227,6 +227,25 @@ def test_encode_operands_definition(orc, ta, tb):
     np.testing.assert_array_equal(e.bcolabs, np.abs(opB).sum(0))
 
 
+@pytest.mark.parametrize("ta,tb", list(itertools.product(TRANS, TRANS)))
+def test_encode_vectors_predict_tile_checksums(orc, ta, tb):
+    """Huang-Abraham invariant of the per-tile scheme (§2.2): a_I^T op(B)
+    is the column checksum e^T (op(A) op(B))_IJ of every tile, op(A) b_J its
+    row checksum; exact on integers, so a vector summed over the wrong rows,
+    the wrong axis or a shifted tile boundary fails."""
+    rng = np.random.default_rng(10)
+    M, N, K, BM, BN = 23, 17, 11, 8, 5
+    opA = rng.integers(-9, 10, (M, K)).astype(float); opB = rng.integers(-9, 10, (K, N)).astype(float)
+    e = orc.encode_operands(ta, tb, M, N, K, stored(opA, ta), stored(opB, tb), BM, BN)
+    P = opA.astype(np.int64) @ opB.astype(np.int64)
+    for I in range(-(-M // BM)):
+        rows = slice(I * BM, min(M, (I + 1) * BM))
+        for J in range(-(-N // BN)):
+            cols = slice(J * BN, min(N, (J + 1) * BN))
+            np.testing.assert_array_equal(e.acs[I] @ opB[:, cols], P[rows, cols].sum(0))
+            np.testing.assert_array_equal(opA[rows] @ e.bcs[J], P[rows, cols].sum(1))
+
+
 # --------------------------------------------------------------------------- seeded fault list
 
 def test_splitmix64_golden(orc):
