@@ -23,10 +23,11 @@ function cites the passage it follows:
                           (``split_gemm``) and the plain BF16 form
                           (``bf16_round``, ``bf16_gemm``).
 
-Parity of the oracle to numbers printed in the paper is unpinned: the paper
-prints none (its figures are elided and it gives no worked example).  Every
-function is pinned instead by closed forms, exact rational arithmetic,
-integer-exact cases and invariants in ``tests/test_oracle.py``.
+The paper prints no worked example and no numeric output to compare with,
+so every function is pinned by what the mathematics fixes: closed forms,
+exact rational arithmetic, integer-exact cases, the checksum invariants and
+brute force on tiny inputs (``tests/test_oracle.py``,
+``tests/test_oracle_split.py``).
 """
 from __future__ import annotations
 
