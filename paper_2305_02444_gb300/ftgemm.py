@@ -123,14 +123,24 @@ def lib():
     return _lib
 
 
-def _ptr(x) -> int | None:
-    if x is None:
-        return None
-    if isinstance(x, int):
+def _ptr(x, device: bool = True) -> int | None:
+    """Address of a matrix argument: None, a raw pointer (int), a float64 torch
+    tensor on the GPU (device arguments) or on the CPU (host arguments), or a
+    float64 numpy array (host arguments).  A tensor on the wrong side or of
+    another dtype raises instead of giving a kernel an address it cannot use."""
+    if x is None or isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
+        if bool(x.is_cuda) != device:
+            raise ValueError(f"expected a {'CUDA' if device else 'CPU'} tensor, got one on {x.device}")
+        if str(x.dtype) != "torch.float64":
+            raise ValueError(f"expected a float64 tensor, got {x.dtype}")
         return x.data_ptr()
-    if hasattr(x, "ctypes"):
+    if hasattr(x, "ctypes") and hasattr(x, "dtype"):
+        if device:
+            raise ValueError("a numpy array is host memory; this argument is a device pointer")
+        if str(x.dtype) != "float64":
+            raise ValueError(f"expected a float64 array, got {x.dtype}")
         return x.ctypes.data
     raise TypeError(type(x))
 
@@ -186,8 +196,8 @@ def ftgemm_d_host(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 
                   stream=None):
     """ftgemm_d on host buffers (copies in and out); returns (rc, report dict)."""
     r, locs = _report(loc_cap)
-    rc = lib().ftgemm_d_host(_c(transA), _c(transB), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta,
-                             _ptr(C), ldc, ctypes.byref(r), _stream(stream))
+    rc = lib().ftgemm_d_host(_c(transA), _c(transB), M, N, K, alpha, _ptr(A, False), lda, _ptr(B, False), ldb,
+                             beta, _ptr(C, False), ldc, ctypes.byref(r), _stream(stream))
     return rc, _report_dict(r, locs, loc_cap)
 
 

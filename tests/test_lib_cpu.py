@@ -272,3 +272,37 @@ def test_ksplit_query_arguments(ft):
     assert L.ftgemm_query_ksplit(4, 4, 4, 152, ctypes.byref(sp), None) == -6
     assert ft.ftgemm_query_ksplit(0, 300, 300) == (0, 1, 0)
     assert ft.ftgemm_query_ksplit(300, 300, 0) == (0, 1, 9)
+
+
+def test_binding_refuses_addresses_a_kernel_cannot_use(ft):
+    """Device arguments take CUDA float64 tensors or raw pointers; host
+    arguments (ftgemm_d_host) CPU float64 tensors or numpy arrays.  A tensor
+    on the wrong side or of another dtype raises before the library is called."""
+    import numpy as np
+    import torch
+
+    class CudaLike:   # what the binding reads from a CUDA tensor
+        is_cuda = True
+        dtype = torch.float64
+        device = "cuda:0"
+
+        def data_ptr(self):
+            return 4096
+
+    cpu64 = torch.zeros(16, dtype=torch.float64)
+    arr = np.zeros(16)
+    assert ft._ptr(CudaLike()) == 4096
+    assert ft._ptr(cpu64, device=False) == cpu64.data_ptr()
+    assert ft._ptr(arr, device=False) == arr.ctypes.data
+    assert ft._ptr(None) is None and ft._ptr(77) == 77
+    for bad, device in ((cpu64, True), (arr, True), (CudaLike(), False),
+                        (torch.zeros(4, dtype=torch.float32), False), (np.zeros(4, np.float32), False)):
+        with pytest.raises(ValueError):
+            ft._ptr(bad, device=device)
+    with pytest.raises(TypeError):
+        ft._ptr("not a buffer")
+    with pytest.raises(ValueError):
+        ft.ftgemm_d("N", "N", 4, 4, 4, 1.0, cpu64, 4, cpu64, 4, 0.0, cpu64, 4)
+    with pytest.raises(ValueError):
+        ft.ftgemm_d_host("N", "N", 4, 4, 4, 1.0, CudaLike(), 4, cpu64, 4, 0.0, cpu64, 4)
+    assert ft.ftgemm_launch_count() == 0
