@@ -133,12 +133,14 @@ struct SplitParams {
 };
 
 
-// One problem of a batch: its TMA descriptors (global memory, 64-byte aligned)
-// and its parameters (rep/loc/flips point at the problem's own slices).
-struct __align__(64) BatchProblem {
+// One problem of a batch: its TMA descriptors (global memory, 128-byte
+// aligned like every CUtensorMap) and its parameters (rep/loc/flips point at
+// the problem's own slices).
+struct __align__(128) BatchProblem {
   CUtensorMap tmA, tmB, tmC;
   Params p;
 };
+static_assert(alignof(BatchProblem) == 128 && alignof(CUtensorMap) == 128, "descriptor alignment");
 
 constexpr int ERR_TIMEOUT = 2;
 
