@@ -306,3 +306,46 @@ def test_binding_refuses_addresses_a_kernel_cannot_use(ft):
     with pytest.raises(ValueError):
         ft.ftgemm_d_host("N", "N", 4, 4, 4, 1.0, CudaLike(), 4, cpu64, 4, 0.0, cpu64, 4)
     assert ft.ftgemm_launch_count() == 0
+
+
+def test_missing_library_raises(monkeypatch):
+    """No fallback: without libftgemm.so every call raises."""
+    from paper_2305_02444_gb300 import ftgemm
+    monkeypatch.setattr(ftgemm, "_lib", None)
+    monkeypatch.setattr(ftgemm, "LIB_PATH", os.path.join(ROOT, "_no_such_dir", "libftgemm.so"))
+    with pytest.raises(RuntimeError):
+        ftgemm.lib()
+    with pytest.raises(RuntimeError):
+        ftgemm.ftgemm_d("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4)
+
+
+def test_product_code_never_imports_the_oracle():
+    """The package (the product path) has no import of the oracle, and no
+    committed Python file reaches into the scratch folder.  bench.py imports
+    the oracle only in oracle_sample (the CPU baseline and the reference arm)
+    and in the optional --split / --config5 reports, which check sampled rows
+    outside their timed regions."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_2305_02444_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(".py"):
+                src = open(os.path.join(dirpath, f)).read()
+                for node in ast.walk(ast.parse(src)):
+                    if isinstance(node, ast.Import):
+                        assert not any(a.name.split(".")[0] == "oracle" for a in node.names), f
+                    elif isinstance(node, ast.ImportFrom):
+                        assert (node.module or "").split(".")[0] != "oracle", f
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    allowed = {"oracle_sample", "split", "config5"}
+    for fn in tree.body:
+        for node in ast.walk(fn):
+            names = ([a.name for a in node.names] if isinstance(node, ast.Import)
+                     else [node.module or ""] if isinstance(node, ast.ImportFrom) else [])
+            if any(n.split(".")[0] == "oracle" for n in names):
+                assert isinstance(fn, ast.FunctionDef) and fn.name in allowed, getattr(fn, "name", "module level")
+    scratch = re.compile(r"(?<![A-Za-z0-9_])" + "_" + r"work(?![A-Za-z0-9_])")   # the git-ignored scratch folder
+    tracked = subprocess.run(["git", "ls-files", "*.py"], cwd=ROOT, capture_output=True, text=True).stdout.split()
+    for f in tracked:
+        if os.path.abspath(os.path.join(ROOT, f)) != os.path.abspath(__file__):
+            assert not scratch.search(open(os.path.join(ROOT, f)).read()), f
