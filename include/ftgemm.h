@@ -279,9 +279,9 @@ int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan);
  * compiles the checks out (overhead baseline).  Injection
  * (ftgemm_set_injection) flips bits of the FP64 accumulator after the slice
  * pair numbered `kstep` has been folded in (kstep < number of pairs).
- * Returns -14 for an invalid nslices, -15 for an invalid ft (ft = 2 needs
- * nslices >= 1 and operands that are 16-byte aligned with even leading
- * dimensions). */
+ * Returns -14 for an invalid nslices, -15 for an invalid ft (0, 1 or 2;
+ * ft = 2 needs nslices >= 1), FTGEMM_ERR_UNALIGNED when ft = 2 and an
+ * operand is not 16-byte aligned or has an odd leading dimension. */
 int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                    const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                    double *C, int64_t ldc, int nslices, int ft, ftgemm_report *rep, void *stream);
