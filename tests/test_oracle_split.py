@@ -267,3 +267,38 @@ def test_bf16_round_halfway_and_limits(orc):
     np.testing.assert_array_equal(got, want)
     assert math.copysign(1.0, got[12]) == -1.0
     assert np.isnan(orc.bf16_round(np.array([math.nan])))[0]
+
+
+def test_plain_form_is_exact_on_bf16_values(orc):
+    """Operands already on the bf16 grid (8 significant bits) are not changed
+    by the rounding: the plain form then equals the FP64 product."""
+    rng = np.random.default_rng(21)
+    A = rng.integers(-255, 256, (9, 13)) * 2.0 ** rng.integers(-20, 20, (9, 13))
+    B = rng.integers(-255, 256, (13, 7)) * 2.0 ** rng.integers(-20, 20, (13, 7))
+    C = rng.uniform(-1, 1, (9, 7))
+    np.testing.assert_array_equal(orc.bf16_round(A), A)
+    got, _ = orc.bf16_gemm("N", "N", 1.5, A, B, 0.5, C)
+    ref, _ = orc.gemm("N", "N", 1.5, A, B, 0.5, C)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_split_beta_zero_never_reads_c(orc):
+    rng = np.random.default_rng(22)
+    A = rng.uniform(-1, 1, (4, 6)); B = rng.uniform(-1, 1, (6, 5))
+    got = orc.split_gemm("N", "N", 1.0, A, B, 0.0, np.full((4, 5), np.nan), 3)
+    assert np.all(np.isfinite(got))
+    np.testing.assert_array_equal(got, orc.split_gemm("N", "N", 1.0, A, B, 0.0, np.zeros((4, 5)), 3))
+
+
+@pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "T"), ("T", "T")])
+def test_split_layouts_agree(orc, ta, tb):
+    """op(X) = X^T for 'T': every layout gives the bits of the 'N','N'
+    product of the transposed storage."""
+    rng = np.random.default_rng(23)
+    opA = rng.uniform(-1, 1, (7, 30)) * 10.0 ** rng.integers(-2, 3, (7, 30))
+    opB = rng.uniform(-1, 1, (30, 5))
+    C = rng.uniform(-1, 1, (7, 5))
+    A = opA if ta == "N" else opA.T.copy()
+    B = opB if tb == "N" else opB.T.copy()
+    np.testing.assert_array_equal(orc.split_gemm(ta, tb, 1.25, A, B, -0.5, C, 4),
+                                  orc.split_gemm("N", "N", 1.25, opA, opB, -0.5, C, 4))
