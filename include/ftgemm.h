@@ -72,6 +72,11 @@ extern "C" {
                                    aligned or its leading dimension is odd */
 #define FTGEMM_ERR_BATCH 10     /* batched calls: count < 0, or a NULL plan pointer or
                                    per-problem array (count > 0) */
+#define FTGEMM_ERR_TOO_LARGE 11 /* ftgemm_d_split: M or N above FTGEMM_SPLIT_MAX_ROWS */
+
+/* Largest M and N of ftgemm_d_split (the slicing passes run one block per 8
+ * operand rows along the 65535-block y dimension of their grids). */
+#define FTGEMM_SPLIT_MAX_ROWS 524280
 
 /* Size of the device array that ftgemm_d_noalloc uses as scratch. */
 #define FTGEMM_NOALLOC_SCRATCH_BYTES (32u << 20)
@@ -280,8 +285,10 @@ int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan);
  * (ftgemm_set_injection) flips bits of the FP64 accumulator after the slice
  * pair numbered `kstep` has been folded in (kstep < number of pairs).
  * Returns -14 for an invalid nslices, -15 for an invalid ft (0, 1 or 2;
- * ft = 2 needs nslices >= 1), FTGEMM_ERR_UNALIGNED when ft = 2 and an
- * operand is not 16-byte aligned or has an odd leading dimension. */
+ * ft = 2 needs nslices >= 1), FTGEMM_ERR_TOO_LARGE when M or N exceeds
+ * FTGEMM_SPLIT_MAX_ROWS (before any device work), FTGEMM_ERR_UNALIGNED when
+ * ft = 2 and an operand is not 16-byte aligned or has an odd leading
+ * dimension. */
 int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                    const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                    double *C, int64_t ldc, int nslices, int ft, ftgemm_report *rep, void *stream);

@@ -1081,6 +1081,7 @@ const char *ftgemm_strerror(int code) {
     case FTGEMM_ERR_SCRATCH: return "problem needs more scratch than ftgemm_d_noalloc holds";
     case FTGEMM_ERR_UNALIGNED: return "operand not 16-byte aligned or leading dimension odd";
     case FTGEMM_ERR_BATCH: return "invalid batch: count < 0, or a NULL plan pointer or per-problem array";
+    case FTGEMM_ERR_TOO_LARGE: return "ftgemm_d_split: M or N above FTGEMM_SPLIT_MAX_ROWS";
     default: return "unknown error";
   }
 }
@@ -1753,6 +1754,9 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   cudaStream_t s = (cudaStream_t)stream;
   if (K == 0 || alpha == 0.0)
     return gemm_impl(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rep, s, true);
+  // the slicing passes give each 8 rows of an operand one block along grid y
+  static_assert(FTGEMM_SPLIT_MAX_ROWS == 8LL * 65535, "largest row count of the slicing grids");
+  if (M > FTGEMM_SPLIT_MAX_ROWS || N > FTGEMM_SPLIT_MAX_ROWS) return FTGEMM_ERR_TOO_LARGE;
   int dev = 0;
   Workspace *wp = workspace(&dev);
   if (!wp) return FTGEMM_ERR_NODEVICE;

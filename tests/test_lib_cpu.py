@@ -349,3 +349,22 @@ def test_product_code_never_imports_the_oracle():
     for f in tracked:
         if os.path.abspath(os.path.join(ROOT, f)) != os.path.abspath(__file__):
             assert not scratch.search(open(os.path.join(ROOT, f)).read()), f
+
+
+def test_split_shape_limit_before_the_device(ft):
+    """ftgemm_d_split refuses M or N above FTGEMM_SPLIT_MAX_ROWS (the slicing
+    grids' limit) before any device work; at the limit it goes on (and, with
+    no GPU here, stops at the device)."""
+    big = ft.SPLIT_MAX_ROWS + 1
+    assert ft.ftgemm_d_split("N", "N", big, 4, 4, 1.0, 0, big, 0, 4, 0.0, 0, big, nslices=3, ft=0,
+                             report=False, stream=0)[0] == ft.ERR_TOO_LARGE
+    assert ft.ftgemm_d_split("N", "N", 4, big, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4, nslices=0, ft=0,
+                             report=False, stream=0)[0] == ft.ERR_TOO_LARGE
+    at = ft.SPLIT_MAX_ROWS
+    rc = ft.ftgemm_d_split("N", "N", at, 4, 4, 1.0, 0, at, 0, 4, 0.0, 0, at, nslices=3, ft=0,
+                           report=False, stream=0)[0]
+    assert rc != ft.ERR_TOO_LARGE
+    assert "FTGEMM_SPLIT_MAX_ROWS" in ft.ftgemm_strerror(ft.ERR_TOO_LARGE)
+    # K = 0: no slicing, the BLAS quick return applies at any size
+    assert ft.ftgemm_d_split("N", "N", big, 4, 0, 1.0, 0, big, 0, 1, 1.0, 0, big, nslices=3, ft=0,
+                             report=False, stream=0)[0] != ft.ERR_TOO_LARGE
