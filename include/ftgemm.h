@@ -294,8 +294,9 @@ int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, do
                    double *C, int64_t ldc, int nslices, int ft, ftgemm_report *rep, void *stream);
 
 /* ftgemm_d on HOST matrices: copies A, B (and C unless beta == 0) to device
- * workspace, runs ftgemm_d, copies C back, and waits for the stream.  Pinned
- * host memory makes the copies fastest; pageable memory also works. */
+ * workspace, runs ftgemm_d, copies the M x N result back (rows M..ldc-1 of C
+ * are left as they were), and waits for the stream.  Pinned host memory
+ * makes the copies fastest; pageable memory also works. */
 int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, ftgemm_report *rep, void *stream);

@@ -809,8 +809,16 @@ int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
   rc = gemm_impl(transA, transB, M, N, K, alpha, (const double *)w.hA.p, lda, (const double *)w.hB.p, ldb, beta,
                  (double *)w.hC.p, ldc, r, s, true);
   if (rc && rc != FTGEMM_ERR_TIMEOUT) return rc;
-  cudaMemcpyAsync(C, w.hC.p, cbytes, cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  // only the M x N block goes back: rows M..ldc-1 of the caller's C are not
+  // the call's to write (with beta == 0 the workspace never held them)
+  const cudaError_t ce =
+      ldc == M ? cudaMemcpyAsync(C, w.hC.p, cbytes, cudaMemcpyDeviceToHost, s)
+               : cudaMemcpy2DAsync(C, sizeof(double) * (size_t)ldc, w.hC.p, sizeof(double) * (size_t)ldc,
+                                   sizeof(double) * (size_t)M, (size_t)N, cudaMemcpyDeviceToHost, s);
+  if (ce != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_CUDA;
+  }
   return rc;
 }
 

@@ -405,6 +405,24 @@ def test_host_buffers_api(ft, orc):
     assert_parity(orc, P, C, ref, E)
 
 
+def test_host_buffers_beta_zero_leaves_padding(ft, orc):
+    """beta = 0 uploads no C, yet rows M..ldc-1 of the caller's C must come
+    back as they were: a first call with finite padding and beta != 0 leaves
+    that padding in the device workspace, which the second call (NaN
+    padding, beta = 0) must not copy back."""
+    P = make_problem("N", "N", 150, 70, 90, seed=73, pad=(0, 0, 5))
+    A, B = P["A"].pin_memory(), P["B"].pin_memory()
+    C1 = P["C"].clone()
+    C1[:, P["M"]:] = 7.0
+    rc, _ = ft.ftgemm_d_host("N", "N", 150, 70, 90, 1.0, A, P["lda"], B, P["ldb"], 0.5, C1.pin_memory(), P["ldc"])
+    assert rc == 0
+    ref, E = oracle_ref(orc, P, 1.5, 0.0)
+    C = P["C"].clone().pin_memory()
+    rc, rep = ft.ftgemm_d_host("N", "N", 150, 70, 90, 1.5, A, P["lda"], B, P["ldb"], 0.0, C, P["ldc"])
+    assert rc == 0 and rep["detected"] == 0
+    assert_parity(orc, P, C, ref, E)
+
+
 # ------------------------------------------------------------------------------ split-K
 
 @pytest.mark.parametrize("ta,tb", list(itertools.product("NT", "NT")))
