@@ -1,9 +1,10 @@
 """FT-DGEMM oracle: plain CPU statement of FT-GEMM's fault-tolerant DGEMM.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
-``bench.py``'s ``cpu_baseline`` / reference leg may import this package.  The
-GPU library (``paper_2305_02444_gb300``) shares no code with it and never
-imports it.
+``bench.py``'s CPU legs (the ``cpu_baseline`` sample, the reference arm, and
+the sampled-row accuracy checks of its optional ``--split`` / ``--config5``
+reports, outside any timed region) may import this package.  The GPU library
+(``paper_2305_02444_gb300``) shares no code with it and never imports it.
 
 The arithmetic lives in ``ftgemm_oracle.c`` (compiled with contraction off so
 every operation rounds once); this module only marshals numpy arrays.  Each

@@ -12,7 +12,9 @@
  * beta*C_in, compared against reference checksums summed from the computed
  * C_out, and an element found wrong is corrected.
  *
- * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (the
+ * cpu_baseline sample, the reference arm, and the sampled-row accuracy checks
+ * of its optional --split / --config5 reports, outside any timed region) may
  * load this library.  The GPU library shares no code with it.
  *
  * Build: gcc -O2 -fno-fast-math -ffp-contract=off -fopenmp -shared -fPIC.
