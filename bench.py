@@ -83,6 +83,18 @@ def reduce_max(x: float, ws: int, device) -> float:
     return float(t.item())
 
 
+def reduce_sum(x: float, ws: int, device) -> float:
+    """Sum of x over all ranks (the whole job's fault counts: a host-level
+    scalar reduction, not a data-path collective); identity on one rank."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_tflops(ws: int, flops_per_rank_step: float, steps: int, t_max: float) -> float:
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time (weak scaling: every rank runs its own replica)."""
@@ -745,14 +757,19 @@ def main():
     t_e2e = max_over_ranks((time.perf_counter() - te0) / args.e2e_steps)
     ftgemm.ftgemm_set_injection(mode=0)
 
+    # the whole job's fault counts: every rank's reports summed (all ranks
+    # take part before rank 0 alone reports)
+    det = [r["detected"] for r in reps]
+    cor = [r["corrected"] for r in reps]
+    job_counts = [int(round(reduce_sum(float(x), ws, "cuda")))
+                  for x in (det[-1] if det else 0, cor[-1] if cor else 0, sum(det), sum(cor))]
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
         return
 
     value = job_tflops(ws, flops, args.steps, t_inj)
-    det = [r["detected"] for r in reps]
-    cor = [r["corrected"] for r in reps]
     avg_main = main_ms / max(1, main_n) / 1e3
     achieved = flops / avg_main / 1e12
     line = {
@@ -771,10 +788,10 @@ def main():
         "checksum_pass": {"ms": ft_aux / max(1, ft_n), "bytes_read": 8 * (M * K + K * N),
                           "gbs": 8 * (M * K + K * N) / (max(1e-9, ft_aux / max(1, ft_n)) / 1e3) / 1e9,
                           "what": "operand checksum vectors (and the report reset) before each fault-free call"},
-        "errors": {"injected_per_step": FLIPS, "detected_per_step": det[-1] if det else None,
-                   "corrected_per_step": cor[-1] if cor else None,
-                   "detected_total": sum(det), "corrected_total": sum(cor),
-                   "per_minute": 60.0 * FLIPS / (t_inj / args.steps)},
+        "errors": {"injected_per_step": FLIPS * ws, "detected_per_step": job_counts[0] if det else None,
+                   "corrected_per_step": job_counts[1] if cor else None,
+                   "detected_total": job_counts[2], "corrected_total": job_counts[3],
+                   "per_minute": 60.0 * FLIPS * ws / (t_inj / args.steps)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": read_traffic("ftdgemm_nn_ft_inj_8192"),

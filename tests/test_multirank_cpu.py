@@ -36,7 +36,8 @@ def _rank_main(rank, world, port, q):
         local_t = 2.0 + rank          # rank 1 is the slower replica
         t_max = bench.reduce_max(local_t, ws, "cpu")
         v = bench.job_tflops(ws, 1.0e12, 4, t_max)
-        q.put((rank, ws, r, local, t_max, v))
+        faults = bench.reduce_sum(float(10 + rank), ws, "cpu")   # fault counts add over ranks
+        q.put((rank, ws, r, local, t_max, v, faults))
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -54,10 +55,11 @@ def test_two_rank_replicas_max_timing():
         p.join(timeout=120)
         assert p.exitcode == 0
     res = sorted(q.get(timeout=10) for _ in range(world))
-    for rank, ws, r, local, t_max, v in res:
+    for rank, ws, r, local, t_max, v, faults in res:
         assert ws == 2 and r == rank and local == rank
         assert t_max == 3.0                      # max over ranks
         assert v == pytest.approx(2 * 1.0e12 * 4 / 3.0 / 1e12)
+        assert faults == 21.0                    # 10 + 11, on every rank
 
 
 def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
