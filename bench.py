@@ -794,7 +794,7 @@ def main():
                    "per_minute": 60.0 * FLIPS * ws / (t_inj / args.steps)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": read_traffic("ftdgemm_nn_ft_inj_8192"),
+                     "traffic": read_traffic(f"ftdgemm_nn_ft_inj_{M}") if M == N == K else None,
                      "kernel": "ftdgemm_kernel<N,N,FT,INJ> (main FT-DGEMM kernel)",
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz",
                      "pre_kernel_ms_per_step": aux_ms / max(1, main_n)},

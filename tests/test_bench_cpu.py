@@ -104,3 +104,68 @@ def test_fp64_peak_from_unit_counts():
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
     peaks = bench.measured_peaks()
     assert peaks["source"] in ("measured", "fallback") and peaks["hbm_gbs"] > 0 and peaks["bf16_tflops"] > 0
+
+
+def test_main_assembles_the_line_with_fakes(monkeypatch, capsys):
+    """bench.main() end to end on the CPU with the device and the library
+    replaced by stand-ins: the JSON line carries every key of the contract,
+    the fault counts of all timed steps, and no traffic figure for a size the
+    DRAM capture was not taken at."""
+    import json
+    import torch
+    from paper_2305_02444_gb300 import build as b, ftgemm, inputs
+
+    class Stream:
+        cuda_stream = 0
+
+    class Event:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 100.0
+
+    real_matrix = inputs.matrix
+    monkeypatch.setattr(torch.cuda, "is_available", lambda: True)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: Stream())
+    monkeypatch.setattr(torch.cuda, "Event", Event)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(inputs, "matrix", lambda r, c, seed, dist="uniform", ld=None, device="cpu",
+                        fill_pad=float("nan"): real_matrix(r, c, seed, dist, ld, "cpu", fill_pad))
+    monkeypatch.setattr(b, "build", lambda *a, **k: None)
+    monkeypatch.setattr(ftgemm, "lib", lambda: object())
+    monkeypatch.setattr(ftgemm, "ftgemm_d", lambda *a, report=True, **k: (0, {"detected": 3, "corrected": 3}
+                                                                         if report else None))
+    monkeypatch.setattr(ftgemm, "ftgemm_d_noft", lambda *a, **k: 0)
+    monkeypatch.setattr(ftgemm, "ftgemm_d_unfused", lambda *a, **k: (0, None))
+    monkeypatch.setattr(ftgemm, "ftgemm_d_host", lambda *a, **k: (0, {"detected": 3, "corrected": 3}))
+    monkeypatch.setattr(ftgemm, "ftgemm_set_injection", lambda **k: 0)
+    count = iter(range(0, 10 ** 6, 6))
+    monkeypatch.setattr(ftgemm, "ftgemm_launch_count", lambda: next(count))
+    monkeypatch.setattr(ftgemm, "ftgemm_timing", lambda on: 0)
+    monkeypatch.setattr(ftgemm, "ftgemm_timing_read", lambda: (90.0, 4, 1.0))
+    monkeypatch.setattr(bench, "sample_clocks_start", lambda dev, path: (None, None))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--size", "256", "--steps", "4", "--warmup", "3",
+                                      "--no-cpu-baseline"])
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    try:
+        bench.main()
+    finally:
+        bench.set_size(8192)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches",
+                "clocks", "errors"):
+        assert key in line, key
+    assert line["n_gpus"] == 1 and line["steps"] == 4 and line["config"]["M"] == 256
+    assert line["errors"]["detected_per_step"] == 3 and line["errors"]["detected_total"] == 12
+    assert line["errors"]["injected_per_step"] == 1
+    assert line["roofline"]["traffic"] is None and line["roofline"]["bound"] == "alu"
+    assert line["e2e"]["h2d_bytes_per_step"] == 3 * 256 * 256 * 8
+    assert line["gpu_launches"] == 6
