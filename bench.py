@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -711,8 +712,7 @@ def main():
     ft_call()
 
     # 1) headline: FT path with injection, inputs resident in HBM
-    clk_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                            f"bench_clocks_r{rank}.csv")
+    clk_path = os.path.join(os.environ.get("FTGEMM_BENCH_DIR", tempfile.gettempdir()), f"bench_clocks_r{rank}.csv")
     proc, fh = sample_clocks_start(local, clk_path)
     ftgemm.ftgemm_set_injection(mode=1, seed=seed, count=FLIPS)
     l0 = ftgemm.ftgemm_launch_count()
