@@ -368,3 +368,18 @@ def test_split_shape_limit_before_the_device(ft):
     # K = 0: no slicing, the BLAS quick return applies at any size
     assert ft.ftgemm_d_split("N", "N", big, 4, 0, 1.0, 0, big, 0, 1, 1.0, 0, big, nslices=3, ft=0,
                              report=False, stream=0)[0] != ft.ERR_TOO_LARGE
+
+
+def test_header_is_plain_c_and_a_c_caller_links(ft, tmp_path):
+    """include/ftgemm.h compiles as C11 with warnings as errors (no C++ or
+    torch types at the boundary); a C program links against libftgemm.so and
+    runs the host-only paths without a GPU."""
+    src = os.path.join(ROOT, "tests", "abi", "c_caller.c")
+    exe = str(tmp_path / "c_caller")
+    libdir = os.path.dirname(ft.LIB_PATH)
+    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"), src,
+           "-o", exe, "-L", libdir, "-lftgemm", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
