@@ -3,6 +3,7 @@ host-only logic (argument codes, injection settings, error strings) works
 without a GPU.  No compute call is made here."""
 from __future__ import annotations
 
+import ctypes
 import os
 import re
 import subprocess
@@ -383,3 +384,22 @@ def test_header_is_plain_c_and_a_c_caller_links(ft, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_binding_structs_match_the_header_layout(ft, tmp_path):
+    """Every struct of include/ftgemm.h has the same size and field offsets
+    in C (compiled here) and in the binding's ctypes declarations."""
+    exe = str(tmp_path / "layout")
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "abi", "layout.c"), "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    c_layout = dict(line.rsplit(" ", 1) for line in subprocess.run([exe], capture_output=True, text=True,
+                                                                     check=True).stdout.splitlines())
+    pairs = {"ftgemm_loc": ft.Loc, "ftgemm_report": ft.Report, "ftgemm_flip": ft.Flip,
+             "ftgemm_inject": ft.Inject, "ftgemm_flip_log": ft.FlipLog}
+    for cname, cls in pairs.items():
+        assert int(c_layout[f"{cname} sizeof"]) == ctypes.sizeof(cls), cname
+        c_fields = [k.split(".", 1)[1] for k in c_layout if k.startswith(cname + ".")]
+        assert c_fields == [f for f, _ in cls._fields_], cname
+        for f, _ in cls._fields_:
+            assert int(c_layout[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
