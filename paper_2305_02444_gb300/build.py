@@ -58,7 +58,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
+    exports = os.path.join(CSRC, "exports.map")   # only the ftgemm_* entry points are exported
+    subprocess.run([nvcc()] + ARCH + ["-shared", "-Xlinker", "--version-script=" + exports, "-o", tmp] + objs,
+                   check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -41,11 +41,15 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol(ft):
+    """Exactly the functions the header declares: the internal launchers and
+    library templates stay local (linker version script)."""
     out = subprocess.run(["nm", "-D", "--defined-only", ft.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    exported = set(l.split()[-1].split("@")[0] for l in out.splitlines() if l.strip())
+    exported.discard("")
     for name in declared_functions():
         assert name in exported, name
         assert getattr(ft.lib(), name) is not None
+    assert exported == set(declared_functions()), sorted(exported ^ set(declared_functions()))
 
 
 def test_build_targets_sm103a_only():
