@@ -31,7 +31,8 @@ def _device_name() -> str:
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
     try:
-        return json.load(open(path))
+        with open(path) as f:
+            return json.load(f)
     except (OSError, ValueError):
         return {}
 
@@ -72,6 +73,7 @@ def tune_batched(shapes, reps: int = 5, seed: int = 1, cache_path: str = DEFAULT
     cache[sig] = {"schedule": best, "ms": {str(k): v for k, v in times.items()}, "n": len(shapes)}
     os.makedirs(os.path.dirname(cache_path), exist_ok=True)
     tmp = cache_path + f".tmp{os.getpid()}"
-    json.dump(cache, open(tmp, "w"), indent=1)
+    with open(tmp, "w") as f:   # closed (flushed) before it replaces the cache
+        json.dump(cache, f, indent=1)
     os.replace(tmp, cache_path)
     return best, times
