@@ -106,13 +106,16 @@ def sample_clocks_start(dev_index: int, path: str):
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    f = None
     try:
         f = open(path, "w")
         p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
                               "--format=csv,noheader,nounits", "-lms", "200"], stdout=f,
                              stderr=subprocess.DEVNULL)
         return p, f
-    except (OSError, FileNotFoundError):
+    except OSError:   # no writable folder, or no nvidia-smi: no clock record
+        if f is not None:
+            f.close()
         return None, None
 
 
@@ -127,7 +130,9 @@ def sample_clocks_stop(proc, f, path: str):
     f.close()
     sm, mx, reasons = [], None, set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in open(path):
+    with open(path) as fh:
+        lines = fh.read().splitlines()
+    for line in lines:
         parts = [x.strip() for x in line.split(",")]
         if len(parts) < 9:
             continue
@@ -153,8 +158,11 @@ def read_traffic(kernel_tag: str):
     if not os.path.exists(path):
         return None
     src = os.path.join(ROOT, "paper_2305_02444_gb300", "csrc", "ftgemm_kernel.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    for line in open(path):
+    with open(src, "rb") as fh:
+        h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    with open(path) as fh:
+        lines = fh.read().splitlines()
+    for line in lines:
         if line.startswith("#") or not line.strip():
             continue
         tag, src_hash, nbytes = line.split()[:3]

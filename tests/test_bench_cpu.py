@@ -169,3 +169,12 @@ def test_main_assembles_the_line_with_fakes(monkeypatch, capsys):
     assert line["roofline"]["traffic"] is None and line["roofline"]["bound"] == "alu"
     assert line["e2e"]["h2d_bytes_per_step"] == 3 * 256 * 256 * 8
     assert line["gpu_launches"] == 6
+
+
+def test_clock_sampler_absent_tool(tmp_path, monkeypatch):
+    """Without nvidia-smi the sampler reports no clock record (and leaves no
+    open file); the bench line then carries "clocks": null."""
+    monkeypatch.setenv("PATH", str(tmp_path))
+    proc, fh = bench.sample_clocks_start(0, str(tmp_path / "c.csv"))
+    assert proc is None and fh is None
+    assert bench.sample_clocks_stop(proc, fh, str(tmp_path / "c.csv")) is None
