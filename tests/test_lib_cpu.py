@@ -407,3 +407,24 @@ def test_binding_structs_match_the_header_layout(ft, tmp_path):
         assert c_fields == [f for f, _ in cls._fields_], cname
         for f, _ in cls._fields_:
             assert int(c_layout[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_gpu_probes_compile():
+    """The probe programs of the GPU tests include the kernel headers: they
+    must keep compiling for sm_103a as those headers change (compiled here,
+    run only on the GPU)."""
+    import tempfile
+    from paper_2305_02444_gb300 import build
+    pdir = os.path.join(ROOT, "tests", "probes")
+    with tempfile.TemporaryDirectory() as tmp:
+        procs = []
+        for f in sorted(os.listdir(pdir)):
+            if f.endswith(".cu"):
+                cmd = [build.nvcc()] + build.ARCH + ["-O3", "-std=c++17", "-I" + build.CSRC,
+                                                     "-I" + os.path.join(ROOT, "include"), "-c",
+                                                     os.path.join(pdir, f), "-o", os.path.join(tmp, f + ".o")]
+                procs.append((f, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        assert procs
+        for f, p in procs:
+            out, _ = p.communicate(timeout=600)
+            assert p.returncode == 0, (f, out.decode(errors="replace")[-2000:])
