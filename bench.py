@@ -217,7 +217,7 @@ def run_cpu_baseline(target_s: float = 15.0):
                       f"per-tile encode/verify/correct, {dt:.1f} s"}
 
 
-SPLIT_ENGINES = {"tc": 2, "mma": 1, "tcp": 5, "tcp2": 6}   # ftgemm_set_split_engine codes
+SPLIT_ENGINES = {"tc": 2, "mma": 1, "tcp": 5}   # ftgemm_set_split_engine codes
 METRIC = "FT-GEMM TFLOP/s (FP64) & % FP64 peak; ABFT overhead % vs plain; errors fixed"
 
 
@@ -429,7 +429,7 @@ def split(args):
     engines = [e for e in args.split_engine.split(",") if e]
     forms = [("fp64_dfma", None, 1, None)]
     for eng in engines:
-        sfx = {"tc": "", "mma": "_mma", "tcp": "_tcp", "tcp2": "_tcp2"}[eng]
+        sfx = {"tc": "", "mma": "_mma", "tcp": "_tcp"}[eng]
         forms += [(f"emulated_S{S}_fp64ck{sfx}", S, 2, eng) for S in args.split_slices]
         forms += [(f"bf16_plain{sfx}", 0, 0, eng)]
     forms += [(f"emulated_S{S}_fp32ck_mma", S, 1, "mma") for S in args.split_slices] + \
@@ -631,7 +631,7 @@ def main():
     ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
     ap.add_argument("--split-engine", default="tc,mma",
                     help="split engines: tc (tcgen05, one CTA per tile), tcp (persistent tcgen05), "
-                         "tcp2 (persistent tcgen05 on CTA pairs), mma (mma.sync)")
+                         "mma (mma.sync)")
     ap.add_argument("--split-forms", default="", help="comma list of form names to run (default: all)")
     ap.add_argument("--config5", action="store_true", help="32768^3 normal(0,1), beta 1, flips at a rate")
     ap.add_argument("--flip-rate", type=float, default=360.0, help="flips per minute for --config5")

@@ -357,17 +357,13 @@ int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits,
  * cores with the FP32 accumulators and the FP64 fold in tensor memory, when
  * ft is 0 or 2:
  *   2: one CTA per 128 x 128 tile;
- *   3 / 4: the same kernel in 1 x 2 / 2 x 2 thread-block clusters that
- *      share each A (and B) slab through TMA multicast;
  *   5: persistent, one CTA per SM walking its tiles, each tile finished
  *      from tensor memory while the next one's loads and MMAs run;
- *   6: engine 5 on pairs of CTAs (clusters of 2) whose MMAs run as one
- *      256 x 128 MMA (cta_group::2), each CTA staging half of the B slab;
- *      grids of one tile row run engine 5;
  *   0 (default): engine 5.
  * 1: every call on the mma.sync kernel.  ft = 1 (FP32 checksums summed from
  * the staged slices on the CUDA cores) always runs on the mma.sync kernel.
- * Process-global; returns -1 for another value. */
+ * Every CTA loads its own operand tiles (no thread-block clusters, no TMA
+ * multicast).  Process-global; returns -1 for another value. */
 int ftgemm_set_split_engine(int engine);
 
 /* Per-k-panel verification (FT-BLAS style; FT-GEMM blocks K by K_C, §2.1):

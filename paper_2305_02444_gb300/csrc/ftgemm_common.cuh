@@ -189,32 +189,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// try_wait with acquire at cluster scope: for barriers that threads of
-// another CTA of the cluster arrive on.
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for phase `parity` of an mbarrier (CLUSTER: acquire at
-// cluster scope).  Gives up after limit_ns nanoseconds of %globaltimer (or
-// 2^28 polls, whichever comes first), records ERR_TIMEOUT in the device
-// report and returns false; never traps.
-template <bool CLUSTER = false>
+// Bounded wait for phase `parity` of an mbarrier.  Gives up after limit_ns
+// nanoseconds of %globaltimer (or 2^28 polls, whichever comes first), records
+// ERR_TIMEOUT in the device report and returns false; never traps.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   unsigned long long limit_ns, int *err) {
-  auto try_wait = [&]() { return CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
-  if (try_wait()) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   unsigned long long t0 = globaltimer_ns();
   for (uint32_t it = 1; it < (1u << 28); ++it) {
-    if (try_wait()) return true;
+    if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) break;
   }
   atomicExch(err, ERR_TIMEOUT);

@@ -42,12 +42,10 @@ cudaError_t launch_panel_tt(bool, const CUtensorMap &, const CUtensorMap &, cons
                             cudaStream_t);
 cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s);
-cudaError_t launch_split_tc(bool ta, bool tb, int ck, int cluster, const CUtensorMap &a, const CUtensorMap &b,
-                            const CUtensorMap &b2, const SplitParams &p, cudaStream_t s);
+cudaError_t launch_split_tc(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
+                            const SplitParams &p, cudaStream_t s);
 cudaError_t launch_split_tcp(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                              const SplitParams &p, int nctas, cudaStream_t s);
-cudaError_t launch_split_tcp2(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &bh,
-                              const SplitParams &p, int max_pairs, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
                            int S, int w, int plain, void *out, unsigned long long *mb, int nsm, cudaStream_t s);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
@@ -228,11 +226,9 @@ bool tma_ok(const void *p, long long ld) {
 
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
-// split precision: 0 default (persistent tcgen05), 1 mma.sync, 2 / 3 / 4 tcgen05 in clusters of 1 / 2 / 4
-// CTAs, 5 persistent tcgen05, 6 persistent tcgen05 on CTA pairs (cta_group::2)
+// split precision: 0 default (persistent tcgen05), 1 mma.sync, 2 tcgen05 with one CTA per tile,
+// 5 persistent tcgen05
 int g_split_engine = 0;
-constexpr int SPLIT_DEFAULT_CLUSTER = 1;
-constexpr bool SPLIT_DEFAULT_PERSISTENT = true;
 int g_correct = 0;  // correction rule of the FP64 kernels (ftgemm_set_correction)
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
 int g_panel = 0;   // verify the accumulators every g_panel k-slabs (0: only at the end of the tile)
@@ -1003,7 +999,7 @@ int ftgemm_set_panel_check(int kslabs) {
 
 int ftgemm_set_split_engine(int engine) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (engine < 0 || engine > 6) return -1;
+  if (engine != 0 && engine != 1 && engine != 2 && engine != 5) return -1;
   g_split_engine = engine;
   return 0;
 }
@@ -1817,29 +1813,19 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
           cudaSuccess)
     return FTGEMM_ERR_CUDA;
   g_launches += plain ? 2 : 4;
-  // tcgen05 kernel (ft 0 / 2): 2 x 2 clusters load 64-row halves; otherwise whole 128-row slabs
+  // tcgen05 kernel (ft 0 / 2): persistent (at most one CTA per SM, the
+  // default) or one CTA per tile
   const bool tc = g_split_engine != 1 && ft != 1;
-  const int cl = !tc ? 1 : g_split_engine == 0 ? SPLIT_DEFAULT_CLUSTER : g_split_engine == 3 ? 2
-                 : g_split_engine == 4 ? 4 : 1;
-  const bool pairs = tc && g_split_engine == 6;
-  const bool persist = tc && (pairs || g_split_engine == 5 || (g_split_engine == 0 && SPLIT_DEFAULT_PERSISTENT));
-  // one tcgen05 launch: on CTA pairs (bh: B maps with 64-row boxes; grids of
-  // two or more tile rows), persistent (at most one CTA per SM) or one CTA
-  // per tile
-  auto run_tc = [&](bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &b2,
-                    const CUtensorMap &bh, const SplitParams &q, cudaStream_t st) {
-    if (pairs && q.nI >= 2) return launch_split_tcp2(ta, tb, ck, a, bh, q, nsm / 2, st);
+  const bool persist = tc && g_split_engine != 2;
+  auto run_tc = [&](bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b, const SplitParams &q,
+                    cudaStream_t st) {
     if (persist)
       return launch_split_tcp(ta, tb, ck, a, b, q, (int)std::min<long long>((long long)q.nI * q.nJ, nsm), st);
-    return launch_split_tc(ta, tb, ck, cl, a, b, b2, q, st);
+    return launch_split_tc(ta, tb, ck, a, b, q, st);
   };
-  const int boxA = cl == 1 ? SP_BM : SP_BM / 2, boxB = cl == 4 ? SP_BM / 2 : SP_BM;
-  CUtensorMap mA, mB, mB2, mBh;
-  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S, boxA)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S, boxB)))
+  CUtensorMap mA, mB;
+  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S, SP_BM)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S, SP_BN)))
     return rc;
-  mB2 = mB;
-  mBh = mB;
-  if (pairs && (rc = make_map_slices(&mBh, w.spB.p, Kp, N, S, SP_BN / 2))) return rc;
 
   SplitParams p;
   memset(&p, 0, sizeof(p));
@@ -1876,12 +1862,10 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
                          nsm, s) != cudaSuccess)
         return FTGEMM_ERR_CUDA;
       g_launches += 4;
-      CUtensorMap mPA, mPB, mPBh;
-      if ((rc = make_map_slices(&mPA, w.spPA.p, Kp, nI, S, boxA)) ||
-          (rc = make_map_slices(&mPB, w.spPB.p, Kp, nJ, S, boxB)))
+      CUtensorMap mPA, mPB;
+      if ((rc = make_map_slices(&mPA, w.spPA.p, Kp, nI, S, SP_BM)) ||
+          (rc = make_map_slices(&mPB, w.spPB.p, Kp, nJ, S, SP_BN)))
         return rc;
-      mPBh = mPB;
-      if (pairs && (rc = make_map_slices(&mPBh, w.spPB.p, Kp, nJ, S, SP_BN / 2))) return rc;
       SplitParams q1 = p, q2 = p;
       q1.M = nI; q1.nI = (int)((nI + SP_BM - 1) / SP_BM);
       q1.eA = (const int *)w.spEPA.p; q1.C = (double *)w.uP1.p; q1.ldc = ldp1;
@@ -1892,8 +1876,8 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
       if ((rc = ensure_side(w))) return rc;
       cudaEventRecord(w.fork_ev, s);
       cudaStreamWaitEvent(w.side, w.fork_ev, 0);
-      if (run_tc(false, false, 0, mPA, mB, mB, mBh, q1, s) != cudaSuccess ||
-          run_tc(false, false, 0, mA, mPB, mPB, mPBh, q2, w.side) != cudaSuccess)
+      if (run_tc(false, false, 0, mPA, mB, q1, s) != cudaSuccess ||
+          run_tc(false, false, 0, mA, mPB, q2, w.side) != cudaSuccess)
         return FTGEMM_ERR_CUDA;
       cudaEventRecord(w.join_ev, w.side);
       cudaStreamWaitEvent(s, w.join_ev, 0);
@@ -1918,8 +1902,8 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     p.flips = tmp.flips; p.tile_off = tmp.tile_off; p.inj = inj ? 1 : 0;
   }
   if (persist && ft == 2) {
-    // one tile per CTA of the grid (pairs: two per pair tile, a padding one included)
-    const long long ctas = std::min<long long>(pairs && nI >= 2 ? 2 * ((nI + 1) / 2) * nJ : nI * nJ, nsm);
+    // one tile per CTA of the grid
+    const long long ctas = std::min<long long>(nI * nJ, nsm);
     if (ensure(w.tscr, sizeof(double) * SP_BM * SP_BN * (size_t)ctas))
       return FTGEMM_ERR_NOMEM;
     p.tscratch = (double *)w.tscr.p;
@@ -1929,7 +1913,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  if ((tc ? run_tc(ta_t, tb_t, ft, mA, mB, mB2, mBh, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
+  if ((tc ? run_tc(ta_t, tb_t, ft, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
       cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);

@@ -63,23 +63,13 @@ __device__ __forceinline__ double scaled_exact_f32(uint32_t fb, int sh) {
   return tc_pack_f64((fb & 7u) << 29, hi);
 }
 
-// CL = 1: one CTA per tile, each loading its own slabs (tmA / tmB with
-// 128-row boxes).  CL = 2: 1 x 2 clusters (tiles (I, J0 + rank)); each CTA
-// loads one 64-row half of the shared A slab (tmA with 64-row boxes) and
-// multicasts it to both, and its whole B slab (tmB2, 128-row boxes): a
-// quarter fewer L2 reads; empty barriers count the two CTAs.  CL = 4: 2 x 2 clusters of tiles (I0 + a, J0 + b), rank
-// a + 2b; the A slab of a tile row is fetched once for the two CTAs that
-// share it (each loads one 64-row half and multicasts it to both), the B slab
-// likewise (tmA / tmB with 64-row boxes): half the L2 reads per CTA.  A ring
-// stage may then be refilled only when the CTA and the two partners writing
-// into it have consumed it: the MMA commits arrive at the empty barriers of
-// all three (count 3).
-template <bool TA, bool TB, int CK, int CL>
+// One CTA per tile, each loading its own slabs (tmA / tmB: slice maps with
+// 128-row boxes).
+template <bool TA, bool TB, int CK>
 __global__ void __launch_bounds__(256, 1)
     ftsplit_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ SplitParams p) {
+                      const __grid_constant__ SplitParams p) {
   static_assert(CK == 0 || CK == 2, "FP32 checksums are taken by the mma.sync kernel");
-  static_assert(CL == 1 || CL == 2 || CL == 4, "clusters of 1, 1 x 2 or 2 x 2 tiles");
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -96,29 +86,13 @@ __global__ void __launch_bounds__(256, 1)
   // by column, so that the CTAs resident at one time cover a compact block of
   // tiles and share the slices' slabs in L2
   int I, J;
-  uint32_t rank = 0;
-  if (CL == 1) {
+  {
     const int b = blockIdx.x, per = TC_GROUP * p.nJ, g = b / per, r = b % per;
     const int rows = min(TC_GROUP, p.nI - g * TC_GROUP);
     I = g * TC_GROUP + r % rows;
     J = r / rows;
-  } else if (CL == 2) {  // 1 x 2 blocks: the two tiles of a pair of columns share the A slab
-    rank = cluster_rank();
-    const int nCJ = (p.nJ + 1) / 2;
-    const int b = blockIdx.x / 2, per = TC_GROUP * nCJ, g = b / per, r = b % per;
-    const int rows = min(TC_GROUP, p.nI - g * TC_GROUP);
-    I = g * TC_GROUP + r % rows;
-    J = 2 * (r / rows) + (int)rank;
-  } else {  // the same order over 2 x 2 blocks of tiles (the grid is padded to even tile counts)
-    rank = cluster_rank();
-    const int nCI = (p.nI + 1) / 2, nCJ = (p.nJ + 1) / 2, G2 = max(1, TC_GROUP / 2);
-    const int b = blockIdx.x / 4, per = G2 * nCJ, g = b / per, r = b % per;
-    const int rows = min(G2, nCI - g * G2);
-    I = 2 * (g * G2 + r % rows) + (int)(rank & 1);
-    J = 2 * (r / rows) + (int)(rank >> 1);
   }
-  const bool valid = I < p.nI && J < p.nJ;  // padding tiles of a cluster only help load
-  const int tile = valid ? I + J * p.nI : 0;  // injection and location records number tiles column-major
+  const int tile = I + J * p.nI;  // injection and location records number tiles column-major
   const int i0 = I * SP_BM, j0 = J * SP_BN;
   int *err = &p.rep->err;
   const unsigned long long limit = p.wait_limit_ns;
@@ -127,7 +101,7 @@ __global__ void __launch_bounds__(256, 1)
     for (int c = 0; c < 8; ++c) cnt[c] = 0;
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, CL == 1 ? 1 : CL == 2 ? 2 : 3);
+      mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
@@ -137,15 +111,13 @@ __global__ void __launch_bounds__(256, 1)
     fence_mbar_init();
     prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
-    if (CL == 2) prefetch_tmap(&tmB2);
   }
   if (warp == 2) {
     tmem_alloc(smem_u32(s_tmem), TC_TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
-  if (CL > 1) cluster_sync();  // the partners' barriers exist before anything is multicast to them
-  else __syncthreads();
+  __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *s_tmem;
 
@@ -169,29 +141,6 @@ __global__ void __launch_bounds__(256, 1)
         if (*(volatile int *)&cnt[3]) break;
         const uint32_t sb = smem_u32(smem + st * SP_STAGE_BYTES), fb = full0 + 8 * st;
         mbar_arrive_expect_tx(fb, SP_STAGE_BYTES);
-        if (CL == 2) {
-          // my half of the A slab to both CTAs, my whole B slab to myself
-          tma_load_3d_mc(sb + (int)rank * (SP_A_BYTES / 2), &tmA, fb, slab * SP_BK, i0 + (int)rank * (SP_BM / 2),
-                         p.pair_s[pq], (uint16_t)3u);
-          asm volatile(
-              "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-              " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb + SP_A_BYTES),
-              "l"(reinterpret_cast<uint64_t>(&tmB2)), "r"(fb), "r"(slab * SP_BK), "r"(j0), "r"(p.pair_t[pq])
-              : "memory");
-          issued = step + 1;
-          continue;
-        }
-        if (CL == 4) {
-          // my half of the A slab to the CTAs of my tile row, my half of the
-          // B slab to those of my tile column
-          const int ha = (int)(rank >> 1), hb = (int)(rank & 1);
-          tma_load_3d_mc(sb + ha * (SP_A_BYTES / 2), &tmA, fb, slab * SP_BK, i0 + ha * (SP_BM / 2), p.pair_s[pq],
-                         (uint16_t)((1u << (rank & 1)) | (1u << ((rank & 1) + 2))));
-          tma_load_3d_mc(sb + SP_A_BYTES + hb * (SP_B_BYTES / 2), &tmB, fb, slab * SP_BK, j0 + hb * (SP_BN / 2),
-                         p.pair_t[pq], (uint16_t)(3u << (2 * (rank >> 1))));
-          issued = step + 1;
-          continue;
-        }
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb),
@@ -230,10 +179,7 @@ __global__ void __launch_bounds__(256, 1)
             for (int kk = 0; kk < SP_BK / 16; ++kk)
               tc_mma_bf16(dt, tc_desc_k128(a0 + 32 * kk), tc_desc_k128(b0 + 32 * kk), TC_IDESC,
                           (slab > s0 || kk > 0) ? 1u : 0u);
-            if (CL == 2) tc_commit_mc(empty0 + 8 * st, (uint16_t)3u);
-            else if (CL == 4)
-              tc_commit_mc(empty0 + 8 * st, (uint16_t)((1u << rank) | (1u << (rank ^ 1)) | (1u << (rank ^ 2))));
-            else tc_commit(empty0 + 8 * st);
+            tc_commit(empty0 + 8 * st);
             if (slab + 1 == s1) tc_commit(accf0 + 8 * b);
           }
           __syncwarp();
@@ -276,7 +222,7 @@ __global__ void __launch_bounds__(256, 1)
     const uint32_t trow = tbase + ((uint32_t)(fw * 32) << 16);
     const uint32_t t64 = trow + TC_ACC64_COL;
     int fptr = 0, fend = 0;
-    if (CK >= 1 && p.inj && valid) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+    if (CK >= 1 && p.inj) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
     int item = 0;
     const bool plain = p.S == 0;
     for (int pq = 0; pq < p.npairs && ok; ++pq) {
@@ -355,7 +301,6 @@ __global__ void __launch_bounds__(256, 1)
   tc_fence_after();
   if (cnt[3]) {
     if (warp == 2) tmem_dealloc(tbase, TC_TMEM_COLS);
-    if (CL > 1) cluster_sync();  // no CTA leaves while a partner may still write into it
     return;
   }
   // the ring is free: stage the FP64 accumulators as a column-major tile
@@ -378,9 +323,8 @@ __global__ void __launch_bounds__(256, 1)
     tc_fence_after();
     tmem_dealloc(tbase, TC_TMEM_COLS);
   }
-  if (valid) split_tile_finish<TA, TB, CK>(p, sC, reinterpret_cast<double *>(smem + SP_BM * SP_BN * 8), s_fr,
-                                            s_fc, cnt, tile, I, J);
-  if (CL > 1) cluster_sync();
+  split_tile_finish<TA, TB, CK>(p, sC, reinterpret_cast<double *>(smem + SP_BM * SP_BN * 8), s_fr, s_fc, cnt,
+                                tile, I, J);
 }
 
 }  // namespace ftg

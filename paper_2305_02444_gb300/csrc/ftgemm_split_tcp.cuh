@@ -86,15 +86,13 @@ __device__ __forceinline__ float colsum16_ru(float (&v)[16], int lane) {
 // lane): fold each pair (k-chunk) of the tile into the FP64 accumulators as
 // the MMAs finish it, inject, then finish the tile (see the file comment).
 // `item` is the running accumulator-item counter; acce0 is the address of
-// the accumulator-release barriers that `arrive` reaches (the CTA's own, or
-// the pair leader's).  A padding tile (valid false, the second tile of a pair
-// below the matrix) is folded but not finished.  Returns false when a wait
-// gave up; the four folder warps agree on it.
-template <bool TA, bool TB, int CK, typename Arrive>
-__device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int J, bool valid, int &item,
-                                                uint32_t tbase, uint32_t accf0, uint32_t acce0, Arrive arrive,
-                                                double *s_co, double *s_cc, float *s_ca, double *s_sig, int *s_fr,
-                                                int *s_fc, int *cnt, int nchunks, int fw, int lane) {
+// the accumulator-release barriers.  Returns false when a wait gave up; the
+// four folder warps agree on it.
+template <bool TA, bool TB, int CK>
+__device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int J, int &item, uint32_t tbase,
+                                                uint32_t accf0, uint32_t acce0, double *s_co, double *s_cc,
+                                                float *s_ca, double *s_sig, int *s_fr, int *s_fc, int *cnt,
+                                                int nchunks, int fw, int lane) {
   const int il = fw * 32 + lane;
   const uint32_t trow = tbase + ((uint32_t)(fw * 32) << 16);
   const uint32_t t64 = trow + TC_ACC64_COL;
@@ -107,7 +105,7 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
   const int i0 = I * SP_BM, j0 = J * SP_BN;
   const int mI = (int)min((long long)SP_BM, p.M - i0), nJt = (int)min((long long)SP_BN, p.N - j0);
   int fptr = 0, fend = 0;
-  if (CK >= 1 && p.inj && valid) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
+  if (CK >= 1 && p.inj) { fptr = p.tile_off[tile]; fend = p.tile_off[tile + 1]; }
   int blast = 0;
   for (int pq = 0; pq < p.npairs && ok; ++pq) {
     const int sh = p.w * (p.pair_s[pq] + p.pair_t[pq] + 2);  // the pair's weight is 2^-sh
@@ -141,10 +139,10 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) arrive(acce0 + 8 * b);
+      if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
     if (!ok) break;
-    if (CK >= 1 && p.inj && valid) {
+    if (CK >= 1 && p.inj) {
       // injection point: after pair pq has been folded in (kstep = pair index)
       while (fptr < fend) {
         DevFlip *f = p.flips + fptr;
@@ -170,14 +168,6 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
     }
   }
   if (!ok) return false;
-  if (!valid) {  // a padding tile of a pair: nothing to finish
-    if (direct) {
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) arrive(acce0 + 8 * blast);
-    }
-    return true;
-  }
 
   // ------------------------------------------------------------ end of the tile
   const bool rowok = il < mI;
@@ -216,7 +206,7 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
     if (direct) {
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) arrive(acce0 + 8 * blast);
+      if (lane == 0) mbar_arrive(acce0 + 8 * blast);
     }
     return true;
   }
@@ -486,9 +476,8 @@ __global__ void __launch_bounds__(256, 1)
     for (int n = blockIdx.x; n < ntiles && ok; n += gridDim.x) {
       int I, J;
       tile_coords(n, I, J);
-      ok = tcp_folder_tile<TA, TB, CK>(p, I, J, true, item, tbase, accf0, acce0,
-                                       [](uint32_t bar) { mbar_arrive(bar); }, s_co, s_cc, s_ca, s_sig, s_fr,
-                                       s_fc, cnt, nchunks, fw, lane);
+      ok = tcp_folder_tile<TA, TB, CK>(p, I, J, item, tbase, accf0, acce0, s_co, s_cc, s_ca, s_sig, s_fr, s_fc,
+                                       cnt, nchunks, fw, lane);
     }
     if (!ok && lane == 0) atomicExch(&cnt[3], 1);
   }
@@ -499,213 +488,6 @@ __global__ void __launch_bounds__(256, 1)
     tc_fence_after();
     tmem_dealloc(tbase, TC_TMEM_COLS);
   }
-}
-
-// ------------------------------------------------------------------ pair form
-// The persistent kernel on pairs of CTAs (clusters of 2) whose MMAs run as one
-// 256 x 128 MMA (cta_group::2).  CTA rank r of a pair owns tile (2P + r, J)
-// of pair tile (P, J) and stages its 128 rows of the A slab and rows
-// 64r .. 64r + 63 of the B slab, so that each SM receives 24 KiB per 64-k
-// slab instead of 32 KiB for the same MMA work.  The leader (rank 0) waits
-// and issues the MMAs; both CTAs' loads complete on the leader's full
-// barriers; the leader's commits arrive at the barriers of both CTAs; both
-// CTAs' folders release an accumulator at the leader's barrier (count 8).
-// Each CTA folds and finishes its own tile from its own tensor memory with
-// tcp_folder_tile.  A pair below the last tile row has a padding peer tile
-// (loaded as zeros by TMA, not finished).
-constexpr int TCP2_B_BYTES = (SP_BN / 2) * SP_BK * 2;        // 8 KiB: this CTA's half of the B slab
-constexpr int TCP2_STAGE_BYTES = SP_A_BYTES + TCP2_B_BYTES;  // 24 KiB
-#ifndef FTG_TCP2_STAGES
-#define FTG_TCP2_STAGES 8
-#endif
-constexpr int TCP2_STAGES = FTG_TCP2_STAGES;
-constexpr uint32_t TC_IDESC_PAIR = tc_idesc_bf16_f32(2 * SP_BM, SP_BN);
-constexpr int TCP2_SMEM_BYTES = TCP2_STAGES * TCP2_STAGE_BYTES + 2 * 4 * 128 * 8 + 4 * 128 * 4 + 8 * 8 +
-                                2 * 128 * 4 + 64 * 4 + (2 * TCP2_STAGES + 5) * 8 + 16 + 1024;
-static_assert(TCP2_SMEM_BYTES <= 232448, "shared memory per CTA");
-static_assert(TCP2_STAGE_BYTES % 1024 == 0 && SP_A_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
-
-template <bool TA, bool TB, int CK>
-__global__ void __launch_bounds__(256, 1)
-    ftsplit_tcp2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-                        const __grid_constant__ SplitParams p) {
-  static_assert(CK == 0 || CK == 2, "FP32 checksums are taken by the mma.sync kernel");
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *smem =
-      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  double *s_co = reinterpret_cast<double *>(smem + TCP2_STAGES * TCP2_STAGE_BYTES);
-  double *s_cc = s_co + 4 * 128;
-  float *s_ca = reinterpret_cast<float *>(s_cc + 4 * 128);
-  double *s_sig = reinterpret_cast<double *>(s_ca + 4 * 128);
-  int *s_fr = reinterpret_cast<int *>(s_sig + 8);
-  int *s_fc = s_fr + 128;
-  int *cnt = s_fc + 128;  // [0] nr [1] nc [2] det [3] abort [4] unverifiable
-  uint64_t *bars = reinterpret_cast<uint64_t *>(cnt + 64);
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 2 * TCP2_STAGES + 5);
-  const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * TCP2_STAGES;
-  const uint32_t accf0 = empty0 + 8 * TCP2_STAGES, acce0 = accf0 + 16, done_bar = acce0 + 16;
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t rank = cluster_rank();
-  const bool leader = rank == 0;
-  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-  const int nPI = (p.nI + 1) / 2, npt = nPI * p.nJ;
-  // pair tile n of the grouped rasterization (TC_GROUP tile rows per group)
-  auto pair_coords = [&](int n, int &P, int &J) {
-    const int G2 = max(1, TC_GROUP / 2);
-    const int per = G2 * p.nJ, g = n / per, r = n % per;
-    const int rows = min(G2, nPI - g * G2);
-    P = g * G2 + r % rows;
-    J = r / rows;
-  };
-  int *err = &p.rep->err;
-  const unsigned long long limit = p.wait_limit_ns;
-
-  if (tid == 0) {
-    for (int c = 0; c < 8; ++c) cnt[c] = 0;
-    for (int s = 0; s < TCP2_STAGES; ++s) {
-      mbar_init(full0 + 8 * s, 1);   // the leader's expect_tx; both CTAs' bytes
-      mbar_init(empty0 + 8 * s, 1);  // the leader's commit
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 8);  // four folder warps in each CTA (used in the leader)
-    }
-    mbar_init(done_bar, 1);
-    fence_mbar_init();
-    prefetch_tmap(&tmA);
-    prefetch_tmap(&tmBh);
-  }
-  if (warp == 2) {
-    tmem_alloc_pair(smem_u32(s_tmem), TC_TMEM_COLS);
-    tmem_relinquish_pair();
-  }
-  tc_fence_before();
-  cluster_sync();  // both CTAs' barriers exist before either signals the other's
-  tc_fence_after();
-  const uint32_t tbase = *s_tmem;
-  const uint32_t full_lead0 = mapa_shared(full0, 0), acce_lead0 = mapa_shared(acce0, 0);
-
-  const int nslab = (int)(p.Kp / SP_BK);
-  const int chunk_slabs = max(1, p.kchunk / SP_BK);
-  const int nchunks = (nslab + chunk_slabs - 1) / chunk_slabs;
-  const int nsteps = p.npairs * nslab;  // per pair tile
-
-  if (warp == 0) {
-    // ---------------------------------------------------------------- producer (both CTAs)
-    if (lane == 0) {
-      bool ok = true;
-      int step = 0;
-      for (int n = cid; n < npt && ok; n += ncl) {
-        int P, J;
-        pair_coords(n, P, J);
-        const int i0 = (2 * P + (int)rank) * SP_BM, jb = J * SP_BN + (int)rank * (SP_BN / 2);
-        for (int s = 0; s < nsteps; ++s, ++step) {
-          const int pq = s / nslab, slab = s % nslab, st = step % TCP2_STAGES;
-          if (step >= TCP2_STAGES &&
-              !mbar_wait_bounded(empty0 + 8 * st, ((step / TCP2_STAGES) - 1) & 1, limit, err)) {
-            ok = false;
-            break;
-          }
-          if (*(volatile int *)&cnt[3]) { ok = false; break; }
-          const uint32_t sb = smem_u32(smem + st * TCP2_STAGE_BYTES), fb = full_lead0 + 8 * st;
-          if (leader) mbar_arrive_expect_tx(full0 + 8 * st, 2 * TCP2_STAGE_BYTES);
-          tma_load_3d_pair(sb, &tmA, fb, slab * SP_BK, i0, p.pair_s[pq]);
-          tma_load_3d_pair(sb + SP_A_BYTES, &tmBh, fb, slab * SP_BK, jb, p.pair_t[pq]);
-        }
-      }
-      if (!ok) atomicExch(&cnt[3], 1);
-      // the leader's full barriers count both CTAs' loads: the last ones in
-      // flight land before the pair may leave (bounded)
-      if (leader)
-        for (int n = step > TCP2_STAGES ? step - TCP2_STAGES : 0; n < step; ++n)
-          mbar_wait_bounded(full0 + 8 * (n % TCP2_STAGES), (n / TCP2_STAGES) & 1, limit, err);
-    }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA issuer (leader)
-    bool stop = false;
-    if (leader) {
-      int step = 0, item = 0;
-      for (int n = cid; n < npt && !stop; n += ncl) {
-        for (int pq = 0; pq < p.npairs && !stop; ++pq) {
-          for (int c = 0; c < nchunks && !stop; ++c, ++item) {
-            const int b = item & 1;
-            const uint32_t dt = tbase + (uint32_t)(b * SP_BN);
-            const int s0 = c * chunk_slabs, s1 = min(nslab, s0 + chunk_slabs);
-            for (int slab = s0; slab < s1; ++slab, ++step) {
-              if (bar_red_or(TC_HANDOFF_BAR, 64, false)) { stop = true; break; }
-              tc_fence_after();
-              const int st = step % TCP2_STAGES;
-              if (elect_one()) {
-                const uint32_t a0 = smem_u32(smem + st * TCP2_STAGE_BYTES), b0 = a0 + SP_A_BYTES;
-#pragma unroll
-                for (int kk = 0; kk < SP_BK / 16; ++kk)
-                  tc_mma_bf16_pair(dt, tc_desc_k128(a0 + 32 * kk), tc_desc_k128(b0 + 32 * kk), TC_IDESC_PAIR,
-                                   (slab > s0 || kk > 0) ? 1u : 0u);
-                tc_commit_pair_mc(empty0 + 8 * st, (uint16_t)3u);
-                if (slab + 1 == s1) tc_commit_pair_mc(accf0 + 8 * b, (uint16_t)3u);
-              }
-              __syncwarp();
-            }
-          }
-        }
-      }
-      // every MMA issued above has completed (in both CTAs) before the
-      // tensor memory is freed
-      if (elect_one()) tc_commit_pair_mc(done_bar, (uint16_t)3u);
-      __syncwarp();
-    }
-    if (lane == 0) {
-      if (stop) atomicExch(&cnt[3], 1);
-      mbar_wait_bounded(done_bar, 0, limit, err);
-    }
-  } else if (warp == 3) {
-    // ---------------------------------------------------------------- waiter (leader)
-    if (leader) {
-      int step = 0, item = 0;
-      bool bad = false;
-      for (int n = cid; n < npt && !bad; n += ncl) {
-        for (int pq = 0; pq < p.npairs && !bad; ++pq) {
-          for (int c = 0; c < nchunks && !bad; ++c, ++item) {
-            const int b = item & 1;
-            const int s0 = c * chunk_slabs, s1 = min(nslab, s0 + chunk_slabs);
-            for (int slab = s0; slab < s1; ++slab, ++step) {
-              int fail = 0;
-              if (lane == 0) {
-                if (slab == s0 && item >= 2 &&
-                    !mbar_wait_bounded<true>(acce0 + 8 * b, ((item >> 1) - 1) & 1, limit, err))
-                  fail = 1;
-                const int st = step % TCP2_STAGES;
-                if (!fail && !mbar_wait_bounded(full0 + 8 * st, (step / TCP2_STAGES) & 1, limit, err)) fail = 1;
-              }
-              fail = __shfl_sync(0xffffffffu, fail, 0);
-              if (bar_red_or(TC_HANDOFF_BAR, 64, fail != 0)) { bad = true; break; }
-            }
-          }
-        }
-      }
-    }
-  } else if (warp >= 4) {
-    // ---------------------------------------------------------------- folders (both CTAs)
-    const int fw = warp - 4;
-    int item = 0;
-    bool ok = true;
-    for (int n = cid; n < npt && ok; n += ncl) {
-      int P, J;
-      pair_coords(n, P, J);
-      const int I = 2 * P + (int)rank;
-      ok = tcp_folder_tile<TA, TB, CK>(p, I, J, I < p.nI, item, tbase, accf0, acce_lead0,
-                                       [](uint32_t bar) { mbar_arrive_cluster(bar); }, s_co, s_cc, s_ca, s_sig,
-                                       s_fr, s_fc, cnt, nchunks, fw, lane);
-    }
-    if (!ok && lane == 0) atomicExch(&cnt[3], 1);
-  }
-
-  tc_fence_before();
-  __syncthreads();
-  cluster_sync();  // neither CTA frees its tensor memory or leaves while the pair may still use it
-  tc_fence_after();
-  if (warp == 2) tmem_dealloc_pair(tbase, TC_TMEM_COLS);
 }
 
 }  // namespace ftg

@@ -301,9 +301,8 @@ def ftgemm_set_correction(mode: int) -> int:
 
 
 def ftgemm_set_split_engine(engine: int) -> int:
-    """Split precision: 0 default (= 5), 1 mma.sync, 2 tcgen05 one CTA per tile, 3 / 4 tcgen05 in
-    1x2 / 2x2 clusters, 5 persistent tcgen05, 6 persistent tcgen05 on CTA pairs (cta_group::2)
-    (ft=1 always runs on mma.sync)."""
+    """Split precision: 0 default (= 5), 1 mma.sync, 2 tcgen05 one CTA per tile, 5 persistent
+    tcgen05 (ft=1 always runs on mma.sync); other values return -1."""
     return lib().ftgemm_set_split_engine(engine)
 
 

@@ -88,10 +88,10 @@ def test_host_settings_and_strings(ft):
 
 
 def test_split_engine_knob_codes(ft):
-    assert ft.ftgemm_set_split_engine(7) == -1
-    for e in (6, 5, 4, 3, 2):
+    for e in (7, 6, 4, 3, -1):   # 3, 4 and 6 (cluster forms) no longer exist
+        assert ft.ftgemm_set_split_engine(e) == -1
+    for e in (5, 2):
         assert ft.ftgemm_set_split_engine(e) == 0
-    assert ft.ftgemm_set_split_engine(-1) == -1
     assert ft.ftgemm_set_split_engine(1) == 0
     assert ft.ftgemm_set_split_engine(0) == 0
 
