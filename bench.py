@@ -217,6 +217,61 @@ def run_cpu_baseline(target_s: float = 15.0):
                       f"per-tile encode/verify/correct, {dt:.1f} s"}
 
 
+def _flip_bit(x: float, bit: int) -> float:
+    import struct
+    u = struct.unpack("<Q", struct.pack("<d", x))[0] ^ (1 << bit)
+    return struct.unpack("<d", struct.pack("<Q", u))[0]
+
+
+def flip_accounting(log, rep, A, B, Cin, out_at, tm: int = 128, tn: int = 128):
+    """Classify the injected faults of one call by the oracle (CPU leg, after
+    the timed regions): each fault's effect alpha * (flipped - true partial
+    sum) against the oracle's row and column thresholds of its tile.  Above:
+    more than 4x the larger threshold (must be detected, located and
+    corrected); below: under a quarter of the smaller one (no checksum scheme
+    sees it); the band between may go either way.  out_at(i, j) returns the
+    call's output element, checked against the oracle's value within the
+    parity bound for every located fault.  A, B, Cin: (M, K), (K, N), (M, N)
+    numpy views of the call's inputs."""
+    import oracle
+    Mx, Kx = A.shape
+    Nx = B.shape[1]
+    enc = oracle.encode_operands("N", "N", Mx, Nx, Kx, A, B, tm, tn)
+    above, band, below = [], [], []
+    for L in log:
+        i, j, s, bit, kf = L["row"], L["col"], L["kstep"], L["bit"], L["kfirst"]
+        kend = min(Kx, 16 * (s + 1))
+        part = oracle.partial("N", "N", i, j, kend, A, B) if kf == 0 else \
+            float(A[i, kf:kend] @ B[kf:kend, j])
+        d = _flip_bit(part, bit) - part
+        eff = abs(ALPHA * d) if math.isfinite(d) else math.inf
+        I, J = i // tm, j // tn
+        cols = slice(J * tn, min(Nx, (J + 1) * tn))
+        rows = slice(I * tm, min(Mx, (I + 1) * tm))
+        tr = oracle.tau(Kx, cols.stop - cols.start, ALPHA, enc.arowabs[i], enc.babsmax[J], BETA,
+                        float(abs(Cin[i, cols]).sum()))
+        tc = oracle.tau(Kx, rows.stop - rows.start, ALPHA, enc.bcolabs[j], enc.aabsmax[I], BETA,
+                        float(abs(Cin[rows, j]).sum()))
+        (above if eff > 4 * max(tr, tc) else below if eff < 0.25 * min(tr, tc) else band).append((i, j))
+    located = {(l[0], l[1]) for l in rep["locs"]}
+    det_above = sum(1 for x in set(above) if x in located)
+    det_band = sum(1 for x in set(band) if x in located)
+    within = True
+    for (i, j) in located:
+        r, E = oracle.gemm("N", "N", ALPHA, A[i:i + 1], B[:, j:j + 1], BETA, Cin[i:i + 1, j:j + 1], want_E=True)
+        within = within and abs(out_at(i, j) - r[0, 0]) <= oracle.parity_tol(Kx, E)[0, 0]
+    return {"checked_call": {"injected": len(log), "above_threshold": len(above), "in_guard_band": len(band),
+                             "below_threshold": len(below), "detected": rep["detected"],
+                             "corrected": rep["corrected"], "detected_above": det_above,
+                             "detected_in_band": det_band,
+                             "detected_elsewhere": rep["detected"] - det_above - det_band,
+                             "every_above_threshold_fault_fixed": det_above == len(set(above)) and
+                             rep["corrected"] == rep["detected"] and within,
+                             "located_within_parity_bound": within,
+                             "rule": "above: alpha*|flip effect| > 4 max(tau_row, tau_col) of the oracle; "
+                                     "below: < min/4; corrected elements checked against the oracle"}}
+
+
 SPLIT_ENGINES = {"tc": 2, "mma": 1, "tcp": 5}   # ftgemm_set_split_engine codes
 METRIC = "FT-GEMM TFLOP/s (FP64) & % FP64 peak; ABFT overhead % vs plain; errors fixed"
 
@@ -750,7 +805,8 @@ def main():
 
     # 3) end to end through the host-buffer entry point (pinned host memory)
     hA, hB = A.cpu().pin_memory(), B.cpu().pin_memory()
-    hC = C0.cpu().pin_memory()
+    hC0 = C0.cpu()
+    hC = hC0.pin_memory()
     ftgemm.ftgemm_set_injection(mode=1, seed=seed, count=FLIPS)
     rc, _ = ftgemm.ftgemm_d_host("N", "N", M, N, K, ALPHA, hA, M, hB, K, BETA, hC, M, loc_cap=0)
     barrier()
@@ -814,6 +870,18 @@ def main():
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline()
+        # the fault accounting of one call, classified by the oracle on the CPU
+        C.copy_(C0)
+        ftgemm.ftgemm_set_injection(mode=1, seed=seed, count=FLIPS)
+        try:
+            rc, rep = ftgemm.ftgemm_d("N", "N", M, N, K, ALPHA, A, M, B, K, BETA, C, M, loc_cap=4 * FLIPS + 64)
+            log = ftgemm.ftgemm_injection_log()
+        finally:
+            ftgemm.ftgemm_set_injection(mode=0)
+        torch.cuda.synchronize()
+        if rc == 0:
+            line["errors"].update(flip_accounting(log, rep, hA.T.numpy(), hB.T.numpy(), hC0.T.numpy(),
+                                                  lambda i, j: float(C[j, i])))
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

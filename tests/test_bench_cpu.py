@@ -178,3 +178,33 @@ def test_clock_sampler_absent_tool(tmp_path, monkeypatch):
     proc, fh = bench.sample_clocks_start(0, str(tmp_path / "c.csv"))
     assert proc is None and fh is None
     assert bench.sample_clocks_stop(proc, fh, str(tmp_path / "c.csv")) is None
+
+
+def test_flip_accounting_against_the_oracles_own_call():
+    """The bench's fault accounting of one call, fed with the oracle's own
+    FT-DGEMM (256 x 256 x 512, the bench's alpha and beta, 40 seeded faults
+    over every bit range): the classification counts add up, every fault
+    above the threshold band is found among the located elements, and each
+    located element is checked against the oracle's value.  A planted wrong
+    output element makes the check fail."""
+    import numpy as np
+    oracle = pytest.importorskip("oracle")
+    from paper_2305_02444_gb300 import inputs
+    M_, N_, K_ = 256, 256, 512
+    A = inputs.matrix(M_, K_, 5).T.numpy()
+    B = inputs.matrix(K_, N_, 6).T.numpy()
+    C = inputs.matrix(M_, N_, 7).T.numpy()
+    flips = oracle.random_flips(99, 40, M_, N_, K_ // 16)
+    r = oracle.ft_gemm("N", "N", bench.ALPHA, A, B, bench.BETA, C, flips=flips)
+    log = [{"row": int(i), "col": int(j), "kstep": int(s), "bit": int(b), "kfirst": 0} for i, j, s, b in flips]
+    rep = {"detected": r.counts["detected"], "corrected": r.counts["corrected"], "locs": r.locs}
+    acc = bench.flip_accounting(log, rep, A, B, C, lambda i, j: float(r.C[i, j]))["checked_call"]
+    assert acc["injected"] == 40
+    assert acc["above_threshold"] + acc["in_guard_band"] + acc["below_threshold"] == 40
+    assert acc["above_threshold"] >= 10 and acc["below_threshold"] >= 5      # bits 0..62 span both sides
+    assert acc["detected_above"] == acc["above_threshold"] and acc["detected_elsewhere"] == 0
+    assert acc["every_above_threshold_fault_fixed"] and acc["located_within_parity_bound"]
+    i, j = r.locs[0][:2]
+    bad = bench.flip_accounting(log, rep, A, B, C, lambda a, b: float(r.C[a, b]) + (1.0 if (a, b) == (i, j) else 0))
+    assert not bad["checked_call"]["located_within_parity_bound"]
+    assert not bad["checked_call"]["every_above_threshold_fault_fixed"]

@@ -255,6 +255,26 @@ def test_splitmix64_golden(orc):
         assert orc.splitmix64(int(seed), int(n)) == int(hx, 16)
 
 
+def _golden_splitmix64():
+    here = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+    rows = [l.split() for l in open(here) if l.strip() and not l.startswith("#")]
+    return {(int(seed), int(n)): int(hx, 16) for seed, n, hx in rows}
+
+
+def test_random_flips_field_mapping_from_golden_outputs(orc):
+    """Fault f takes generator outputs 4f, 4f+1, 4f+2, 4f+3 as (row mod M,
+    col mod N, k-step mod nks, bit mod 63): checked against the published
+    outputs themselves (not the oracle's generator), for fault 0 of two
+    seeds and the row of fault 1 (output 4) -- a mistake in the stride, the
+    field order or a modulus fails here."""
+    g = _golden_splitmix64()
+    for seed in (0, 1234567):
+        M, N, nks = 1000003, 999983, 517       # primes: no modulus hides another
+        f = orc.random_flips(seed, 2, M, N, nks)
+        assert tuple(f[0]) == (g[(seed, 0)] % M, g[(seed, 1)] % N, g[(seed, 2)] % nks, g[(seed, 3)] % 63)
+        assert f[1][0] == g[(seed, 4)] % M
+
+
 def test_random_flips_ranges_and_determinism(orc):
     f1 = orc.random_flips(1234, 500, 100, 37, 9)
     f2 = orc.random_flips(1234, 500, 100, 37, 9)
