@@ -73,6 +73,8 @@ extern "C" {
 #define FTGEMM_ERR_BATCH 10     /* batched calls: count < 0, or a NULL plan pointer or
                                    per-problem array (count > 0) */
 #define FTGEMM_ERR_TOO_LARGE 11 /* ftgemm_d_split: M or N above FTGEMM_SPLIT_MAX_ROWS */
+#define FTGEMM_ERR_CAPTURE 12   /* ftgemm_d_noalloc: a report was requested (rep != NULL) on a
+                                   stream that is being captured; nothing was enqueued */
 
 /* Largest M and N of ftgemm_d_split (the slicing passes run one block per 8
  * operand rows along the 65535-block y dimension of their grids). */
@@ -196,6 +198,13 @@ int ftgemm_d_noft(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
  *    most 1024 location records per call.
  *  - The first call on each device looks up the array's device address with
  *    that device current; make that first call before any stream capture.
+ *    The address is kept for the life of the process: a cudaDeviceReset
+ *    between calls is not supported (the kept address would be stale).
+ *  - With rep != NULL the call waits for its stream to read the report back;
+ *    on a stream that is being captured it returns FTGEMM_ERR_CAPTURE before
+ *    enqueueing anything.  With rep == NULL it does not wait, so it cannot
+ *    return FTGEMM_ERR_TIMEOUT either: a pipeline wait that expired on the
+ *    device shows only in a report.
  *  - Every call shares the one array and it keeps the last call's contents;
  *    the call clears what must start at zero.  Calls that overlap on the GPU
  *    (different streams, threads or processes' graphs) race on it.

@@ -1086,6 +1086,7 @@ const char *ftgemm_strerror(int code) {
     case FTGEMM_ERR_UNALIGNED: return "operand not 16-byte aligned or leading dimension odd";
     case FTGEMM_ERR_BATCH: return "invalid batch: count < 0, or a NULL plan pointer or per-problem array";
     case FTGEMM_ERR_TOO_LARGE: return "ftgemm_d_split: M or N above FTGEMM_SPLIT_MAX_ROWS";
+    case FTGEMM_ERR_CAPTURE: return "ftgemm_d_noalloc: a report cannot be read back inside a stream capture";
     default: return "unknown error";
   }
 }
@@ -1206,6 +1207,16 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
   const NoallocLayout L = noalloc_layout(ta_t, tb_t, M, N, K, nsm);
   if (L.total > (size_t)FTGEMM_NOALLOC_SCRATCH_BYTES) return FTGEMM_ERR_SCRATCH;
   if (!tma_ok(A, lda) || !tma_ok(B, ldb) || !tma_ok(C, ldc)) return FTGEMM_ERR_UNALIGNED;
+  if (rep) {
+    // reading the report back waits for the stream, which a stream capture
+    // does not allow: refuse before anything is enqueued
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return FTGEMM_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return FTGEMM_ERR_CAPTURE;
+  }
 
   if (!g_noalloc_ptr[dev]) {
     void *ptr = nullptr;

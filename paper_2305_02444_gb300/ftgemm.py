@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libftgemm.so")
 BM = BN = 128
 KSTEP = 16
 ERR_CUDA, ERR_TIMEOUT, ERR_NODEVICE, ERR_NOMEM, ERR_INJECT, ERR_TENSORMAP = 1, 2, 4, 5, 6, 7
-ERR_SCRATCH, ERR_UNALIGNED, ERR_BATCH, ERR_TOO_LARGE = 8, 9, 10, 11
+ERR_SCRATCH, ERR_UNALIGNED, ERR_BATCH, ERR_TOO_LARGE, ERR_CAPTURE = 8, 9, 10, 11, 12
 SPLIT_MAX_ROWS = 524280
 
 _i64 = ctypes.c_int64

@@ -74,3 +74,24 @@ def test_noalloc_rejects_what_it_cannot_hold(ft):
     A = torch.zeros(8 * 9, dtype=torch.float64, device="cuda")
     rc, _ = ft.ftgemm_d_noalloc("N", "N", 9, 8, 8, 1.0, A, 9, A, 8, 0.0, A, 9)  # odd lda
     assert rc == ft.ERR_UNALIGNED
+
+
+def test_noalloc_refuses_a_report_inside_a_stream_capture(ft):
+    """A report is read back by waiting for the stream, which a stream
+    capture does not allow: the call returns ERR_CAPTURE and enqueues
+    nothing (the captured graph stays empty)."""
+    import warnings
+    n = 128
+    A = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    C = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    rc, _ = ft.ftgemm_d_noalloc("N", "N", n, n, n, 1.0, A, n, A, n, 0.0, C, n)   # set-up outside the capture
+    assert rc == 0
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")      # the graph is empty by design
+        with torch.cuda.graph(g, stream=side):
+            rc, _ = ft.ftgemm_d_noalloc("N", "N", n, n, n, 1.0, A, n, A, n, 0.0, C, n, stream=side)
+    assert rc == ft.ERR_CAPTURE
+    assert "capture" in ft.ftgemm_strerror(rc)
