@@ -259,14 +259,15 @@ def flip_accounting(log, rep, A, B, Cin, out_at, tm: int = 128, tn: int = 128):
     within = True
     for (i, j) in located:
         r, E = oracle.gemm("N", "N", ALPHA, A[i:i + 1], B[:, j:j + 1], BETA, Cin[i:i + 1, j:j + 1], want_E=True)
-        within = within and abs(out_at(i, j) - r[0, 0]) <= oracle.parity_tol(Kx, E)[0, 0]
+        within = within and bool(abs(out_at(i, j) - r[0, 0]) <= oracle.parity_tol(Kx, E)[0, 0])
     return {"checked_call": {"injected": len(log), "above_threshold": len(above), "in_guard_band": len(band),
                              "below_threshold": len(below), "detected": rep["detected"],
                              "corrected": rep["corrected"], "detected_above": det_above,
                              "detected_in_band": det_band,
                              "detected_elsewhere": rep["detected"] - det_above - det_band,
-                             "every_above_threshold_fault_fixed": det_above == len(set(above)) and
-                             rep["corrected"] == rep["detected"] and within,
+                             "every_above_threshold_fault_fixed": bool(det_above == len(set(above)) and
+                                                                       rep["corrected"] == rep["detected"] and
+                                                                       within),
                              "located_within_parity_bound": within,
                              "rule": "above: alpha*|flip effect| > 4 max(tau_row, tau_col) of the oracle; "
                                      "below: < min/4; corrected elements checked against the oracle"}}

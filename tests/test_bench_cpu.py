@@ -198,7 +198,10 @@ def test_flip_accounting_against_the_oracles_own_call():
     r = oracle.ft_gemm("N", "N", bench.ALPHA, A, B, bench.BETA, C, flips=flips)
     log = [{"row": int(i), "col": int(j), "kstep": int(s), "bit": int(b), "kfirst": 0} for i, j, s, b in flips]
     rep = {"detected": r.counts["detected"], "corrected": r.counts["corrected"], "locs": r.locs}
-    acc = bench.flip_accounting(log, rep, A, B, C, lambda i, j: float(r.C[i, j]))["checked_call"]
+    out = bench.flip_accounting(log, rep, A, B, C, lambda i, j: float(r.C[i, j]))
+    import json
+    json.dumps(out)                                   # goes into the bench's JSON line as it is
+    acc = out["checked_call"]
     assert acc["injected"] == 40
     assert acc["above_threshold"] + acc["in_guard_band"] + acc["below_threshold"] == 40
     assert acc["above_threshold"] >= 10 and acc["below_threshold"] >= 5      # bits 0..62 span both sides
