@@ -162,3 +162,82 @@ def bf16_gemm(ta: str, tb: str, alpha: float, A, B, beta: float, C, want_E: bool
     alpha bf16(op(A)) bf16(op(B)) + beta C, with its bound matrix E."""
     from . import gemm
     return gemm(ta, tb, alpha, bf16_round(A), bf16_round(B), beta, C, want_E=want_E)
+
+
+# ---------------------------------------------------------------------------
+# Fault tolerance of the plain BF16 form (checksums carried in FP32).
+#
+# The plain form sums exact products of bf16 values (8-bit significands, so
+# every product is exact in FP32) in an FP32 accumulator.  How a tensor core
+# adds within one instruction is not documented, so the bound below assumes
+# only that the accumulation proceeds in blocks of n >= 2 inputs (the running
+# sum and n - 1 or more products), each block aligned to its largest input
+# with at least 24 bits kept, summed, and rounded or truncated once to FP32.
+# One block then errs by at most (n + 2) 2^-23 times the sum of its inputs'
+# magnitudes, and K products in blocks of n by at most
+#     (K / n) (n + 2) 2^-23 sum_k |a_k b_k|  <=  2 K 2^-23 sum_k |a_k b_k|;
+# plain recursive FP32 summation (n = 2, rounding to nearest) is within it.
+# With 16 more products of slack for ragged blocks:
+#     e32(K) = (K + 16) 2^-22.
+#
+# Checksums of one 128 x 128 tile (I, J), column j (rows symmetric):
+#   reference  sum_{i in I} out_ij, out_ij = fl64(alpha v_ij + beta c_ij),
+#              v_ij the FP32 accumulator;
+#   predicted  alpha P1_Ij + beta sum_i c_ij, P1_Ij = sum_k acs_I[k] b_kj with
+#              acs_I[k] = fl32(sum_{i in I} a_ik) split into two bf16 pieces
+#              (hi = bf16(acs), lo = bf16(acs - hi); |acs - hi - lo| <=
+#              2^-16 |acs|), each piece's product accumulated in FP32 and
+#              the two results added in FP64.
+# With H >= sum_k sum_{i in I} |a_ik||b_kj| (the Hoelder bound
+# max_k sum_{i in I} |a_ik| * sum_k |b_kj|) and L the rows of the tile:
+#   |ref - alpha X| <= |alpha| e32 H                       (X the exact sums)
+#   |P1 - X|        <= (1.02 e32 + 1.01 (L - 1) 2^-24 + 1.01 2^-16) H
+# plus the FP64 roundings of the L-term sums and the epilogue, and an
+# absolute term for FP32 results below the normal range.  A fault whose
+# effect on the column sum exceeds tau_plain is seen by the check.
+# ---------------------------------------------------------------------------
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+
+
+def bf16_acc_bound(K: int) -> float:
+    """e32(K): |fl32-accumulated sum of K exact products - exact sum| <=
+    e32(K) * sum of the products' magnitudes, under the block model above."""
+    return (K + 16) * 2.0 ** -22
+
+
+def bf16_tau(K: int, L: int, alpha: float, gmax: float, vsum: float, beta: float, abscsum: float) -> float:
+    """Detection threshold of one row or column checksum of a plain-BF16 tile.
+    K: contraction length; L: the tile's rows (column check) or columns (row
+    check); gmax: max_k of the tile group's absolute sums of the summed
+    operand (max_k sum_{i in I} |a_ik| for a column check); vsum: the other
+    operand's absolute sum along k for this column or row (sum_k |b_kj|), so
+    that H = gmax * vsum bounds the absolute checksum; abscsum: sum of |C_in|
+    over the same row/column segment.  The last terms cover FP32 results
+    below the normal range: flushed products and checksum pieces that lose
+    bits there (at most 2^-134 per piece entry, times |b_kj|)."""
+    e32 = bf16_acc_bound(K)
+    H = gmax * vsum
+    fp32 = abs(alpha) * H * (2.04 * e32 + 1.01 * (L + 1) * U32 + 1.01 * 2.0 ** -16)
+    fp64 = 2.01 * (L + 40) * U64 * (abs(alpha) * H * (1.0 + e32) + abs(beta) * abscsum)
+    tiny = abs(alpha) * ((L + 2) * (K + 16) * 2.0 ** -124 + vsum * 2.0 ** -130) + (L + 40) * 2.0 ** -1021
+    return fp32 + fp64 + tiny
+
+
+def bf16_elem_tol(K: int, alpha: float, ab: float, beta: float, c: float) -> float:
+    """Largest difference between the plain form's output element
+    fl64(alpha v + beta c) and its FP64 recomputation from the bf16 operands
+    fl64(alpha fl64(sum_k a_k b_k) + beta c), ab = sum_k |a_k b_k|."""
+    e32 = bf16_acc_bound(K)
+    return (abs(alpha) * ab * 1.01 * e32 + 2.01 * (K + 4) * U64 * (abs(alpha) * ab + abs(beta * c))
+            + abs(alpha) * (K + 16) * 2.0 ** -124)
+
+
+def bf16_pieces(x) -> tuple[np.ndarray, np.ndarray]:
+    """The two bf16 pieces of FP32 values x: hi = bf16(x), lo = bf16(x - hi)
+    (x - hi is exact in FP32)."""
+    x = np.asarray(x, dtype=np.float32).astype(np.float64)
+    hi = bf16_round(x)
+    lo = bf16_round((x - hi).astype(np.float32).astype(np.float64))
+    return hi, lo

@@ -302,3 +302,192 @@ def test_split_layouts_agree(orc, ta, tb):
     B = opB if tb == "N" else opB.T.copy()
     np.testing.assert_array_equal(orc.split_gemm(ta, tb, 1.25, A, B, -0.5, C, 4),
                                   orc.split_gemm("N", "N", 1.25, opA, opB, -0.5, C, 4))
+
+
+# ---------------------------------------------------------------------------
+# Fault tolerance of the plain BF16 form: the FP32 accumulation bound, the
+# two-piece split of the checksum vectors and the detection threshold,
+# pinned against models of an FP32 accumulator written here from their
+# definitions (Python integers and fractions, or numpy float32 adds).
+
+def _fp32_round_nearest(x: Fraction) -> Fraction:
+    """x rounded to the nearest FP32 value (ties to even), normal range."""
+    if x == 0:
+        return Fraction(0)
+    s = -1 if x < 0 else 1
+    a = abs(x)
+    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    q = Fraction(2) ** (e - 23)                   # the spacing of 24-bit significands at a
+    n = a / q
+    f = math.floor(n)
+    r = n - f
+    f = f + 1 if (r > Fraction(1, 2) or (r == Fraction(1, 2) and f % 2 == 1)) else f
+    return s * f * q
+
+
+def _exp_of(a: Fraction) -> int:
+    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    return e
+
+
+def _trunc_block_sum(vals, n: int) -> Fraction:
+    """A truncating fused accumulator: the running sum and the next n - 1
+    products are aligned to the largest of them, each truncated toward zero
+    to 24 bits below that largest exponent, summed exactly, and the block's
+    result truncated toward zero to 24 significant bits."""
+    acc = Fraction(0)
+    vals = [Fraction(v) for v in vals]
+    for b0 in range(0, len(vals), n - 1):
+        block = [acc] + vals[b0:b0 + n - 1]
+        m = max(abs(v) for v in block)
+        if m == 0:
+            continue
+        q = Fraction(2) ** (_exp_of(m) - 23)
+        s = sum((abs(v) // q) * q * (1 if v >= 0 else -1) for v in block)
+        if s == 0:
+            acc = Fraction(0)
+            continue
+        qs = Fraction(2) ** (_exp_of(abs(s)) - 23)
+        acc = (abs(s) // qs) * qs * (1 if s >= 0 else -1)
+    return acc
+
+
+def _bf16_products(rng, K, kind):
+    from oracle import split
+    if kind == "positive":
+        a, b = rng.random(K) + 0.5, rng.random(K) + 0.5
+    elif kind == "loguniform":
+        a = rng.choice([-1.0, 1.0], K) * 10.0 ** rng.uniform(-3, 3, K)
+        b = rng.choice([-1.0, 1.0], K) * 10.0 ** rng.uniform(-3, 3, K)
+    elif kind == "one_large":        # 1 first, then products just below one FP32 ulp of 1 (2^-23)
+        a = np.full(K, 1.9921875); b = np.full(K, 2.0 ** -24)
+        a[0], b[0] = 1.0, 1.0
+    else:
+        a, b = rng.uniform(-1, 1, K), rng.uniform(-1, 1, K)
+    a, b = split.bf16_round(a), split.bf16_round(b)
+    return a * b                                  # exact: two 8-bit significands
+
+
+@pytest.mark.parametrize("kind", ["uniform", "positive", "loguniform", "one_large"])
+@pytest.mark.parametrize("K", [16, 100, 1024])
+def test_bf16_accumulation_bound_holds_for_fp32_accumulators(orc, kind, K):
+    """e32(K) bounds the error of sequential round-to-nearest FP32 sums and
+    of truncating fused blocks of 2, 4, 16 and 17 inputs; on the adversarial
+    'one large product first' input the truncating accumulator reaches a
+    fair share of the bound, so the bound is not loose by orders of
+    magnitude."""
+    from oracle import split
+    rng = np.random.default_rng(K + len(kind))
+    p = _bf16_products(rng, K, kind)
+    exact = sum(Fraction(float(x)) for x in p)
+    mag = float(np.abs(p).sum())
+    e32 = split.bf16_acc_bound(K)
+    seq = np.float32(0)
+    for x in p.astype(np.float32):
+        seq = np.float32(seq + x)
+    worst = abs(float(Fraction(float(seq)) - exact)) / mag
+    for n in (2, 4, 16, 17):
+        worst = max(worst, abs(float(_trunc_block_sum(p, n) - exact)) / mag)
+    assert worst <= e32, (worst, e32)
+    if kind == "one_large" and K >= 100:
+        assert worst >= 0.2 * e32, (worst, e32)
+
+
+def test_bf16_pieces_remainder(orc):
+    """FP32 = hi + lo + r with hi = bf16(x), lo = bf16(x - hi): |r| <= 2^-16
+    |x| over random FP32 bit patterns of normal magnitude, with cases near
+    the bound; hi + lo recovers every FP32 value with at most 16 significant
+    bits exactly."""
+    from oracle import split
+    rng = np.random.default_rng(3)
+    bits = rng.integers(0x0C000000, 0x72000000, 200000).astype(np.uint32)   # 2^-103 .. 2^101
+    x = bits.view(np.float32).astype(np.float64) * rng.choice([-1.0, 1.0], 200000)
+    hi, lo = split.bf16_pieces(x)
+    r = np.abs(x - hi - lo)
+    assert np.all(r <= 2.0 ** -16 * np.abs(x))
+    assert r.max() / np.abs(x)[np.argmax(r / np.abs(x))] > 2.0 ** -18          # the bound is nearly reached
+    short = (rng.integers(1 << 15, 1 << 16, 1000) * 2.0 ** rng.integers(-40, 40, 1000))
+    hi, lo = split.bf16_pieces(short)
+    np.testing.assert_array_equal(hi + lo, short)
+
+
+def _simulate_plain_tile(rng, K, L, alpha, beta, kind, acc):
+    """The plain form's column check of one L x L tile with the accumulator
+    model `acc` (a function of a vector of exact products): returns the
+    residuals |ref_j - pred_j| and the thresholds tau_j (bf16_tau)."""
+    from oracle import split
+    if kind == "loguniform":
+        A = rng.choice([-1.0, 1.0], (L, K)) * 10.0 ** rng.uniform(-3, 3, (L, K))
+        B = rng.choice([-1.0, 1.0], (K, L)) * 10.0 ** rng.uniform(-3, 3, (K, L))
+    elif kind == "positive":
+        A, B = rng.random((L, K)) + 0.5, rng.random((K, L)) + 0.5
+    else:
+        A, B = rng.uniform(-1, 1, (L, K)), rng.uniform(-1, 1, (K, L))
+    C = rng.uniform(-1, 1, (L, L))
+    a, b = split.bf16_round(A), split.bf16_round(B)
+    V = np.array([[acc(a[i] * b[:, j]) for j in range(L)] for i in range(L)])   # FP32 accumulators
+    out = alpha * V + beta * C                                                   # the epilogue, FP64
+    ref = out.sum(axis=0)
+    acs = np.zeros(K, dtype=np.float32)
+    for i in range(L):                                                           # FP32 group sums
+        acs = (acs + a[i].astype(np.float32)).astype(np.float32)
+    hi, lo = split.bf16_pieces(acs)
+    P1 = np.array([acc(hi * b[:, j]) + acc(lo * b[:, j]) for j in range(L)])
+    pred = alpha * P1 + beta * C.sum(axis=0)
+    gmax = np.abs(a).sum(axis=0).max()
+    tau = np.array([split.bf16_tau(K, L, alpha, gmax, np.abs(b[:, j]).sum(), beta, np.abs(C[:, j]).sum())
+                    for j in range(L)])
+    return np.abs(ref - pred), tau
+
+
+def _acc_seq32(p):
+    s = np.float32(0)
+    for x in np.asarray(p, dtype=np.float32):
+        s = np.float32(s + x)
+    return float(s)
+
+
+def _acc_trunc16(p):
+    return float(_trunc_block_sum(p, 17))
+
+
+@pytest.mark.parametrize("kind", ["uniform", "positive", "loguniform"])
+@pytest.mark.parametrize("acc", [_acc_seq32, _acc_trunc16])
+def test_bf16_tau_sound_under_fp32_accumulators(orc, kind, acc):
+    """No fault-free column check of the simulated plain form exceeds its
+    threshold, for round-to-nearest and truncating accumulators, uniform,
+    all-positive and six-decade log-uniform operands; the residual uses a
+    visible share of the threshold on all-positive data under truncation
+    (where both sides' errors pile up) but stays below it."""
+    rng = np.random.default_rng(11)
+    K, L = (96, 12) if acc is _acc_trunc16 else (300, 16)
+    res, tau = _simulate_plain_tile(rng, K, L, 1.5, -0.5, kind, acc)
+    assert np.all(res <= tau), (res / tau).max()
+    assert np.all(tau > 0)
+
+
+def test_bf16_elem_tol_sound(orc):
+    """The element bound covers the difference between the FP32-accumulated
+    output and its FP64 recomputation from the bf16 operands, under both
+    accumulator models, and a change of twice the bound exceeds it."""
+    from oracle import split
+    rng = np.random.default_rng(5)
+    for kind in ("uniform", "positive", "loguniform", "one_large"):
+        for K in (16, 200):
+            p = _bf16_products(rng, K, kind)
+            ab = float(np.abs(p).sum())
+            c = float(rng.uniform(-1, 1))
+            recomputed = math.fma(1.5, math.fsum(p), -0.5 * c) if hasattr(math, "fma") else 1.5 * math.fsum(p) - 0.5 * c
+            tol = split.bf16_elem_tol(K, 1.5, ab, -0.5, c)
+            for acc in (_acc_seq32, _acc_trunc16):
+                out = 1.5 * acc(p) + -0.5 * c
+                assert abs(out - recomputed) <= tol, (kind, K)
+            assert tol < 2.0 ** -20 * 1.5 * ab * K + 1e-300 or kind == "loguniform"
