@@ -487,7 +487,8 @@ def split(args):
     for eng in engines:
         sfx = {"tc": "", "mma": "_mma", "tcp": "_tcp"}[eng]
         forms += [(f"emulated_S{S}_fp64ck{sfx}", S, 2, eng) for S in args.split_slices]
-        forms += [(f"bf16_plain{sfx}", 0, 0, eng)]
+        if eng != "mma":    # the plain form with FP32-carried checksums on the tcgen05 engines
+            forms += [(f"bf16_plain_fp32ck{sfx}", 0, 1, eng)]
     forms += [(f"emulated_S{S}_fp32ck_mma", S, 1, "mma") for S in args.split_slices] + \
         [("bf16_plain_fp32ck_mma", 0, 1, "mma")]
     if args.split_forms:
@@ -537,10 +538,8 @@ def split(args):
                      "flips": nflip, "detected": rep["detected"], "rc": rc,
                      "slices": S, "pairs": npairs if S else (1 if S == 0 else None),
                      "checksums": "fp64" if (S is None or ck == 2) else ("fp32" if ck == 1 else "none"),
-                     "engine": "dfma" if S is None else ("mma.sync" if (eng == "mma" or ck == 1)
-                                                         else "tcgen05" if eng == "tc" else
-                                                         "tcgen05_persistent" if eng == "tcp" else
-                                                         "tcgen05_persistent_pairs"),
+                     "engine": "dfma" if S is None else ("mma.sync" if (eng == "mma" or (ck == 1 and S != 0))
+                                                         else "tcgen05" if eng == "tc" else "tcgen05_persistent"),
                      "unprotected_kernel_ms": kms}
         if S is not None:
             # tensor work of the unprotected kernel: every kept pair is a 2MNK bf16 product

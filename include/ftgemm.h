@@ -284,15 +284,25 @@ int ftgemm_batched_plan_destroy(ftgemm_batched_plan plan);
  *    into FP64 with their power-of-two weights.  S = 11 (w = 5) keeps about
  *    55 bits of every row's largest element; entries far smaller than their
  *    row's (column's) largest keep fewer bits.
- * ft = 1: predicted checksums in FP32 from the staged slices, reference sums,
- * verification and correction (FP64 recomputation from the original operands)
- * in FP64; ft = 2 (emulated forms only): FP64 predicted checksums from the
- * original operands (operand checksum pass + two skinny FP64 GEMMs before the
- * kernel), verified against the scaled result with the FP64 threshold plus
- * the splitting bound -- far more sensitive than FP32 checksums; ft = 0
- * compiles the checks out (overhead baseline).  Injection
+ * ft = 1: checksums carried in FP32, reference sums, verification and
+ * correction in FP64.  Emulated forms (mma.sync kernel): predicted checksums
+ * summed in FP32 from the staged slices, flagged elements recomputed from the
+ * original FP64 operands.  Plain form: on the tcgen05 engines the predicted
+ * checksums are tensor-core products of the FP32 checksum vectors of the bf16
+ * operands (each split into two bf16 pieces), on the mma.sync engine they are
+ * summed from the staged slices; flagged elements are recomputed in FP64
+ * from the same bf16 operands (the form's own value without its FP32
+ * accumulation error), and an element counts as detected when it differs from
+ * that by more than the FP32 accumulation bound (K + 16) 2^-22 sum_k |a~||b~|.
+ * ft = 2 (emulated forms only): FP64 predicted checksums from the original
+ * operands (operand checksum pass + two skinny products before the kernel),
+ * verified against the scaled result with the FP64 threshold plus the
+ * splitting bound -- far more sensitive than FP32 checksums; ft = 0 compiles
+ * the checks out (overhead baseline).  Injection
  * (ftgemm_set_injection) flips bits of the FP64 accumulator after the slice
- * pair numbered `kstep` has been folded in (kstep < number of pairs).
+ * pair numbered `kstep` has been folded in (kstep < number of pairs; the
+ * plain form has one pair, and the flip applies to the FP64 value of its FP32
+ * accumulator).
  * Returns -14 for an invalid nslices, -15 for an invalid ft (0, 1 or 2;
  * ft = 2 needs nslices >= 1), FTGEMM_ERR_TOO_LARGE when M or N exceeds
  * FTGEMM_SPLIT_MAX_ROWS (before any device work), FTGEMM_ERR_UNALIGNED when
@@ -369,8 +379,9 @@ int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits,
  *   5: persistent, one CTA per SM walking its tiles, each tile finished
  *      from tensor memory while the next one's loads and MMAs run;
  *   0 (default): engine 5.
- * 1: every call on the mma.sync kernel.  ft = 1 (FP32 checksums summed from
- * the staged slices on the CUDA cores) always runs on the mma.sync kernel.
+ * 1: every call on the mma.sync kernel.  The emulated forms with ft = 1 (FP32
+ * checksums summed from the staged slices on the CUDA cores) always run on
+ * the mma.sync kernel; the plain form with ft = 1 runs on the engine chosen.
  * Every CTA loads its own operand tiles (no thread-block clusters, no TMA
  * multicast).  Process-global; returns -1 for another value. */
 int ftgemm_set_split_engine(int engine);

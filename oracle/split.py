@@ -183,7 +183,8 @@ def bf16_gemm(ta: str, tb: str, alpha: float, A, B, beta: float, C, want_E: bool
 # Checksums of one 128 x 128 tile (I, J), column j (rows symmetric):
 #   reference  sum_{i in I} out_ij, out_ij = fl64(alpha v_ij + beta c_ij),
 #              v_ij the FP32 accumulator;
-#   predicted  alpha P1_Ij + beta sum_i c_ij, P1_Ij = sum_k acs_I[k] b_kj with
+#   predicted  alpha P1_Ij + beta cs_j, cs_j = fl32(sum_i fl32(c_ij)) (within
+#              (L + 1) 2^-24 sum_i |c_ij|), P1_Ij = sum_k acs_I[k] b_kj with
 #              acs_I[k] = fl32(sum_{i in I} a_ik) split into two bf16 pieces
 #              (hi = bf16(acs), lo = bf16(acs - hi); |acs - hi - lo| <=
 #              2^-16 |acs|), each piece's product accumulated in FP32 and
@@ -219,7 +220,8 @@ def bf16_tau(K: int, L: int, alpha: float, gmax: float, vsum: float, beta: float
     bits there (at most 2^-134 per piece entry, times |b_kj|)."""
     e32 = bf16_acc_bound(K)
     H = gmax * vsum
-    fp32 = abs(alpha) * H * (2.04 * e32 + 1.01 * (L + 1) * U32 + 1.01 * 2.0 ** -16)
+    fp32 = (abs(alpha) * H * (2.04 * e32 + 1.01 * (L + 1) * U32 + 1.01 * 2.0 ** -16)
+            + abs(beta) * abscsum * 1.01 * (L + 1) * U32)
     fp64 = 2.01 * (L + 40) * U64 * (abs(alpha) * H * (1.0 + e32) + abs(beta) * abscsum)
     tiny = abs(alpha) * ((L + 2) * (K + 16) * 2.0 ** -124 + vsum * 2.0 ** -130) + (L + 40) * 2.0 ** -1021
     return fp32 + fp64 + tiny

@@ -130,6 +130,14 @@ struct SplitParams {
   // persistent kernel: one 128 x 128 FP64 tile per CTA, where the flagged
   // elements of a tile are recomputed before the tile is copied to C
   double *tscratch;
+  // plain BF16 form (S == 0) with checks: the bf16 operands the product used
+  // (rows of op(A) and columns of op(B), k contiguous, rows of ldk entries),
+  // from which flagged elements are recomputed; and the predicted checksums
+  // as sums of two pieces, the second at element offset p1_lo of P1 and
+  // p2_lo of P2 (0: a single value)
+  const uint16_t *Ab, *Bb;
+  long long ldk;
+  long long p1_lo, p2_lo;
 };
 
 
@@ -305,6 +313,23 @@ __device__ __forceinline__ float f32_ru_abs(double x) {
     return __uint_as_float(v);
   }
   return __double2float_ru(fabs(x));
+}
+
+// x rounded to FP32, to nearest with ties to even (the result of
+// __double2float_rn): the fields are rounded with integer operations when the
+// result is a normal FP32 number or overflows, the conversion handles zeros,
+// subnormal results, Inf and NaN.  Keeps the C-side checksum sums of the
+// plain BF16 form off the FP64 pipe.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF), ef = E - 1023 + 127;
+  if (E != 0x7FF && ef >= 1 && ef <= 254) {
+    const unsigned long long rest = b & ((1ull << 29) - 1ull), half = 1ull << 28;
+    uint32_t v = ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
+    v += (rest > half || (rest == half && (v & 1u))) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
+    return __uint_as_float(((uint32_t)(b >> 32) & 0x80000000u) | v);
+  }
+  return __double2float_rn(x);
 }
 
 __device__ __forceinline__ double flip_bit(double x, int bit) {

@@ -48,6 +48,9 @@ cudaError_t launch_split_tcp(bool ta, bool tb, int ck, const CUtensorMap &a, con
                              const SplitParams &p, int nctas, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
                            int S, int w, int plain, void *out, unsigned long long *mb, int nsm, cudaStream_t s);
+long long bf16_checksum_scratch(long long R, long long Kp);
+cudaError_t launch_bf16_checksums(const void *X, long long R, long long Kp, void *pieces, double *rowabs,
+                                  double *gmax, float *part, cudaStream_t s);
 // any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
 cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
                            const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
@@ -1798,7 +1801,17 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   }
   // ft 2: the operand checksum pass (FP64 adds) runs on the second stream
   // while the slicing passes (integer and memory work) run on s
-  const long long Kq = (K + BK - 1) / BK * BK, ldp1 = (nI + 1) & ~1LL, ldp2 = (M + 1) & ~1LL;
+  // tcgen05 kernels (ft 0 / 2, and the plain form with ft 1) or the mma.sync
+  // kernel; ck: the kernels' check mode (2: verification against the
+  // checksum products P1 / P2 computed before the product)
+  const bool tc = g_split_engine != 1 && (ft != 1 || plain);
+  const int ck = tc ? (ft ? 2 : 0) : ft;
+  // the plain form on tcgen05 with checks: P1 / P2 are plain BF16 products of
+  // the two bf16 pieces of the checksum vectors (P1 with 2 nI rows, P2 with
+  // 2 nJ columns), computed from the bf16 operands
+  const bool plain_ck = plain && ft == 1 && tc;
+  const long long Kq = (K + BK - 1) / BK * BK, ldp1 = ((plain_ck ? 2 * nI : nI) + 1) & ~1LL,
+                  ldp2 = (M + 1) & ~1LL;
   if (ft == 2) {
     if (ensure(w.acs, sizeof(double) * nI * Kq) || ensure(w.bcs, sizeof(double) * nJ * Kq) ||
         ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
@@ -1826,7 +1839,6 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   g_launches += plain ? 2 : 4;
   // tcgen05 kernel (ft 0 / 2): persistent (at most one CTA per SM, the
   // default) or one CTA per tile
-  const bool tc = g_split_engine != 1 && ft != 1;
   const bool persist = tc && g_split_engine != 2;
   auto run_tc = [&](bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b, const SplitParams &q,
                     cudaStream_t st) {
@@ -1853,6 +1865,55 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   p.rep = (DevReport *)w.rep.p; p.loc = (DevLoc *)w.loc.p; p.loc_cap = LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
   p.verify = ft;
+  if (plain && ft) {  // flagged elements are recomputed from the bf16 operands
+    p.Ab = (const uint16_t *)w.spA.p;
+    p.Bb = (const uint16_t *)w.spB.p;
+    p.ldk = Kp;
+  }
+  if (plain_ck) {
+    // the checksum vectors of the bf16 operands (op(A)'s on s, op(B)'s on the
+    // second stream), then P1 = pieces(acs) op(B) on s and P2 = op(A)
+    // pieces(bcs) on the second stream, as plain products
+    const long long sa = bf16_checksum_scratch(M, Kp), sb = bf16_checksum_scratch(N, Kp);
+    if (ensure(w.spPA, (size_t)2 * nI * Kp * 2) || ensure(w.spPB, (size_t)2 * nJ * Kp * 2) ||
+        ensure(w.spEPA, sizeof(int) * 2 * nI) || ensure(w.spEPB, sizeof(int) * 2 * nJ) ||
+        ensure(w.arowabs, sizeof(double) * M) || ensure(w.aabsmax, sizeof(double) * nI) ||
+        ensure(w.bcolabs, sizeof(double) * N) || ensure(w.babsmax, sizeof(double) * nJ) ||
+        ensure(w.uP1, sizeof(double) * ldp1 * N) || ensure(w.uP2, sizeof(double) * ldp2 * 2 * nJ) ||
+        ensure(w.part_abs, sizeof(float) * sa) || ensure(w.part_abs2, sizeof(float) * sb))
+      return FTGEMM_ERR_NOMEM;
+    if ((rc = ensure_side(w))) return rc;
+    cudaMemsetAsync(w.spEPA.p, 0, sizeof(int) * 2 * nI, s);
+    cudaMemsetAsync(w.spEPB.p, 0, sizeof(int) * 2 * nJ, s);
+    cudaEventRecord(w.fork_ev, s);
+    cudaStreamWaitEvent(w.side, w.fork_ev, 0);
+    if (launch_bf16_checksums(w.spA.p, M, Kp, w.spPA.p, (double *)w.arowabs.p, (double *)w.aabsmax.p,
+                              (float *)w.part_abs.p, s) != cudaSuccess ||
+        launch_bf16_checksums(w.spB.p, N, Kp, w.spPB.p, (double *)w.bcolabs.p, (double *)w.babsmax.p,
+                              (float *)w.part_abs2.p, w.side) != cudaSuccess)
+      return FTGEMM_ERR_CUDA;
+    g_launches += 4;
+    CUtensorMap mPA, mPB;
+    if ((rc = make_map_slices(&mPA, w.spPA.p, Kp, 2 * nI, 1, SP_BM)) ||
+        (rc = make_map_slices(&mPB, w.spPB.p, Kp, 2 * nJ, 1, SP_BN)))
+      return rc;
+    SplitParams q1 = p, q2 = p;
+    q1.M = 2 * nI; q1.nI = (int)((2 * nI + SP_BM - 1) / SP_BM);
+    q1.eA = (const int *)w.spEPA.p; q1.C = (double *)w.uP1.p; q1.ldc = ldp1;
+    q2.N = 2 * nJ; q2.nJ = (int)((2 * nJ + SP_BN - 1) / SP_BN);
+    q2.eB = (const int *)w.spEPB.p; q2.C = (double *)w.uP2.p; q2.ldc = ldp2;
+    for (SplitParams *q : {&q1, &q2}) { q->alpha = 1.0; q->beta = 0.0; q->verify = 0; q->inj = 0; }
+    if (run_tc(false, false, 0, mPA, mB, q1, s) != cudaSuccess ||
+        run_tc(false, false, 0, mA, mPB, q2, w.side) != cudaSuccess)
+      return FTGEMM_ERR_CUDA;
+    cudaEventRecord(w.join_ev, w.side);
+    cudaStreamWaitEvent(s, w.join_ev, 0);
+    g_launches += 2;
+    p.P1 = (const double *)w.uP1.p; p.ldp1 = ldp1; p.p1_lo = nI;
+    p.P2 = (const double *)w.uP2.p; p.ldp2 = ldp2; p.p2_lo = nJ * ldp2;
+    p.arowabs = (const double *)w.arowabs.p; p.aabsmax = (const double *)w.aabsmax.p;
+    p.bcolabs = (const double *)w.bcolabs.p; p.babsmax = (const double *)w.babsmax.p;
+  }
   cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   if (ft == 2) {
     // FP64 predicted checksums of the 128 x 128 tiles from the original
@@ -1912,7 +1973,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     if ((rc = upload_injection(M, N, np, nI, nI * nJ, w, s, tmp, &inj))) return rc;
     p.flips = tmp.flips; p.tile_off = tmp.tile_off; p.inj = inj ? 1 : 0;
   }
-  if (persist && ft == 2) {
+  if (persist && ck == 2) {
     // one tile per CTA of the grid
     const long long ctas = std::min<long long>(nI * nJ, nsm);
     if (ensure(w.tscr, sizeof(double) * SP_BM * SP_BN * (size_t)ctas))
@@ -1924,7 +1985,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  if ((tc ? run_tc(ta_t, tb_t, ft, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
+  if ((tc ? run_tc(ta_t, tb_t, ck, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
       cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);

@@ -234,6 +234,118 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const double *__restri
   }
 }
 
+// ---------------------------------------------------------------- checksum vectors of the plain form
+// From the bf16 operand X (R rows of Kp entries, k contiguous; rows of op(A)
+// or columns of op(B)) and its groups of 128 rows g:
+//   pieces[g][k] and pieces[nG + g][k]: the two bf16 pieces hi = bf16(s),
+//     lo = bf16(s - hi) of s = fl32(sum_{r in g} X[r][k]) (rows in order);
+//   part_row[c][r] = sum over chunk c's k of |X[r][k]|, FP32 rounded up;
+//   part_gmax[c][g] = max over chunk c's k of sum_{r in g} |X[r][k]|, FP32
+//     rounded up.
+// Block (g, c): the 128 rows of g and k-chunk c of BF16CS_KC entries, a thread
+// per two consecutive k (32-bit loads; 128 bytes per warp and row).  FP32
+// adds only: the FP64 pipe is this GPU's scarcest unit.
+constexpr int BF16CS_KC = 512;
+
+__global__ void __launch_bounds__(256) bf16_checksum_kernel(const uint16_t *__restrict__ X, long long R,
+                                                            long long Kp, uint16_t *__restrict__ pieces,
+                                                            float *__restrict__ part_row,
+                                                            float *__restrict__ part_gmax, int nG) {
+  __shared__ float rowp[8][128];
+  __shared__ float colmax[8];
+  const int g = blockIdx.x, c = blockIdx.y, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const long long r0 = (long long)g * 128, nrows = min(128LL, R - r0);
+  const long long k = (long long)c * BF16CS_KC + 2 * t;
+  const bool kin = k < Kp;                       // Kp is even: both entries of the pair are in range
+  float s0 = 0.f, s1 = 0.f, a0 = 0.f, a1 = 0.f;
+  const uint32_t *x = reinterpret_cast<const uint32_t *>(X + r0 * Kp + (kin ? k : 0));
+  const long long stride = Kp / 2;               // in 32-bit words
+#pragma unroll 1
+  for (int r = 0; r < nrows; r += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = (kin && r + u < nrows) ? __ldg(x + (long long)(r + u) * stride) : 0u;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float x0 = __uint_as_float(v[u] << 16), x1 = __uint_as_float(v[u] & 0xFFFF0000u);
+      s0 = __fadd_rn(s0, x0);
+      s1 = __fadd_rn(s1, x1);
+      a0 = __fadd_ru(a0, fabsf(x0));
+      a1 = __fadd_ru(a1, fabsf(x1));
+      float ra = __fadd_ru(fabsf(x0), fabsf(x1));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ra = __fadd_ru(ra, __shfl_xor_sync(0xffffffffu, ra, o));
+      if (lane == 0 && r + u < 128) rowp[w][r + u] = ra;
+    }
+  }
+  if (kin) {
+    const float h0 = __bfloat162float(__float2bfloat16_rn(s0)), h1 = __bfloat162float(__float2bfloat16_rn(s1));
+    const float l0 = __fsub_rn(s0, h0), l1 = __fsub_rn(s1, h1);   // exact
+    const uint32_t hi = (__float_as_uint(h0) >> 16) | (__float_as_uint(h1) & 0xFFFF0000u);
+    const uint32_t lo = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(l0)) |
+                        ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(l1)) << 16);
+    *reinterpret_cast<uint32_t *>(pieces + (long long)g * Kp + k) = hi;
+    *reinterpret_cast<uint32_t *>(pieces + (long long)(nG + g) * Kp + k) = lo;
+  }
+  float m = fmaxf(a0, a1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) colmax[w] = m;
+  __syncthreads();
+  if (t < nrows) {
+    float ra = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ra = __fadd_ru(ra, rowp[q][t]);
+    part_row[(long long)c * R + r0 + t] = ra;
+  }
+  if (t == 0) {
+    float mm = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) mm = fmaxf(mm, colmax[q]);
+    part_gmax[(long long)c * nG + g] = mm;
+  }
+}
+
+// rowabs[r] = sum over chunks of part_row (rounded up, chunk order), gmax[g]
+// = max over chunks of part_gmax; as doubles (exact).
+__global__ void __launch_bounds__(256) bf16_checksum_finish_kernel(const float *__restrict__ part_row,
+                                                                   const float *__restrict__ part_gmax,
+                                                                   long long R, int nG, int nch,
+                                                                   double *__restrict__ rowabs,
+                                                                   double *__restrict__ gmax) {
+  const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (i < R) {
+    float s = 0.f;
+    for (int c = 0; c < nch; ++c) s = __fadd_ru(s, part_row[(long long)c * R + i]);
+    rowabs[i] = (double)s;
+  } else if (i < R + nG) {
+    const int g = (int)(i - R);
+    float m = 0.f;
+    for (int c = 0; c < nch; ++c) m = fmaxf(m, part_gmax[(long long)c * nG + g]);
+    gmax[g] = (double)m;
+  }
+}
+
+// The checksum vectors and absolute sums of the plain form for one bf16
+// operand X (R x Kp): pieces (2 ceil(R/128) rows of Kp bf16), rowabs (R),
+// gmax (ceil(R/128)); part: device scratch of bf16_checksum_scratch floats.
+long long bf16_checksum_scratch(long long R, long long Kp) {
+  const long long nG = (R + 127) / 128, nch = (Kp + BF16CS_KC - 1) / BF16CS_KC;
+  return nch * (R + nG);
+}
+
+cudaError_t launch_bf16_checksums(const void *X, long long R, long long Kp, void *pieces, double *rowabs,
+                                  double *gmax, float *part, cudaStream_t s) {
+  if (R <= 0) return cudaSuccess;
+  const int nG = (int)((R + 127) / 128), nch = (int)((Kp + BF16CS_KC - 1) / BF16CS_KC);
+  float *part_row = part, *part_gmax = part + (long long)nch * R;
+  bf16_checksum_kernel<<<dim3((unsigned)nG, (unsigned)nch), 256, 0, s>>>(
+      (const uint16_t *)X, R, Kp, (uint16_t *)pieces, part_row, part_gmax, nG);
+  bf16_checksum_finish_kernel<<<(unsigned)((R + nG + 255) / 256), 256, 0, s>>>(part_row, part_gmax, R, nG, nch,
+                                                                              rowabs, gmax);
+  return cudaGetLastError();
+}
+
 // Row exponents (unless plain) and slices of op(X) (R x K, padded to Kp);
 // mb: R words of device scratch for the row maxima; nsm: the SM count (sizes
 // the k-split of the maxima pass).

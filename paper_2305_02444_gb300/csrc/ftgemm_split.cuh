@@ -14,14 +14,19 @@
 //  - plain BF16: op(A), op(B) rounded to bf16, one pair, FP32 accumulation
 //    over the whole K (the usual BF16-in / FP32-accumulate GEMM).
 //
-// Fault tolerance: the predicted checksums are carried in FP32 (each slab's
-// column sums of the A slice and row sums of the B slice are taken on the CUDA
-// cores from the staged tiles, then multiplied into the other operand's slab),
-// folded into FP64 with the same weights; the reference sums of the FP64
-// accumulators, the verification and the correction (an FP64 dot product of
-// the original FP64 operands) stay in FP64.  The threshold is the FP32
+// Fault tolerance of this kernel (ft = 1): the predicted checksums are
+// carried in FP32 (each slab's column sums of the A slice and row sums of the
+// B slice are taken on the CUDA cores from the staged tiles, then multiplied
+// into the other operand's slab), folded into FP64 with the same weights; the
+// reference sums of the FP64 accumulators, the verification and the
+// correction (an FP64 dot product of the original FP64 operands, or of the
+// bf16 operands in the plain form) stay in FP64.  The threshold is the FP32
 // rounding bound of the predicted checksums (accumulated alongside as an
-// absolute-value checksum) plus the FP64 folding bound.
+// absolute-value checksum) plus the FP64 folding bound, and in the plain form
+// the tensor core's FP32 accumulation bound.  The tile epilogue below
+// (split_tile_finish, split_check, split_tile_recompute) also serves the
+// tcgen05 kernels, which verify against checksum products computed before the
+// product (CK 2).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -78,9 +83,25 @@ __device__ __forceinline__ float warp_sum_ru(float v) {
 }
 
 
-// Recompute the flagged elements of a tile from the original FP64 operands:
-// the flagged row x column intersections (or, with one side empty or more
-// than 64 of them, the whole flagged row and column segments).  buf holds the
+// FP32 accumulation bound of the plain BF16 form: the tensor core's FP32 sum
+// of K exact bf16 products differs from the exact sum by at most e32(K)
+// times the sum of their magnitudes.  The order and rounding inside one MMA
+// are not documented; the bound assumes only blocks of two or more inputs,
+// each aligned to its largest with 24 bits kept and rounded or truncated
+// once, which errs by at most 2 K 2^-23 of the magnitudes (16 products of
+// slack for ragged blocks).
+__device__ __forceinline__ double plain_acc_bound(long long K) { return (double)(K + 16) * 0x1p-22; }
+
+__device__ __forceinline__ double bf16_bits_to_f64(uint16_t h) {
+  return (double)__uint_as_float((uint32_t)h << 16);
+}
+
+// Recompute the flagged elements of a tile: the flagged row x column
+// intersections (or, with one side empty or more than 64 of them, the whole
+// flagged row and column segments).  The emulated forms recompute from the
+// original FP64 operands; the plain BF16 form from the bf16 operands its
+// product used (p.Ab / p.Bb), in FP64, so that a corrected element is the
+// form's own product without its FP32 accumulation error.  buf holds the
 // tile's output (column-major 128 x 128, shared or global memory) and takes
 // the recomputed values; a value that differs by more than the element bound
 // counts as detected (cnt[2]) with a location record.  Warp `wid` of `nw`
@@ -101,9 +122,11 @@ __device__ __forceinline__ void split_tile_recompute(const SplitParams &p, doubl
     else if (e < nr * nJt) { il = s_fr[e / nJt]; jl = e % nJt; }
     else { il = (e - nr * nJt) % mI; jl = s_fc[(e - nr * nJt) / mI]; }
     const long long gi = i0 + il, gj = j0 + jl;
+    const bool bf = p.S == 0 && p.Ab != nullptr;
     double dot = 0.0, ab = 0.0;
     for (long long k = lane; k < p.K; k += 32) {
-      const double av = sp_glob_a<TA, TB>(p, gi, k), bv = sp_glob_b<TA, TB>(p, k, gj);
+      const double av = bf ? bf16_bits_to_f64(p.Ab[gi * p.ldk + k]) : sp_glob_a<TA, TB>(p, gi, k);
+      const double bv = bf ? bf16_bits_to_f64(p.Bb[gj * p.ldk + k]) : sp_glob_b<TA, TB>(p, k, gj);
       dot = fma(av, bv, dot);
       ab = fma(fabs(av), fabs(bv), ab);
     }
@@ -114,11 +137,21 @@ __device__ __forceinline__ void split_tile_recompute(const SplitParams &p, doubl
       const double nv = use_c ? fma(p.alpha, dot, p.beta * c) : p.alpha * dot;
       // the emulated value may differ from the FP64 one by the splitting error
       // (plain BF16: the input rounding) plus FP64 roundings
-      const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
-      const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
-                                         : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
-      const double te = fabs(p.alpha) * split_err +
-                        2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
+      double te;
+      if (bf) {
+        // the plain form's FP32 accumulation against the FP64 recomputation
+        // from the same bf16 operands (products below the FP32 normal range
+        // may be flushed: the last term)
+        te = fabs(p.alpha) * ab * 1.01 * plain_acc_bound(p.K) +
+             2.01 * (p.K + 4) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0)) +
+             fabs(p.alpha) * (double)(p.K + 16) * 0x1p-124;
+      } else {
+        const double sc = ldexp(1.0, p.eA[gi] + p.eB[gj]);
+        const double split_err = (p.S > 0) ? (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S) * sc
+                                           : 0x1p-7 * ab + 2.01 * (p.K + 2) * 0x1p-24 * ab;
+        te = fabs(p.alpha) * split_err +
+             2.01 * (p.K + p.npairs + 3) * 0x1p-53 * (fabs(p.alpha) * ab + (use_c ? fabs(p.beta * c) : 0.0));
+      }
       const double old = buf[jl * SP_BM + il];
       if ((!isfinite(old) && isfinite(nv)) || fabs(old - nv) > te) {
         atomicAdd(&cnt[2], 1);
@@ -147,21 +180,56 @@ __device__ __forceinline__ void split_tile_report(const SplitParams &p, const in
   if (cnt[4]) atomicAdd(&r->unverifiable, (unsigned long long)cnt[4]);
 }
 
-// The threshold test of one row or column checksum of the emulated product:
-// ref, the sum of the output; cs / ca, the
-// sums of C and of |C| (FP32 rounded up); P, the predicted checksum of the
-// product; S64, the absolute product bound; sig, the splitting-error scale.
-// Returns 0 verified, 1 flagged, 2 unverifiable.
-__device__ __forceinline__ int split_check(const SplitParams &p, double ref, double cs, double ca, double P, double S64,
-                                           double sig) {
+// The threshold test of one row or column checksum: ref, the sum of the
+// output; cs / ca, the sums of C and of |C| (FP32 rounded up); P, the
+// predicted checksum of the product; gmax * vsum, the Hoelder bound of the
+// absolute product checksum (for a column check of tile (I, J):
+// max_k sum_{i in I} |a_ik| and sum_k |b_kj|); sig, the splitting-error
+// scale of the emulated forms.  Returns 0 verified, 1 flagged, 2
+// unverifiable.
+//  - Emulated forms: FP64 roundings of the folded pair sums and the
+//    epilogue, plus the splitting error of the reference (and of P when it
+//    is an emulated product too, in sig).
+//  - Plain BF16 form (S == 0), checksums carried in FP32: the reference's
+//    FP32 accumulation errors (at most e32 H), the predicted checksum's
+//    (the FP32 group sums of the bf16 operands over at most 128 rows, their
+//    two-piece bf16 split within 2^-16, the FP32 accumulation of the piece
+//    products; the sum of C in FP32, within (L + 1) 2^-24 of the sum of
+//    |C|), the FP64 roundings, and results below the FP32 normal range
+//    (flushed products; checksum pieces that lose bits there, at most 2^-134
+//    per entry times the other operand).
+__device__ __forceinline__ int split_check(const SplitParams &p, double ref, double cs, double ca, double P,
+                                           double gmax, double vsum, double sig) {
   const bool use_c = p.beta != 0.0;
   const double pred = use_c ? fma(p.alpha, P, p.beta * cs) : p.alpha * P;
-  const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
-  const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
-  const double tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) + split_err +
-                     n * 0x1p-1021;
+  const double S64 = gmax * vsum;
+  double tau;
+  if (p.S == 0) {
+    const double e32 = plain_acc_bound(p.K), L = (double)SP_BM;
+    tau = fabs(p.alpha) * S64 * (2.04 * e32 + 1.01 * (L + 1.0) * 0x1p-24 + 1.01 * 0x1p-16) +
+          (use_c ? fabs(p.beta) * ca * 1.01 * (L + 1.0) * 0x1p-24 : 0.0) +
+          2.01 * (L + 40.0) * 0x1p-53 * (fabs(p.alpha) * S64 * (1.0 + e32) + (use_c ? fabs(p.beta) * ca : 0.0)) +
+          fabs(p.alpha) * ((L + 2.0) * (double)(p.K + 16) * 0x1p-124 + vsum * 0x1p-130) + (L + 40.0) * 0x1p-1021;
+  } else {
+    const double n = (double)(p.K + SP_BM + 3 + 32 + p.npairs);
+    const double split_err = fabs(p.alpha) * sig * (double)p.K * (p.S + 4) * ldexp(1.0, -p.w * p.S);
+    tau = 2.01 * n * 0x1p-53 * (fabs(p.alpha) * S64 + (use_c ? fabs(p.beta) * ca : 0.0)) + split_err +
+          n * 0x1p-1021;
+  }
   if (!isfinite(pred) || !isfinite(tau)) return 2;
   return fabs(ref - pred) <= tau ? 0 : 1;
+}
+
+// The predicted checksums of the product: column j of tile row I (P1) and
+// row i of tile column J (P2), each the sum of two pieces in the plain
+// BF16 form.
+__device__ __forceinline__ double split_p1(const SplitParams &p, int I, long long gj) {
+  const double *q = p.P1 + (long long)I + gj * p.ldp1;
+  return p.p1_lo ? q[0] + q[p.p1_lo] : q[0];
+}
+__device__ __forceinline__ double split_p2(const SplitParams &p, long long gi, int J) {
+  const double *q = p.P2 + gi + (long long)J * p.ldp2;
+  return p.p2_lo ? q[0] + q[p.p2_lo] : q[0];
 }
 
 // The end of a tile shared by the split kernels, run by 256 threads: sC holds
@@ -245,13 +313,13 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
         ca = (double)__fadd_ru((float)q[2], (float)q[386]);
         sig = (sigp[4] + sigp[5]) * pow2_or_ldexp(p.eA[i0 + idx]);
       }
-      const double P = col ? p.P1[(long long)I + (long long)(j0 + idx) * p.ldp1]
-                           : p.P2[(long long)(i0 + idx) + (long long)J * p.ldp2];
-      const double S64 = col ? p.bcolabs[j0 + idx] * p.aabsmax[I] : p.arowabs[i0 + idx] * p.babsmax[J];
+      const double P = col ? split_p1(p, I, j0 + idx) : split_p2(p, i0 + idx, J);
+      const double gmax = col ? p.aabsmax[I] : p.babsmax[J];
+      const double vsum = col ? p.bcolabs[j0 + idx] : p.arowabs[i0 + idx];
       // splitting error of the reference sum, plus that of the predicted
       // checksum when it is an emulated product as well
       if (p.ePA) sig += col ? ldexp(1.0, p.ePA[I] + p.eB[j0 + idx]) : ldexp(1.0, p.eA[i0 + idx] + p.ePB[J]);
-      const int r = split_check(p, ref, cs, ca, P, S64, sig);
+      const int r = split_check(p, ref, cs, ca, P, gmax, vsum, sig);
       if (r == 2) atomicAdd(&cnt[4], 1);
       else if (r == 1) {
         if (col) s_fc[atomicAdd(&cnt[1], 1)] = idx;
@@ -524,12 +592,14 @@ __global__ void __launch_bounds__(256, 1)
       for (int j = 0; j < SP_BN; ++j) ref += sC[j * SP_BM + tid - 128];
     }
     // the predicted checksum carries the FP32 rounding of up to kchunk products
-    // per pair-chunk; the accumulators carry one FP64 rounding per fold
+    // per pair-chunk (CUDA-core FMAs, rounded to nearest); the accumulators
+    // carry one FP64 rounding per fold, and in the plain BF16 form also the
+    // tensor core's FP32 accumulation over the whole K (plain_acc_bound)
     const double u32 = 0x1p-24, u64 = 0x1p-53;
     const double n32 = (double)(min((long long)p.kchunk, p.Kp) + 128 + 2);
     const double nfold = (double)(p.npairs * ((p.Kp + p.kchunk - 1) / p.kchunk) + 128 + 2);
-    // (x2: the plain BF16 form's accumulators carry the same FP32 rounding)
-    const double tau = 4.02 * n32 * u32 * ca64 + 2.01 * nfold * u64 * ca64 + 0x1p-1000;
+    const double ref32 = p.S == 0 ? 1.01 * plain_acc_bound(p.K) : 2.01 * n32 * u32;
+    const double tau = (2.01 * n32 * u32 + ref32) * ca64 + 2.01 * nfold * u64 * ca64 + 0x1p-1000;
     const int idx = tid & 127;
     const bool valid = (tid < 128) ? (idx < nJt) : (idx < mI);
     if (valid) {

@@ -69,7 +69,7 @@ template <bool TA, bool TB, int CK>
 __global__ void __launch_bounds__(256, 1)
     ftsplit_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ SplitParams p) {
-  static_assert(CK == 0 || CK == 2, "FP32 checksums are taken by the mma.sync kernel");
+  static_assert(CK == 0 || CK == 2, "no checks, or checks against the checksum products P1 / P2");
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));

@@ -68,6 +68,20 @@ __device__ __forceinline__ double f32_bits_to_f64(uint32_t fb) {
   return (double)__uint_as_float(fb);
 }
 
+// The same for FP32 values, rounded to nearest (the plain form's C sums).
+__device__ __forceinline__ float colsum16_rn(float (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
+      v[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+    }
+  }
+  return __fadd_rn(v[0], __shfl_xor_sync(0xffffffffu, v[0], 16));
+}
+
 // The same with FP32 adds rounded upward (the |C| sums of the threshold).
 __device__ __forceinline__ float colsum16_ru(float (&v)[16], int lane) {
 #pragma unroll
@@ -97,7 +111,7 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
   const uint32_t trow = tbase + ((uint32_t)(fw * 32) << 16);
   const uint32_t t64 = trow + TC_ACC64_COL;
   const bool use_c = p.beta != 0.0;
-  const bool direct = CK == 0 && p.S == 0;  // plain BF16: one pair, one chunk, no fold
+  const bool direct = p.S == 0;  // plain BF16: one pair, one chunk, no fold
   int *err = &p.rep->err;
   const unsigned long long limit = p.wait_limit_ns;
   bool ok = true;
@@ -142,7 +156,7 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
       if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
     if (!ok) break;
-    if (CK >= 1 && p.inj) {
+    if (CK >= 1 && p.inj && !direct) {
       // injection point: after pair pq has been folded in (kstep = pair index)
       while (fptr < fend) {
         DevFlip *f = p.flips + fptr;
@@ -174,6 +188,27 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
   const long long gi = i0 + il;
   const int eAi = rowok ? p.eA[gi] : 0;
   double *crow = p.C + gi;  // C(gi, j0 + col) = crow[(j0 + col) * ldc]
+  // CK 2: the verification's inputs (predicted checksums of this thread's
+  // column il and row il, in one or two pieces, and the absolute sums of
+  // their thresholds), loaded now so that their latency passes under pass 1
+  double v_p1a = 0.0, v_p1b = 0.0, v_p2a = 0.0, v_p2b = 0.0, v_amax = 0.0, v_bsum = 0.0, v_bmax = 0.0,
+         v_asum = 0.0;
+  if (CK == 2) {
+    if (il < nJt) {
+      const double *q = p.P1 + (long long)I + (long long)(j0 + il) * p.ldp1;
+      v_p1a = q[0];
+      if (p.p1_lo) v_p1b = q[p.p1_lo];
+      v_amax = p.aabsmax[I];
+      v_bsum = p.bcolabs[j0 + il];
+    }
+    if (rowok) {
+      const double *q = p.P2 + gi + (long long)J * p.ldp2;
+      v_p2a = q[0];
+      if (p.p2_lo) v_p2b = q[p.p2_lo];
+      v_bmax = p.babsmax[J];
+      v_asum = p.arowabs[gi];
+    }
+  }
   if (CK == 0) {
 #pragma unroll 1
     for (int ch = 0; ch < SP_BN / 32; ++ch) {
@@ -211,37 +246,113 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
     return true;
   }
 
-  // CK 2, pass 1: out, written back over the FP64 accumulators, and the sums
+  // CK 2, pass 1: out, written back over the FP64 accumulators, and the sums.
+  // The plain BF16 form reads its FP32 accumulator instead (converted
+  // exactly; an injected fault flips a bit of that FP64 value, its only pair
+  // being k-step 0), writes out into the unused FP64 columns and then
+  // releases the accumulator to the next tile's MMAs; its C-side sums are
+  // FP32 like the rest of its predicted checksums (the reference sums of out
+  // stay FP64).  The next chunk's C is loaded while the current one is
+  // summed.
   double rs0 = 0.0, rs1 = 0.0, rc0 = 0.0, rc1 = 0.0;  // row sums of out and C over even / odd columns
+  float rf0 = 0.0f, rf1 = 0.0f;                       // plain form: row sums of C in FP32
   float ra0 = 0.0f, ra1 = 0.0f;                       // and of |C| (rounded up)
-#pragma unroll 1
-  for (int ch = 0; ch < SP_BN / 16; ++ch) {
-    uint32_t d[32];
-    tmem_ld_x32(t64 + (uint32_t)(ch * 32), d);
-    double cv[16], ov[16];
-    float av[16];
+  const bool tile_faults = direct && CK >= 1 && p.inj && fptr < fend;
+  const bool beta1 = p.beta == 1.0;
+  double cn[16];
+  auto load_c = [&](int ch, double (&dst)[16]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int col = ch * 16 + j;
-      cv[j] = (use_c && rowok && col < nJt) ? crow[(long long)(j0 + col) * p.ldc] : 0.0;
+      dst[j] = (use_c && rowok && col < nJt) ? crow[(long long)(j0 + col) * p.ldc] : 0.0;
     }
+  };
+  load_c(0, cn);
+#pragma unroll 1
+  for (int ch = 0; ch < SP_BN / 16; ++ch) {
+    double cv[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) cv[j] = cn[j];
+    if (ch + 1 < SP_BN / 16) load_c(ch + 1, cn);
+    uint32_t d[32];
+    if (direct) {
+      uint32_t f[16];
+      tmem_ld_x16(trow + (uint32_t)(blast * SP_BN + ch * 16), f);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const double v = f32_bits_to_f64(f[j]);
+        d[2 * j] = tc_lo(v);
+        d[2 * j + 1] = tc_hi(v);
+      }
+      if (tile_faults) {
+        for (int q = fptr; q < fend; ++q) {
+          DevFlip *fl = p.flips + q;
+          const int fc = (int)(fl->col - j0) - ch * 16;
+          if ((int)(fl->row - i0) != il || fc < 0 || fc >= 16) continue;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (j == fc) {
+              const double before = tc_pack_f64(d[2 * j], d[2 * j + 1]);
+              const double after = flip_bit(before, fl->bit);
+              d[2 * j] = tc_lo(after);
+              d[2 * j + 1] = tc_hi(after);
+              fl->before = before;
+              fl->after = after;
+              fl->applied = 1;
+              fl->kfirst = 0;
+            }
+        }
+      }
+    } else {
+      tmem_ld_x32(t64 + (uint32_t)(ch * 32), d);
+    }
+    double bc[16], ov[16];  // beta C (C itself when beta is 1: the same values)
+    if (beta1) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) bc[j] = cv[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) bc[j] = p.beta * cv[j];
+    }
+    float av[16], cf[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int col = ch * 16 + j;
       double o = 0.0;
       if (rowok && col < nJt) {
-        const double v = scale_pow2_int(tc_pack_f64(d[2 * j], d[2 * j + 1]), eAi + __ldg(p.eB + j0 + col));
-        o = use_c ? fma(p.alpha, v, p.beta * cv[j]) : p.alpha * v;
+        const double a = tc_pack_f64(d[2 * j], d[2 * j + 1]);
+        const double v = direct ? a : scale_pow2_int(a, eAi + __ldg(p.eB + j0 + col));
+        o = use_c ? fma(p.alpha, v, bc[j]) : p.alpha * v;
       }
       ov[j] = o;
       d[2 * j] = tc_lo(o);
       d[2 * j + 1] = tc_hi(o);
       av[j] = f32_ru_abs(cv[j]);
-      if (j & 1) { rs1 += o; rc1 += cv[j]; ra1 = __fadd_ru(ra1, av[j]); }
-      else { rs0 += o; rc0 += cv[j]; ra0 = __fadd_ru(ra0, av[j]); }
+      if (j & 1) { rs1 += o; ra1 = __fadd_ru(ra1, av[j]); }
+      else { rs0 += o; ra0 = __fadd_ru(ra0, av[j]); }
+    }
+    if (direct) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        cf[j] = f32_rn(cv[j]);
+        if (j & 1) rf1 = __fadd_rn(rf1, cf[j]);
+        else rf0 = __fadd_rn(rf0, cf[j]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (j & 1) rc1 += cv[j];
+        else rc0 += cv[j];
+      }
     }
     tmem_st_x32(t64 + (uint32_t)(ch * 32), d);
-    const double so = colsum16(ov, lane), sc = colsum16(cv, lane);
+    if (direct && ch + 1 == SP_BN / 16) {  // the FP32 accumulator is read: the next tile's MMAs may reuse it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce0 + 8 * blast);
+    }
+    const double so = colsum16(ov, lane);
+    const double sc = direct ? (double)colsum16_rn(cf, lane) : colsum16(cv, lane);
     const float sa = colsum16_ru(av, lane);
     if (lane < 16) {
       s_co[fw * 128 + ch * 16 + lane] = so;
@@ -249,7 +360,10 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
       s_ca[fw * 128 + ch * 16 + lane] = sa;
     }
   }
-  {
+  if (direct) {
+    rc0 = (double)rf0;
+    rc1 = (double)rf1;
+  } else {  // the splitting-error scales of the emulated forms
     const double sa = warp_sum(rowok ? pow2_or_ldexp(eAi) : 0.0);
     const double sb = warp_sum(il < nJt ? pow2_or_ldexp(p.eB[j0 + il]) : 0.0);
     if (lane == 0) { s_sig[fw] = sa; s_sig[4 + fw] = sb; }
@@ -261,17 +375,17 @@ __device__ __forceinline__ bool tcp_folder_tile(const SplitParams &p, int I, int
     const double ref = (s_co[il] + s_co[128 + il]) + (s_co[256 + il] + s_co[384 + il]);
     const double cs = (s_cc[il] + s_cc[128 + il]) + (s_cc[256 + il] + s_cc[384 + il]);
     const double ca = (double)__fadd_ru(__fadd_ru(s_ca[il], s_ca[128 + il]), __fadd_ru(s_ca[256 + il], s_ca[384 + il]));
-    double sig = ((s_sig[0] + s_sig[1]) + (s_sig[2] + s_sig[3])) * pow2_or_ldexp(p.eB[gj]);
+    double sig = direct ? 0.0 : ((s_sig[0] + s_sig[1]) + (s_sig[2] + s_sig[3])) * pow2_or_ldexp(p.eB[gj]);
     if (p.ePA) sig += ldexp(1.0, p.ePA[I] + p.eB[gj]);
-    const int r = split_check(p, ref, cs, ca, p.P1[(long long)I + gj * p.ldp1], p.bcolabs[gj] * p.aabsmax[I], sig);
+    const int r = split_check(p, ref, cs, ca, p.p1_lo ? v_p1a + v_p1b : v_p1a, v_amax, v_bsum, sig);
     if (r == 2) atomicAdd(&cnt[4], 1);
     else if (r == 1) s_fc[atomicAdd(&cnt[1], 1)] = il;
   }
   if (rowok) {
-    double sig = ((s_sig[4] + s_sig[5]) + (s_sig[6] + s_sig[7])) * pow2_or_ldexp(eAi);
+    double sig = direct ? 0.0 : ((s_sig[4] + s_sig[5]) + (s_sig[6] + s_sig[7])) * pow2_or_ldexp(eAi);
     if (p.ePA) sig += ldexp(1.0, eAi + p.ePB[J]);
     const int r = split_check(p, rs0 + rs1, rc0 + rc1, (double)__fadd_ru(ra0, ra1),
-                              p.P2[gi + (long long)J * p.ldp2], p.arowabs[gi] * p.babsmax[J], sig);
+                              p.p2_lo ? v_p2a + v_p2b : v_p2a, v_bmax, v_asum, sig);
     if (r == 2) atomicAdd(&cnt[4], 1);
     else if (r == 1) s_fr[atomicAdd(&cnt[0], 1)] = il;
   }
@@ -316,7 +430,7 @@ template <bool TA, bool TB, int CK>
 __global__ void __launch_bounds__(256, 1)
     ftsplit_tcp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        const __grid_constant__ SplitParams p) {
-  static_assert(CK == 0 || CK == 2, "FP32 checksums are taken by the mma.sync kernel");
+  static_assert(CK == 0 || CK == 2, "no checks, or checks against the checksum products P1 / P2");
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));

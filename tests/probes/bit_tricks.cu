@@ -3,12 +3,13 @@
 //   f32_ru_abs(x)        vs __double2float_ru(fabs(x))
 //   bf16_rn_bits(x)      vs __double2bfloat16(x)
 //   scale_pow2_int(x, e) vs scale_pow2(x, e)
-//   f32_bits_to_f64(f)   vs (double)f
+//   f32_bits_to_f64(f)   vs (double)f (FP32 subnormals included)
+//   f32_rn(x)            vs __double2float_rn(x)
 //   scaled_exact_f32(f, sh) vs the FP64 product 2^-sh * f, for integer-valued
 //                        f with |f| < 2^24 (the exact FP32 pair products) and
 //                        0 <= sh < 800
 // Inputs come from a counter-based hash (splitmix64) in eight families: raw
-// 64-bit patterns, the FP32 exponent range, exact bf16 halfway cases, values
+// 64-bit patterns, the FP32 exponent range, exact bf16 and FP32 halfway cases, values
 // exact in FP32, values near the FP32 maximum and minimum, zeros / Inf / NaN /
 // FP64 subnormals, raw FP32 patterns, integer pair products.  Prints one JSON
 // line: the mismatch count of each check and the first mismatching input.
@@ -19,7 +20,7 @@
 
 using namespace ftg;
 
-constexpr int NCHECK = 5;
+constexpr int NCHECK = 6;
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   z += 0x9E3779B97F4A7C15ull;
@@ -44,8 +45,10 @@ __global__ void check(unsigned long long n, unsigned long long *bad, unsigned lo
     switch (i & 7) {
       case 0: b = h; break;
       case 1: b = sign | ((unsigned long long)(866 + g % 316) << 52) | mant; break;  // around the FP32 range
-      case 2: b = sign | ((unsigned long long)(850 + g % 310) << 52) | (mant & ~((1ull << 45) - 1)) | (1ull << 44);
-        break;  // exact bf16 halfway
+      case 2:
+        b = (g & 2) ? sign | ((unsigned long long)(850 + g % 310) << 52) | (mant & ~((1ull << 45) - 1)) | (1ull << 44)
+                    : sign | ((unsigned long long)(850 + g % 310) << 52) | (mant & ~((1ull << 29) - 1)) | (1ull << 28);
+        break;  // exact bf16 / FP32 halfway
       case 3: b = sign | ((unsigned long long)(896 + g % 254) << 52) | (mant & ~((1ull << 29) - 1)) | (g & 1); break;
       case 4: b = sign | ((unsigned long long)((g & 1) ? 1150 : 897) << 52) | mant; break;  // FP32 max / min
       case 5: {
@@ -58,7 +61,8 @@ __global__ void check(unsigned long long n, unsigned long long *bad, unsigned lo
     }
     const double x = __longlong_as_double((long long)b);
     // 0: |x| rounded up to FP32
-    if (__float_as_uint(f32_ru_abs(x)) != __float_as_uint(__double2float_ru(fabs(x)))) record(bad, first, 0, b);
+    const float u1 = f32_ru_abs(x), u2 = __double2float_ru(fabs(x));
+    if (__float_as_uint(u1) != __float_as_uint(u2) && !(isnan(u1) && isnan(u2))) record(bad, first, 0, b);
     // 1: bf16 rounding
     if (bf16_rn_bits(x) != (uint32_t)__bfloat16_as_ushort(__double2bfloat16(x))) record(bad, first, 1, b);
     // 2: power-of-two scaling
@@ -66,7 +70,7 @@ __global__ void check(unsigned long long n, unsigned long long *bad, unsigned lo
     const double s1 = scale_pow2_int(x, e), s2 = scale_pow2(x, e);
     if (dbits(s1) != dbits(s2) && !(isnan(s1) && isnan(s2))) record(bad, first, 2, b);
     // 3: FP32 -> FP64
-    const uint32_t fb = (i & 1) ? (uint32_t)h : __float_as_uint((float)x);
+    const uint32_t fb = (i & 3) == 3 ? ((uint32_t)h & 0x807FFFFFu) : (i & 1) ? (uint32_t)h : __float_as_uint((float)x);
     const double c1 = f32_bits_to_f64(fb), c2 = (double)__uint_as_float(fb);
     if (dbits(c1) != dbits(c2) && !(isnan(c1) && isnan(c2))) record(bad, first, 3, fb);
     // 4: 2^-sh * f for an integer-valued f, |f| < 2^24
@@ -74,6 +78,9 @@ __global__ void check(unsigned long long n, unsigned long long *bad, unsigned lo
     const int sh = (int)(g % 800);
     const double p1 = scaled_exact_f32(__float_as_uint(f), sh), p2 = (double)f * ldexp(1.0, -sh);
     if (dbits(p1) != dbits(p2)) record(bad, first, 4, __float_as_uint(f) | ((unsigned long long)sh << 32));
+    // 5: FP32 rounding to nearest
+    const float r1 = f32_rn(x), r2 = __double2float_rn(x);
+    if (__float_as_uint(r1) != __float_as_uint(r2) && !(isnan(r1) && isnan(r2))) record(bad, first, 5, b);
   }
 }
 
@@ -88,8 +95,8 @@ int main() {
   if (cudaMemcpy(h, bad, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return 2;
   cudaFree(bad);
   printf("{\"inputs\": %llu, \"mismatch\": {\"f32_ru_abs\": %llu, \"bf16_rn_bits\": %llu, \"scale_pow2_int\": %llu, "
-         "\"f32_bits_to_f64\": %llu, \"scaled_exact_f32\": %llu}, \"first\": [\"%llx\", \"%llx\", \"%llx\", \"%llx\", "
-         "\"%llx\"]}\n",
-         n, h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8], h[9]);
+         "\"f32_bits_to_f64\": %llu, \"scaled_exact_f32\": %llu, \"f32_rn\": %llu}, \"first\": [\"%llx\", \"%llx\", "
+         "\"%llx\", \"%llx\", \"%llx\", \"%llx\"]}\n",
+         n, h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], h[8], h[9], h[10], h[11]);
   return 0;
 }

@@ -441,7 +441,10 @@ def _simulate_plain_tile(rng, K, L, alpha, beta, kind, acc):
         acs = (acs + a[i].astype(np.float32)).astype(np.float32)
     hi, lo = split.bf16_pieces(acs)
     P1 = np.array([acc(hi * b[:, j]) + acc(lo * b[:, j]) for j in range(L)])
-    pred = alpha * P1 + beta * C.sum(axis=0)
+    cs = np.zeros(L, dtype=np.float32)
+    for i in range(L):                                                           # FP32 sums of C
+        cs = (cs + C[i].astype(np.float32)).astype(np.float32)
+    pred = alpha * P1 + beta * cs.astype(np.float64)
     gmax = np.abs(a).sum(axis=0).max()
     tau = np.array([split.bf16_tau(K, L, alpha, gmax, np.abs(b[:, j]).sum(), beta, np.abs(C[:, j]).sum())
                     for j in range(L)])
