@@ -315,7 +315,15 @@ int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, int64_t K, do
 /* ftgemm_d on HOST matrices: copies A, B (and C unless beta == 0) to device
  * workspace, runs ftgemm_d, copies the M x N result back (rows M..ldc-1 of C
  * are left as they were), and waits for the stream.  Pinned host memory
- * makes the copies fastest; pageable memory also works. */
+ * makes the copies fastest; pageable memory also works.
+ * Large problems run in column panels so that the copies overlap the
+ * compute: op(A) goes up first, then each panel's columns of op(B) and C on
+ * a copy stream; each panel's FT-DGEMM starts as soon as its columns have
+ * landed, and its result goes back on a second copy stream while the next
+ * panel computes.  The results equal those of ftgemm_d (output tiles are
+ * independent); injected faults are drawn or listed over the whole M x N
+ * problem as for ftgemm_d and the report and injection log cover the whole
+ * call.  ftgemm_set_host_panels chooses the number of panels. */
 int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, double alpha,
                   const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                   double *C, int64_t ldc, ftgemm_report *rep, void *stream);
@@ -358,6 +366,12 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
  * splits of every tile (fewer when K is short).  ftgemm_d_noalloc never
  * splits; per-k-panel verification (ftgemm_set_panel_check) does not split. */
 int ftgemm_set_splitk(int nsplit);
+
+/* Column panels of ftgemm_d_host: 0 (default) picks them automatically (up to
+ * 8, each at least four waves of 128 x 128 tiles on the GPU; one panel, i.e.
+ * no overlap, for smaller problems), n >= 1 uses n panels (at most one per
+ * 128 columns).  Process-global; returns -1 for a negative value. */
+int ftgemm_set_host_panels(int panels);
 
 /* The K split that ftgemm_d (and ftgemm_d_host) would use for an M x N x K
  * problem on a GPU with nsm SMs under the current settings (host only, no

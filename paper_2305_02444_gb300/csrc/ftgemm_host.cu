@@ -98,9 +98,20 @@ struct Workspace {
   cudaEvent_t ipin_ev[2] = {nullptr, nullptr};  // recorded after each staging buffer's copies
   int ipin_next = 0;
   bool encc_attr = false;   // enc_c_kernel's shared-memory attribute set on this device
-  // the last injected call, for ftgemm_injection_log
+  // ftgemm_d_host with column panels: copy streams, events, the panels'
+  // report regions and fault tables
+  cudaStream_t up = nullptr, down = nullptr;
+  std::vector<cudaEvent_t> pev;
+  Buf prep, ploc, pfl;
+  // the last injected call, for ftgemm_injection_log: one segment per fault
+  // table (a call of panels has one per panel)
+  struct LogSeg {
+    const DevFlip *dev;
+    std::vector<long long> orig;  // sorted position in the table -> index of the fault in the call
+    long long col_off;            // added to the table's columns (the panel's first column)
+  };
   long long last_nflips = 0;
-  std::vector<long long> last_perm;  // sorted position -> original index
+  std::vector<LogSeg> last_log;
 };
 Workspace g_ws[MAX_DEV];
 
@@ -463,12 +474,10 @@ void zero_report(ftgemm_report *rep) {
   rep->panel_detected = 0;
 }
 
-// Build and upload the injection table for this call (FT path only).
-int upload_injection(long long M, long long N, long long nks, long long nI, long long ntiles, Workspace &w,
-                     cudaStream_t s, Params &p, bool *inj) {
-  *inj = false;
-  if (g_inj.mode == 0) return 0;
-  std::vector<ftgemm_flip> L;
+// The faults of one M x N call under the injection setting: drawn (mode 1)
+// or listed (mode 2); FTGEMM_ERR_INJECT when one lies outside the problem.
+int injection_list(long long M, long long N, long long nks, std::vector<ftgemm_flip> &L) {
+  L.clear();
   if (g_inj.mode == 1) {
     L.resize((size_t)std::max(0LL, g_inj.count));
     for (long long f = 0; f < (long long)L.size(); ++f) {
@@ -478,13 +487,39 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
       L[f].bit = (int)(splitmix64(g_inj.seed, 4 * (uint64_t)f + 3) % 63u);
       L[f].problem = 0;
     }
-  } else {
+  } else if (g_inj.mode == 2) {
     L = g_inj.list;
   }
   for (const auto &f : L)
     if (f.row < 0 || f.row >= M || f.col < 0 || f.col >= N || f.kstep < 0 || f.kstep >= nks || f.bit < 0 ||
         f.bit > 62)
       return FTGEMM_ERR_INJECT;
+  return 0;
+}
+
+// Where one call's fault table comes from and goes (ftgemm_d_host's panels):
+// an explicit list in the call's own coordinates, the device memory that
+// holds the table (and stays there for the log), the original index of each
+// listed fault and the column offset the log adds back.
+struct InjPanel {
+  const std::vector<ftgemm_flip> *list;
+  const std::vector<long long> *orig;
+  void *table;
+  long long col_off;
+};
+
+// Build and upload the injection table for this call (FT path only); with
+// `pan`, the panel's list into its own table, appended to the call's log.
+int upload_injection(long long M, long long N, long long nks, long long nI, long long ntiles, Workspace &w,
+                     cudaStream_t s, Params &p, bool *inj, const InjPanel *pan = nullptr) {
+  *inj = false;
+  if (g_inj.mode == 0) return 0;
+  std::vector<ftgemm_flip> L;
+  if (pan) {
+    L = *pan->list;
+  } else if (int rc = injection_list(M, N, nks, L)) {
+    return rc;
+  }
   const long long nf = (long long)L.size();
   std::vector<long long> perm(nf);
   for (long long q = 0; q < nf; ++q) perm[q] = q;
@@ -505,7 +540,9 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
   if (!w.ipin_ev[k] && cudaEventCreateWithFlags(&w.ipin_ev[k], cudaEventDisableTiming) != cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (cudaEventSynchronize(w.ipin_ev[k]) != cudaSuccess) return FTGEMM_ERR_CUDA;
-  if (ensure(w.flips, fbytes + obytes) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096)) return FTGEMM_ERR_NOMEM;
+  if ((!pan && ensure(w.flips, fbytes + obytes)) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096))
+    return FTGEMM_ERR_NOMEM;
+  void *table = pan ? pan->table : w.flips.p;
   DevFlip *hf = (DevFlip *)w.ipin[k].p;
   int *ho = (int *)((char *)w.ipin[k].p + fbytes);
   std::fill(ho, ho + ntiles + 1, 0);
@@ -516,14 +553,30 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
     ho[tile_of(f) + 1]++;
   }
   for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
-  cudaMemcpyAsync(w.flips.p, hf, fbytes + obytes, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(table, hf, fbytes + obytes, cudaMemcpyHostToDevice, s);
   cudaEventRecord(w.ipin_ev[k], s);
-  w.last_nflips = nf;
-  w.last_perm = perm;
-  p.flips = (DevFlip *)w.flips.p;
-  p.tile_off = (const int *)((const char *)w.flips.p + fbytes);
+  Workspace::LogSeg seg;
+  seg.dev = (const DevFlip *)table;
+  seg.orig.resize((size_t)nf);
+  for (long long q = 0; q < nf; ++q) seg.orig[q] = pan ? (*pan->orig)[perm[q]] : perm[q];
+  seg.col_off = pan ? pan->col_off : 0;
+  if (!pan) {
+    w.last_log.clear();
+    w.last_nflips = 0;
+  }
+  w.last_log.push_back(std::move(seg));
+  w.last_nflips += nf;
+  p.flips = (DevFlip *)table;
+  p.tile_off = (const int *)((const char *)table + fbytes);
   *inj = true;
   return 0;
+}
+
+// Bytes of one fault table (upload_injection's layout) of nf faults over
+// ntiles tiles.
+size_t injection_table_bytes(long long nf, long long ntiles) {
+  return ((sizeof(DevFlip) * (size_t)std::max(1LL, nf) + 255) & ~(size_t)255) +
+         ((sizeof(int) * (size_t)(ntiles + 1) + 255) & ~(size_t)255);
 }
 
 // Copy the device report (and up to rep->cap location records) into rep,
@@ -558,9 +611,18 @@ int copy_report(Workspace &w, ftgemm_report *rep, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
 
+// One column panel of ftgemm_d_host: its own device report and location
+// records, and its faults (none: no injection in this panel).
+struct GemmPanel {
+  DevReport *rep;
+  DevLoc *loc;
+  long long loc_cap;
+  const InjPanel *inj;
+};
+
 int gemm_impl(char transA, char transB, long long M, long long N, long long K, double alpha, const double *A,
               long long lda, const double *B, long long ldb, double beta, double *C, long long ldc,
-              ftgemm_report *rep, cudaStream_t s, bool ft) {
+              ftgemm_report *rep, cudaStream_t s, bool ft, const GemmPanel *gp = nullptr) {
   int rc = check_args(transA, transB, M, N, K, lda, ldb, ldc);
   if (rc) return rc;
   zero_report(rep);
@@ -623,12 +685,12 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
   p.M = M; p.N = N; p.K = K; p.alpha = alpha; p.beta = beta;
   p.A = Ause; p.B = Buse; p.C = Cuse; p.lda = ldaU; p.ldb = ldbU; p.ldc = ldcU;
   p.nI = (int)nI; p.nJ = (int)nJ; p.nks = (int)nks; p.Kp = Kp;
-  p.rep = (DevReport *)w.rep.p;
-  p.loc = (DevLoc *)w.loc.p;
-  p.loc_cap = LOC_CAP_DEV;
+  p.rep = gp ? gp->rep : (DevReport *)w.rep.p;
+  p.loc = gp ? gp->loc : (DevLoc *)w.loc.p;
+  p.loc_cap = gp ? gp->loc_cap : LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
   p.correct_mode = g_correct;
-  cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
+  cudaMemsetAsync(p.rep, 0, sizeof(DevReport), s);
 
   cudaEvent_t ea0 = nullptr, ea1 = nullptr, em0 = nullptr, em1 = nullptr;
   if (g_tim.on) {
@@ -648,7 +710,8 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     p.acs = (const double *)w.acs.p; p.bcs = (const double *)w.bcs.p;
     p.arowabs = (const double *)w.arowabs.p; p.aabsmax = (const double *)w.aabsmax.p;
     p.bcolabs = (const double *)w.bcolabs.p; p.babsmax = (const double *)w.babsmax.p;
-    rc = upload_injection(M, N, nks, nI, ntiles, w, s, p, &inj);
+    if (!gp) rc = upload_injection(M, N, nks, nI, ntiles, w, s, p, &inj);
+    else if (gp->inj) rc = upload_injection(M, N, nks, nI, ntiles, w, s, p, &inj, gp->inj);
     if (rc) return rc;
   }
 
@@ -756,6 +819,171 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
   return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
 }
 
+// ftgemm_d_host's column panels: 0 automatic, n >= 1 that many panels (at
+// most one per tile column) -- ftgemm_set_host_panels.
+int g_host_panels = 0;
+
+// Columns per panel of an M x N host-buffer call (N: one panel, no
+// pipeline).  Automatic: up to 8 panels, each at least four waves of tiles,
+// so that the panels keep the whole-launch efficiency of the grid.
+long long host_panel_cols(long long M, long long N, int nsm) {
+  const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN;
+  const long long P = g_host_panels > 0 ? std::min<long long>(g_host_panels, nJ)
+                                        : std::min<long long>({8LL, nJ, (nI * nJ) / (4LL * nsm)});
+  if (P <= 1) return N;
+  return (nJ + P - 1) / P * BN;
+}
+
+int ensure_copy_streams(Workspace &w, size_t nev) {
+  if (!w.up && cudaStreamCreateWithFlags(&w.up, cudaStreamNonBlocking) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  if (!w.down && cudaStreamCreateWithFlags(&w.down, cudaStreamNonBlocking) != cudaSuccess) return FTGEMM_ERR_CUDA;
+  while (w.pev.size() < nev) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return FTGEMM_ERR_CUDA;
+    w.pev.push_back(e);
+  }
+  return 0;
+}
+
+// ftgemm_d_host in column panels of NB columns of op(B) and C: op(A) goes up
+// first, then each panel's op(B) and C columns, on a copy stream; a panel's
+// FT-DGEMM runs on the caller's stream as soon as its columns have landed
+// and its result goes down on a second copy stream while the next panel
+// computes.  Output tiles are independent, so the results equal those of one
+// call.  The faults of the call are drawn (or listed) over the whole M x N
+// problem and each runs in the panel that holds its column; every panel
+// reports into its own device region, merged (columns and tile numbers
+// shifted back) after the last panel.
+int host_panels(char transA, char transB, long long M, long long N, long long K, double alpha, const double *A,
+                long long lda, const double *B, long long ldb, double beta, double *C, long long ldc,
+                ftgemm_report *r, cudaStream_t s, Workspace &w, long long NB) {
+  const long long P = (N + NB - 1) / NB;
+  const bool tb_n = is_n(transB);
+  const long long acols = is_n(transA) ? K : M, bcols = tb_n ? N : K;
+  const size_t abytes = sizeof(double) * (size_t)(lda * acols), bbytes = sizeof(double) * (size_t)(ldb * bcols);
+  const size_t cbytes = sizeof(double) * (size_t)(ldc * N);
+  if (ensure(w.hA, abytes) || ensure(w.hB, bbytes) || ensure(w.hC, cbytes)) return FTGEMM_ERR_NOMEM;
+  const long long nks = (K + BK - 1) / BK, nI = (M + BM - 1) / BM;
+  std::vector<ftgemm_flip> all;
+  if (int rc = injection_list(M, N, nks, all)) return rc;
+  std::vector<std::vector<ftgemm_flip>> pl((size_t)P);
+  std::vector<std::vector<long long>> po((size_t)P);
+  for (long long q = 0; q < (long long)all.size(); ++q) {
+    ftgemm_flip f = all[q];
+    const long long pp = f.col / NB;
+    f.col -= pp * NB;
+    pl[pp].push_back(f);
+    po[pp].push_back(q);
+  }
+  const long long capp = LOC_CAP_DEV / P;
+  std::vector<size_t> toff((size_t)P + 1, 0);
+  for (long long pp = 0; pp < P; ++pp) {
+    const long long nc = std::min(N, (pp + 1) * NB) - pp * NB;
+    toff[pp + 1] = toff[pp] + injection_table_bytes((long long)pl[pp].size(), nI * ((nc + BN - 1) / BN));
+  }
+  if (ensure(w.prep, sizeof(DevReport) * (size_t)P) || ensure(w.ploc, sizeof(DevLoc) * (size_t)(capp * P)) ||
+      ensure(w.pfl, toff[P]))
+    return FTGEMM_ERR_NOMEM;
+  if (int rc = ensure_side(w)) return rc;
+  if (int rc = ensure_copy_streams(w, (size_t)(2 * P + 2))) return rc;
+  // ev[0] fork (later: the upload stream's join), ev[1 + p] panel p landed, ev[1 + P + p] panel p
+  // computed, ev[2 P + 1] the download stream's join
+  cudaEvent_t *ev = w.pev.data();
+  cudaEventRecord(ev[0], s);
+  cudaStreamWaitEvent(w.up, ev[0], 0);
+  cudaStreamWaitEvent(w.down, ev[0], 0);
+  double *hA = (double *)w.hA.p, *hB = (double *)w.hB.p, *hC = (double *)w.hC.p;
+  cudaMemcpyAsync(hA, A, abytes, cudaMemcpyHostToDevice, w.up);
+  for (long long pp = 0; pp < P; ++pp) {
+    const long long j0 = pp * NB, nc = std::min(N, j0 + NB) - j0;
+    if (tb_n)
+      cudaMemcpyAsync(hB + j0 * ldb, B + j0 * ldb, sizeof(double) * (size_t)(ldb * nc), cudaMemcpyHostToDevice,
+                      w.up);
+    else
+      cudaMemcpy2DAsync(hB + j0, sizeof(double) * (size_t)ldb, B + j0, sizeof(double) * (size_t)ldb,
+                        sizeof(double) * (size_t)nc, (size_t)K, cudaMemcpyHostToDevice, w.up);
+    if (beta != 0.0)
+      cudaMemcpyAsync(hC + j0 * ldc, C + j0 * ldc, sizeof(double) * (size_t)(ldc * nc), cudaMemcpyHostToDevice,
+                      w.up);
+    cudaEventRecord(ev[1 + pp], w.up);
+  }
+  if (g_inj.mode) {  // this call's log is built panel by panel
+    w.last_log.clear();
+    w.last_nflips = 0;
+  }
+  int rc = 0;
+  for (long long pp = 0; pp < P && !rc; ++pp) {
+    const long long j0 = pp * NB, nc = std::min(N, j0 + NB) - j0;
+    cudaStreamWaitEvent(s, ev[1 + pp], 0);
+    InjPanel ip{&pl[pp], &po[pp], (char *)w.pfl.p + toff[pp], j0};
+    GemmPanel gp{(DevReport *)w.prep.p + pp, (DevLoc *)w.ploc.p + pp * capp, capp,
+                 (g_inj.mode && !pl[pp].empty()) ? &ip : nullptr};
+    rc = gemm_impl(transA, transB, M, nc, K, alpha, hA, lda, hB + (tb_n ? j0 * ldb : j0), ldb, beta, hC + j0 * ldc,
+                   ldc, nullptr, s, true, &gp);
+    if (rc) break;
+    cudaEventRecord(ev[1 + P + pp], s);
+    cudaStreamWaitEvent(w.down, ev[1 + P + pp], 0);
+    // only the M x nc block goes back: rows M..ldc-1 of the caller's C are
+    // not the call's to write
+    if (ldc == M)
+      cudaMemcpyAsync(C + j0 * ldc, hC + j0 * ldc, sizeof(double) * (size_t)(ldc * nc), cudaMemcpyDeviceToHost,
+                      w.down);
+    else
+      cudaMemcpy2DAsync(C + j0 * ldc, sizeof(double) * (size_t)ldc, hC + j0 * ldc, sizeof(double) * (size_t)ldc,
+                        sizeof(double) * (size_t)M, (size_t)nc, cudaMemcpyDeviceToHost, w.down);
+  }
+  // join both copy streams back into the caller's stream
+  cudaEventRecord(ev[2 * P + 1], w.down);
+  cudaStreamWaitEvent(s, ev[2 * P + 1], 0);
+  cudaEventRecord(ev[0], w.up);
+  cudaStreamWaitEvent(s, ev[0], 0);
+  if (rc) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    return rc;
+  }
+  // the panels' reports and location records, in one copy after the last panel
+  const long long cap = std::max<long long>(r->loc ? r->cap : 0, 0), per = std::min(capp, cap);
+  const size_t need = sizeof(DevReport) * (size_t)P + sizeof(DevLoc) * (size_t)(per * P);
+  if (ensure_pinned(w.pin, need + 4096)) return FTGEMM_ERR_NOMEM;
+  DevReport *hr = (DevReport *)w.pin.p;
+  DevLoc *hl = (DevLoc *)(hr + P);
+  cudaMemcpyAsync(hr, w.prep.p, sizeof(DevReport) * (size_t)P, cudaMemcpyDeviceToHost, s);
+  for (long long pp = 0; pp < P && per > 0; ++pp)
+    cudaMemcpyAsync(hl + pp * per, (DevLoc *)w.ploc.p + pp * capp, sizeof(DevLoc) * (size_t)per,
+                    cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FTGEMM_ERR_CUDA;
+  }
+  long long nout = 0;
+  bool timeout = false;
+  for (long long pp = 0; pp < P; ++pp) {
+    const DevReport &d = hr[pp];
+    r->detected += (long long)d.detected;
+    r->corrected += (long long)d.corrected;
+    r->checksum_only += (long long)d.checksum_only;
+    r->unverifiable += (long long)d.unverifiable;
+    r->flagged_rows += (long long)d.flagged_rows;
+    r->flagged_cols += (long long)d.flagged_cols;
+    r->recomputed += (long long)d.recomputed;
+    r->panel_detected += (long long)d.panel_detected;
+    r->n_loc += (long long)d.n_loc;
+    timeout = timeout || d.err;
+    const long long j0 = pp * NB;
+    for (long long q = 0; q < std::min<long long>(per, (long long)d.n_loc) && nout < cap; ++q, ++nout) {
+      const DevLoc &l = hl[pp * per + q];
+      r->loc[nout].row = l.row;
+      r->loc[nout].col = l.col + j0;
+      r->loc[nout].tile = (int)(l.tile + (j0 / BN) * nI);
+      r->loc[nout].kind = l.kind;
+      r->loc[nout].delta = l.delta;
+    }
+  }
+  if (timeout) return FTGEMM_ERR_TIMEOUT;
+  return cudaGetLastError() == cudaSuccess ? 0 : FTGEMM_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -787,6 +1015,15 @@ int ftgemm_d_host(char transA, char transB, int64_t M, int64_t N, int64_t K, dou
   if (!wp) return FTGEMM_ERR_NODEVICE;
   Workspace &w = *wp;
   cudaStream_t s = (cudaStream_t)stream;
+  if (K > 0 && alpha != 0.0) {
+    const long long NB = host_panel_cols(M, N, device_sms(dev));
+    if (NB < N) {
+      ftgemm_report local;
+      memset(&local, 0, sizeof(local));
+      return host_panels(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, rep ? rep : &local, s, w,
+                         NB);
+    }
+  }
   const long long acols = is_n(transA) ? K : M, bcols = is_n(transB) ? N : K;
   const size_t abytes = sizeof(double) * (size_t)(lda * acols), bbytes = sizeof(double) * (size_t)(ldb * bcols);
   const size_t cbytes = sizeof(double) * (size_t)(ldc * N);
@@ -955,21 +1192,25 @@ int64_t ftgemm_injection_log(ftgemm_flip_log *out, int64_t cap) {
   Workspace &w = *wp;
   const long long nf = w.last_nflips;
   if (nf == 0 || cap <= 0) return nf;
-  std::vector<DevFlip> h((size_t)nf);
-  if (cudaDeviceSynchronize() != cudaSuccess ||
-      cudaMemcpy(h.data(), w.flips.p, sizeof(DevFlip) * nf, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return -FTGEMM_ERR_CUDA;
-  for (long long q = 0; q < nf; ++q) {
-    const long long o = w.last_perm[q];
-    if (o >= cap) continue;
-    out[o].row = h[q].row;
-    out[o].col = h[q].col;
-    out[o].kstep = h[q].kstep;
-    out[o].bit = h[q].bit;
-    out[o].applied = h[q].applied;
-    out[o].before = h[q].before;
-    out[o].after = h[q].after;
-    out[o].kfirst = h[q].kfirst;
+  if (cudaDeviceSynchronize() != cudaSuccess) return -FTGEMM_ERR_CUDA;
+  for (const auto &seg : w.last_log) {
+    const long long n = (long long)seg.orig.size();
+    if (n == 0) continue;
+    std::vector<DevFlip> h((size_t)n);
+    if (cudaMemcpy(h.data(), seg.dev, sizeof(DevFlip) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return -FTGEMM_ERR_CUDA;
+    for (long long q = 0; q < n; ++q) {
+      const long long o = seg.orig[q];
+      if (o >= cap) continue;
+      out[o].row = h[q].row;
+      out[o].col = h[q].col + seg.col_off;
+      out[o].kstep = h[q].kstep;
+      out[o].bit = h[q].bit;
+      out[o].applied = h[q].applied;
+      out[o].before = h[q].before;
+      out[o].after = h[q].after;
+      out[o].kfirst = h[q].kfirst;
+    }
   }
   return nf;
 }
@@ -1031,6 +1272,13 @@ int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits, i
   const KSplit k = plan_ksplit(ntiles, nks, nsm, g_panel > 0 && nks > g_panel);
   *splits = k.S;
   *first_split_tile = k.S > 1 ? k.tail_base : ntiles;
+  return 0;
+}
+
+int ftgemm_set_host_panels(int panels) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (panels < 0) return -1;
+  g_host_panels = panels;
   return 0;
 }
 
@@ -1100,7 +1348,8 @@ int ftgemm_finalize(void) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return FTGEMM_ERR_NODEVICE;
   Workspace &w = g_ws[dev];
   cudaDeviceSynchronize();
-  Buf *dbufs[] = {&w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
+  Buf *dbufs[] = {&w.prep, &w.ploc, &w.pfl,
+                  &w.acs, &w.bcs, &w.arowabs, &w.aabsmax, &w.bcolabs, &w.babsmax, &w.part_abs, &w.part_max,
                   &w.rep, &w.loc, &w.flips, &w.stA, &w.stB, &w.stC, &w.hA, &w.hB, &w.hC,
                   &w.W, &w.wpc, &w.wpr, &w.uC, &w.uccs, &w.uccsa, &w.ucrs, &w.ucrsa, &w.uP1, &w.uP2,
                   &w.spA, &w.spB, &w.spEA, &w.spEB, &w.spPA, &w.spPB, &w.spEPA, &w.spEPB, &w.tscr, &w.spMB,
@@ -1121,6 +1370,11 @@ int ftgemm_finalize(void) {
   }
   w.ipin_next = 0;
   if (w.side) cudaStreamDestroy(w.side);
+  if (w.up) cudaStreamDestroy(w.up);
+  if (w.down) cudaStreamDestroy(w.down);
+  for (cudaEvent_t e : w.pev) cudaEventDestroy(e);
+  w.pev.clear();
+  w.up = w.down = nullptr;
   if (w.fork_ev) cudaEventDestroy(w.fork_ev);
   if (w.join_ev) cudaEventDestroy(w.join_ev);
   w.side = nullptr;
@@ -1128,7 +1382,7 @@ int ftgemm_finalize(void) {
   w.pin.cap = 0;
   w.init = false;
   w.last_nflips = 0;
-  w.last_perm.clear();
+  w.last_log.clear();
   return 0;
 }
 

@@ -81,6 +81,8 @@ def lib():
         L.ftgemm_injection_log.restype = _i64
         L.ftgemm_selftest_wait_timeout.argtypes = [_i64, _vp]
         L.ftgemm_launch_count.restype = _i64
+        L.ftgemm_set_host_panels.argtypes = [ctypes.c_int]
+        L.ftgemm_set_host_panels.restype = ctypes.c_int
         L.ftgemm_set_panel_check.argtypes = [ctypes.c_int]
         L.ftgemm_set_panel_check.restype = ctypes.c_int
         L.ftgemm_query_ksplit.argtypes = [_i64, _i64, _i64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -288,6 +290,11 @@ def ftgemm_selftest_wait_timeout(limit_ns: int, stream=None) -> int:
 def ftgemm_set_panel_check(kslabs: int) -> int:
     """Verify accumulators every kslabs k-slabs (0: only at the end of K)."""
     return lib().ftgemm_set_panel_check(kslabs)
+
+
+def ftgemm_set_host_panels(panels: int) -> int:
+    """ftgemm_d_host's column panels: 0 automatic, n >= 1 that many."""
+    return lib().ftgemm_set_host_panels(panels)
 
 
 def ftgemm_set_splitk(nsplit: int) -> int:

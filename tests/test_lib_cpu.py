@@ -96,6 +96,12 @@ def test_split_engine_knob_codes(ft):
     assert ft.ftgemm_set_split_engine(0) == 0
 
 
+def test_host_panels_knob_codes(ft):
+    assert ft.ftgemm_set_host_panels(-1) == -1
+    for n in (3, 1, 0):
+        assert ft.ftgemm_set_host_panels(n) == 0
+
+
 def test_correction_knob_codes(ft):
     assert ft.ftgemm_set_correction(2) == -1
     assert ft.ftgemm_set_correction(-1) == -1
