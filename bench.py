@@ -364,6 +364,94 @@ def sweep(args):
     print(json.dumps({"sweep": rows, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS}), flush=True)
 
 
+def panel_sweep(args):
+    """Per-k-panel verification (ftgemm_set_panel_check): overhead of checking
+    the accumulators every n k-slabs (n = 8, 32, 128) at 8192^3 and 1024^3
+    (NN, alpha 1.5, beta 0.5, U[-1,1]; and n = 2, finer than the 4-slab k-splits
+    of the 1024^3 grid), fault-free and with one flip per 64
+    tiles, against the unprotected kernel and the end-of-tile check; then
+    several faults in one element across panels at 8192^3 (three flips of
+    each of 64 elements, at k-steps in panels 0, 5 and 10 of 32 slabs): with
+    panel checks each fault is found in its panel, with the end-of-tile check
+    alone they merge into one correction per element; the injected elements
+    against the oracle either way (CPU, after the timed regions)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2305_02444_gb300 import build, ftgemm, inputs
+    build.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    shapes = [int(x) for x in args.panel_sizes.split(",") if x]
+    rows, multi = [], None
+    for n in shapes:
+        A = inputs.matrix(n, n, SEED, device="cuda")
+        B = inputs.matrix(n, n, SEED + 1, device="cuda")
+        C = inputs.matrix(n, n, SEED + 2, device="cuda")
+        nfl = math.ceil((-(-n // 128)) ** 2 / 64)
+        reps = max(2, min(10, int(2e12 / (2.0 * n ** 3))))
+
+        def t(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps / 1e3
+
+        ft_call = lambda: ftgemm.ftgemm_d("N", "N", n, n, n, ALPHA, A, n, B, n, BETA, C, n, report=False)
+        t_noft = t(lambda: ftgemm.ftgemm_d_noft("N", "N", n, n, n, ALPHA, A, n, B, n, BETA, C, n))
+        fl = 2.0 * n ** 3
+        for kslabs in [0] + [int(x) for x in args.panel_slabs.split(",") if x]:
+            ftgemm.ftgemm_set_panel_check(kslabs)
+            t_ft = t(ft_call)
+            ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nfl)
+            t_inj = t(ft_call)
+            rc, rep = ftgemm.ftgemm_d("N", "N", n, n, n, ALPHA, A, n, B, n, BETA, C, n, loc_cap=0)
+            ftgemm.ftgemm_set_injection(mode=0)
+            ftgemm.ftgemm_set_panel_check(0)
+            rows.append({"M": n, "N": n, "K": n, "panel_kslabs": kslabs, "ft_tflops": fl / t_ft / 1e12,
+                         "ft_inj_tflops": fl / t_inj / 1e12, "pct_fp64_peak": 100 * fl / t_ft / 1e12 / FP64_PEAK_TFLOPS,
+                         "overhead_vs_noft_pct": 100 * (t_ft / t_noft - 1),
+                         "overhead_inj_vs_noft_pct": 100 * (t_inj / t_noft - 1),
+                         "flips": nfl, "detected": rep["detected"], "panel_detected": rep["panel_detected"], "rc": rc})
+            print(json.dumps(rows[-1]), flush=True)
+        if n == max(shapes):
+            # several faults in one element, in different panels of 32 slabs
+            rng = np.random.default_rng(SEED)
+            pos = [(int(rng.integers(n)), int(rng.integers(n))) for _ in range(64)]
+            flips = [(i, j, 32 * p + 7, bit) for (i, j) in pos for p, bit in ((0, 62), (5, 58), (10, 55))]
+            Ah, Bh, Ch = A.cpu().T.numpy(), B.cpu().T.numpy(), C.cpu().T.numpy()
+            multi = {}
+            for kslabs in (32, 0):
+                ftgemm.ftgemm_set_panel_check(kslabs)
+                ftgemm.ftgemm_set_injection(mode=2, flips=flips)
+                Cw = C.clone()
+                rc, rep = ftgemm.ftgemm_d("N", "N", n, n, n, ALPHA, A, n, B, n, BETA, Cw, n, loc_cap=4096)
+                ftgemm.ftgemm_set_injection(mode=0)
+                ftgemm.ftgemm_set_panel_check(0)
+                torch.cuda.synchronize()
+                worst = 0.0
+                for (i, j) in pos:
+                    r, E = oracle.gemm("N", "N", ALPHA, Ah[i:i + 1], Bh[:, j:j + 1], BETA, Ch[i:i + 1, j:j + 1],
+                                       want_E=True)
+                    worst = max(worst, abs(float(Cw[j, i]) - r[0, 0]) / oracle.parity_tol(n, E)[0, 0])
+                multi[f"panel_kslabs_{kslabs}"] = {"flips": len(flips), "elements": len(pos),
+                                                  "detected": rep["detected"], "panel_detected": rep["panel_detected"],
+                                                  "corrected": rep["corrected"], "rc": rc,
+                                                  "max_err_over_parity_bound": worst}
+                print(json.dumps({"several_faults_per_element": multi}), flush=True)
+        del A, B, C
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "per-k-panel verification: TFLOP/s and overhead", "rows": rows,
+                      "several_faults_per_element": multi,
+                      "peak": FP64_PEAK_TFLOPS}), flush=True)
+
+
 def batched(args):
     """512 independent FT-DGEMMs, M, N, K each log-uniform in [32, 1024], NN,
     U[-1,1], alpha = 1, beta in {0, 1} per problem, one exponent-bit flip in
@@ -681,6 +769,9 @@ def main():
     ap.add_argument("--sweep-dist", default="uniform", help="input distribution for --sweep")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--batched", action="store_true", help="the batched workload (512 small problems)")
+    ap.add_argument("--panel-sweep", action="store_true", help="per-k-panel verification: overhead and faults")
+    ap.add_argument("--panel-sizes", default="8192,1024", help="M = N = K of --panel-sweep")
+    ap.add_argument("--panel-slabs", default="2,8,32,128", help="k-slabs per panel check for --panel-sweep")
     ap.add_argument("--split", action="store_true", help="split-precision forms (BF16 tensor cores)")
     ap.add_argument("--split-slices", default="7,9,11", help="slice counts for --split")
     ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
@@ -698,6 +789,8 @@ def main():
         return config5(args)
     if args.sweep:
         return sweep(args)
+    if args.panel_sweep:
+        return panel_sweep(args)
     if args.split:
         if args.warmup < 3:
             args.warmup = 3

@@ -364,7 +364,8 @@ int ftgemm_selftest_wait_timeout(int64_t limit_ns, void *stream);
  * tiles over the idle SMs; a reduction kernel sums the partial tiles and runs
  * the verification on the whole tile), 1 never splits, n >= 2 forces n
  * splits of every tile (fewer when K is short).  ftgemm_d_noalloc never
- * splits; per-k-panel verification (ftgemm_set_panel_check) does not split. */
+ * splits; with per-k-panel verification (ftgemm_set_panel_check) each k-split
+ * checks the panels of its own k-range. */
 int ftgemm_set_splitk(int nsplit);
 
 /* Column panels of ftgemm_d_host: 0 (default) picks them automatically (up to
@@ -378,9 +379,8 @@ int ftgemm_set_host_panels(int panels);
  * device work): *splits k-ranges (1: none) for the tiles from
  * *first_split_tile on, in the kernels' tile order; the tiles before it run
  * whole (*first_split_tile = 0: every tile split; = the tile count: none).
- * ftgemm_d_noft plans the same way except that it ignores the per-k-panel
- * setting.  Returns 0, or -i for a bad argument i (M, N, K < 0, nsm <= 0,
- * NULL outputs). */
+ * ftgemm_d_noft plans the same way.  Returns 0, or -i for a bad argument i
+ * (M, N, K < 0, nsm <= 0, NULL outputs). */
 int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits,
                         int64_t *first_split_tile);
 
@@ -406,8 +406,9 @@ int ftgemm_set_split_engine(int engine);
  * predicted checksums of the products done so far, correcting a located
  * accumulator in place, so that faults arriving at different times stay
  * separable and are caught before they spread through the remaining sum.
- * The end-of-tile verification still runs.  0 (default) turns it off.  Such
- * calls never split K. */
+ * The end-of-tile verification still runs.  0 (default) turns it off.  In a
+ * call that splits K (grids of few tiles, ftgemm_set_splitk) each k-split
+ * checks every kslabs k-slabs of its own k-range. */
 int ftgemm_set_panel_check(int kslabs);
 
 /* Correction rule of the FP64 FT-GEMM kernels (ftgemm_d and the calls built

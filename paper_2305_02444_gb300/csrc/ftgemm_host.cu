@@ -15,31 +15,20 @@
 #include "ftgemm_encode.cuh"
 
 namespace ftg {
-// main-kernel launchers, one translation unit per operand layout
-cudaError_t launch_main_nn(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                           const Params &, cudaStream_t);
-cudaError_t launch_main_nt(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                           const Params &, cudaStream_t);
-cudaError_t launch_main_tn(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                           const Params &, cudaStream_t);
-cudaError_t launch_main_tt(bool ft, bool inj, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &,
-                           const Params &, cudaStream_t);
-cudaError_t launch_batched_nn(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
-                              int *, int *, int, cudaStream_t);
-cudaError_t launch_batched_nt(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
-                              int *, int *, int, cudaStream_t);
-cudaError_t launch_batched_tn(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
-                              int *, int *, int, cudaStream_t);
-cudaError_t launch_batched_tt(bool, bool, const BatchProblem *, const int *, const int *, const int *, int, int,
-                              int *, int *, int, cudaStream_t);
-cudaError_t launch_panel_nn(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
-                            cudaStream_t);
-cudaError_t launch_panel_nt(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
-                            cudaStream_t);
-cudaError_t launch_panel_tn(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
-                            cudaStream_t);
-cudaError_t launch_panel_tt(bool, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, const Params &,
-                            cudaStream_t);
+// FP64 kernel launchers, one translation unit per operand layout
+// (ftgemm_launch.cuh): any mode (0 whole tiles, 1 split-K partials, 2 split-K
+// reduction, 3 verify-only pass), modes 0 and 1 optionally with the
+// per-k-panel checks; and the persistent batched kernel
+#define FTG_DECLARE_LAYOUT(XX)                                                                                     \
+  cudaError_t launch_gemm_##XX(bool ft, bool inj, int mode, bool panel, const CUtensorMap &, const CUtensorMap &,  \
+                               const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);            \
+  cudaError_t launch_batched_##XX(bool, bool, const BatchProblem *, const int *, const int *, const int *, int,    \
+                                  int, int *, int *, int, cudaStream_t);
+FTG_DECLARE_LAYOUT(nn)
+FTG_DECLARE_LAYOUT(nt)
+FTG_DECLARE_LAYOUT(tn)
+FTG_DECLARE_LAYOUT(tt)
+#undef FTG_DECLARE_LAYOUT
 cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s);
 cudaError_t launch_split_tc(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
@@ -51,15 +40,6 @@ cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R
 long long bf16_checksum_scratch(long long R, long long Kp);
 cudaError_t launch_bf16_checksums(const void *X, long long R, long long Kp, void *pieces, double *rowabs,
                                   double *gmax, float *part, cudaStream_t s);
-// any mode (0 whole tiles, 1 split-K partials, 2 split-K reduction)
-cudaError_t launch_gemm_nn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
-                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
-cudaError_t launch_gemm_nt(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
-                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
-cudaError_t launch_gemm_tn(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
-                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
-cudaError_t launch_gemm_tt(bool ft, bool inj, int mode, const CUtensorMap &, const CUtensorMap &,
-                           const CUtensorMap &, const CUtensorMap &, const Params &, cudaStream_t);
 }  // namespace ftg
 
 using namespace ftg;
@@ -294,17 +274,17 @@ int choose_tail_splits(long long ntiles, long long nks, int nsm) {
 }
 
 // The k-split plan of one FP64 call: S splits (1: none) of the tiles
-// [tail_base, ntiles), the tiles before tail_base whole.  Per-k-panel
-// verification never splits.
+// [tail_base, ntiles), the tiles before tail_base whole.  (With per-k-panel
+// verification each k-split checks its own panels.)
 struct KSplit {
   int S;
   long long tail_base;
 };
-KSplit plan_ksplit(long long ntiles, long long nks, int nsm, bool panel) {
-  KSplit k{panel ? 1 : choose_splits(ntiles, nks, nsm), 0};
+KSplit plan_ksplit(long long ntiles, long long nks, int nsm) {
+  KSplit k{choose_splits(ntiles, nks, nsm), 0};
   // Large grids whose last wave is partly empty: the full waves take whole
   // tiles, the tail tiles split K over the idle SMs (then a verifying reduction).
-  if (!panel && k.S <= 1) {
+  if (k.S <= 1) {
     const int St = choose_tail_splits(ntiles, nks, nsm);
     if (St > 1) {
       k.S = St;
@@ -726,24 +706,19 @@ int gemm_impl(char transA, char transB, long long M, long long N, long long K, d
     }
   }
   const bool panel = ft && g_panel > 0 && nks > g_panel;
-  const KSplit ksp = plan_ksplit(ntiles, nks, w.nsm, panel);
+  const KSplit ksp = plan_ksplit(ntiles, nks, w.nsm);
   int S = ksp.S;
   const long long tail_base = ksp.tail_base, tail_count = ntiles - ksp.tail_base;
   p.panel_slabs = panel ? g_panel : 0;
   cudaError_t e;
   auto launch = [&](int mode, const CUtensorMap &mW) {
-    if (!ta_t && !tb_t) return launch_gemm_nn(ft, inj, mode, mA, mB, mC, mW, p, s);
-    if (!ta_t && tb_t) return launch_gemm_nt(ft, inj, mode, mA, mB, mC, mW, p, s);
-    if (ta_t && !tb_t) return launch_gemm_tn(ft, inj, mode, mA, mB, mC, mW, p, s);
-    return launch_gemm_tt(ft, inj, mode, mA, mB, mC, mW, p, s);
+    const bool pk = panel && mode < 2;  // the panel checks run in the kernels with a k-loop
+    if (!ta_t && !tb_t) return launch_gemm_nn(ft, inj, mode, pk, mA, mB, mC, mW, p, s);
+    if (!ta_t && tb_t) return launch_gemm_nt(ft, inj, mode, pk, mA, mB, mC, mW, p, s);
+    if (ta_t && !tb_t) return launch_gemm_tn(ft, inj, mode, pk, mA, mB, mC, mW, p, s);
+    return launch_gemm_tt(ft, inj, mode, pk, mA, mB, mC, mW, p, s);
   };
-  if (panel) {
-    if (!ta_t && !tb_t) e = launch_panel_nn(inj, mA, mB, mC, p, s);
-    else if (!ta_t && tb_t) e = launch_panel_nt(inj, mA, mB, mC, p, s);
-    else if (ta_t && !tb_t) e = launch_panel_tn(inj, mA, mB, mC, p, s);
-    else e = launch_panel_tt(inj, mA, mB, mC, p, s);
-    g_launches++;
-  } else if (S <= 1) {
+  if (S <= 1) {
     e = launch(0, mC);
     g_launches++;
   } else {
@@ -1135,10 +1110,10 @@ int ftgemm_d_unfused(char transA, char transB, int64_t M, int64_t N, int64_t K, 
   p.nsplit = 1;
   cudaMemsetAsync(w.rep.p, 0, sizeof(DevReport), s);
   cudaError_t e;
-  if (!ta_t && !tb_t) e = launch_gemm_nn(true, false, 3, mC, mC, mC, mC, p, s);
-  else if (!ta_t && tb_t) e = launch_gemm_nt(true, false, 3, mC, mC, mC, mC, p, s);
-  else if (ta_t && !tb_t) e = launch_gemm_tn(true, false, 3, mC, mC, mC, mC, p, s);
-  else e = launch_gemm_tt(true, false, 3, mC, mC, mC, mC, p, s);
+  if (!ta_t && !tb_t) e = launch_gemm_nn(true, false, 3, false, mC, mC, mC, mC, p, s);
+  else if (!ta_t && tb_t) e = launch_gemm_nt(true, false, 3, false, mC, mC, mC, mC, p, s);
+  else if (ta_t && !tb_t) e = launch_gemm_tn(true, false, 3, false, mC, mC, mC, mC, p, s);
+  else e = launch_gemm_tt(true, false, 3, false, mC, mC, mC, mC, p, s);
   g_launches++;
   if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
   if (rep) return copy_report(w, rep, s);
@@ -1269,7 +1244,7 @@ int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits, i
     *first_split_tile = ntiles;
     return 0;
   }
-  const KSplit k = plan_ksplit(ntiles, nks, nsm, g_panel > 0 && nks > g_panel);
+  const KSplit k = plan_ksplit(ntiles, nks, nsm);
   *splits = k.S;
   *first_split_tile = k.S > 1 ? k.tail_base : ntiles;
   return 0;
@@ -1534,10 +1509,10 @@ extern "C" int ftgemm_d_noalloc(char transA, char transB, int64_t M, int64_t N, 
   p.wait_limit_ns = wait_limit_ns();
   p.correct_mode = g_correct;
   cudaError_t e;
-  if (!ta_t && !tb_t) e = launch_main_nn(true, false, mA, mB, mC, p, s);
-  else if (!ta_t && tb_t) e = launch_main_nt(true, false, mA, mB, mC, p, s);
-  else if (ta_t && !tb_t) e = launch_main_tn(true, false, mA, mB, mC, p, s);
-  else e = launch_main_tt(true, false, mA, mB, mC, p, s);
+  if (!ta_t && !tb_t) e = launch_gemm_nn(true, false, 0, false, mA, mB, mC, mC, p, s);
+  else if (!ta_t && tb_t) e = launch_gemm_nt(true, false, 0, false, mA, mB, mC, mC, p, s);
+  else if (ta_t && !tb_t) e = launch_gemm_tn(true, false, 0, false, mA, mB, mC, mC, p, s);
+  else e = launch_gemm_tt(true, false, 0, false, mA, mB, mC, mC, p, s);
   g_launches++;
   if (e != cudaSuccess) return FTGEMM_ERR_CUDA;
 

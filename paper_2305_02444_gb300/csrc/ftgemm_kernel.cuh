@@ -438,6 +438,12 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     compute_sync();
     if (tid == 0) {
       tma_store_3d(tmW, smem_u32(sC), 0, 0, split * wcount + (tile - p.tile_base));
+      if (PANEL && cnt[C_PDET]) {  // faults this split's panel checks corrected
+        DevReport *r = p.rep;
+        atomicAdd(&r->detected, (unsigned long long)cnt[C_PDET]);
+        atomicAdd(&r->corrected, (unsigned long long)cnt[C_PDET]);
+        atomicAdd(&r->panel_detected, (unsigned long long)cnt[C_PDET]);
+      }
       bulk_commit();
       bulk_wait_all();
     }

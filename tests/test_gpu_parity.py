@@ -547,11 +547,37 @@ def test_panel_check_catches_faults_early_and_separately(ft, orc):
     flips = [(10, 20, 3, 60), (10, 20, 27, 58), (200, 100, 5, 61), (130, 7, 62, 59)]
     assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
     try:
-        with panel(ft, 8):
+        with panel(ft, 8), splitk(ft, 1):
             rc, rep, out = run_gpu(ft, P, 1.0, 1.0)
     finally:
         ft.ftgemm_set_injection(mode=0)
     assert rc == 0
+    assert_parity(orc, P, out, ref, E)
+    assert rep["detected"] == 4 and rep["panel_detected"] == 3
+    kinds = sorted((l[0], l[1], l[3]) for l in rep["locs"])
+    assert kinds == [(10, 20, 2), (10, 20, 2), (130, 7, 0), (200, 100, 2)]
+
+
+def test_panel_check_inside_k_splits(ft, orc):
+    """The same problem split in two k-ranges of 32 k-slabs (the partial
+    kernels check their own panels of 8 slabs, at local slabs 8, 16, 24): a
+    fault in each split is corrected at the next panel boundary of its split
+    (kind 2, over the split's own products), a fault after the last boundary
+    of split 1 is left to the verifying reduction (kind 0); the log records
+    the split's first product; the result is within the parity bound."""
+    P = make_problem("N", "N", 256, 256, 1024, seed=505)
+    ref, E = oracle_ref(orc, P, 1.0, 1.0)
+    flips = [(10, 20, 3, 60), (10, 20, 40, 58), (200, 100, 5, 61), (130, 7, 62, 59)]
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        with panel(ft, 8), splitk(ft, 2):
+            rc, rep, out = run_gpu(ft, P, 1.0, 1.0)
+        log = ft.ftgemm_injection_log()
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    assert rc == 0
+    check_log_against_oracle(orc, P, flips, log)
+    assert [L["kfirst"] for L in log] == [0, 512, 0, 512]
     assert_parity(orc, P, out, ref, E)
     assert rep["detected"] == 4 and rep["panel_detected"] == 3
     kinds = sorted((l[0], l[1], l[3]) for l in rep["locs"])
