@@ -273,7 +273,7 @@ def flip_accounting(log, rep, A, B, Cin, out_at, tm: int = 128, tn: int = 128):
                                      "below: < min/4; corrected elements checked against the oracle"}}
 
 
-SPLIT_ENGINES = {"tc": 2, "mma": 1, "tcp": 5}   # ftgemm_set_split_engine codes
+SPLIT_ENGINES = {"tc": 2, "mma": 1, "tcp": 5, "i8": 7}   # ftgemm_set_split_engine codes
 METRIC = "FT-GEMM TFLOP/s (FP64) & % FP64 peak; ABFT overhead % vs plain; errors fixed"
 
 
@@ -573,9 +573,9 @@ def split(args):
     engines = [e for e in args.split_engine.split(",") if e]
     forms = [("fp64_dfma", None, 1, None)]
     for eng in engines:
-        sfx = {"tc": "", "mma": "_mma", "tcp": "_tcp"}[eng]
+        sfx = {"tc": "", "mma": "_mma", "tcp": "_tcp", "i8": "_i8"}[eng]
         forms += [(f"emulated_S{S}_fp64ck{sfx}", S, 2, eng) for S in args.split_slices]
-        if eng != "mma":    # the plain form with FP32-carried checksums on the tcgen05 engines
+        if eng not in ("mma", "i8"):    # the plain form with FP32-carried checksums on the tcgen05 engines
             forms += [(f"bf16_plain_fp32ck{sfx}", 0, 1, eng)]
     forms += [(f"emulated_S{S}_fp32ck_mma", S, 1, "mma") for S in args.split_slices] + \
         [("bf16_plain_fp32ck_mma", 0, 1, "mma")]
@@ -626,14 +626,18 @@ def split(args):
                      "flips": nflip, "detected": rep["detected"], "rc": rc,
                      "slices": S, "pairs": npairs if S else (1 if S == 0 else None),
                      "checksums": "fp64" if (S is None or ck == 2) else ("fp32" if ck == 1 else "none"),
-                     "engine": "dfma" if S is None else ("mma.sync" if (eng == "mma" or (ck == 1 and S != 0))
+                     "engine": "dfma" if S is None else ("mma.sync_int8" if eng == "i8" else
+                                                         "mma.sync" if (eng == "mma" or (ck == 1 and S != 0))
                                                          else "tcgen05" if eng == "tc" else "tcgen05_persistent"),
                      "unprotected_kernel_ms": kms}
         if S is not None:
-            # tensor work of the unprotected kernel: every kept pair is a 2MNK bf16 product
+            # tensor work of the unprotected kernel: every kept pair is a 2MNK bf16 (or int8) product
             tf = npairs * flops / (kms / 1e3) / 1e12
-            res[name]["kernel_bf16_tflops"] = tf
-            res[name]["kernel_frac_of_bf16_peak"] = tf / peaks["bf16_tflops"]
+            if eng == "i8":
+                res[name]["kernel_int8_tops"] = tf
+            else:
+                res[name]["kernel_bf16_tflops"] = tf
+                res[name]["kernel_frac_of_bf16_peak"] = tf / peaks["bf16_tflops"]
         print(json.dumps({name: res[name]}), flush=True)
     base = res["fp64_dfma"]["tflops_fp64_equiv"] if "fp64_dfma" in res else float("nan")
     line = {"metric": "split-precision FT-GEMM TFLOP/s (FP64-equivalent, 2MNK) and max error vs FP64 oracle",
@@ -777,7 +781,7 @@ def main():
     ap.add_argument("--split-rows", type=int, default=4, help="rows checked against the oracle")
     ap.add_argument("--split-engine", default="tc,mma",
                     help="split engines: tc (tcgen05, one CTA per tile), tcp (persistent tcgen05), "
-                         "mma (mma.sync)")
+                         "mma (mma.sync), i8 (mma.sync with INT8 slices)")
     ap.add_argument("--split-forms", default="", help="comma list of form names to run (default: all)")
     ap.add_argument("--config5", action="store_true", help="32768^3 normal(0,1), beta 1, flips at a rate")
     ap.add_argument("--flip-rate", type=float, default=360.0, help="flips per minute for --config5")

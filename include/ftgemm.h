@@ -396,6 +396,11 @@ int ftgemm_query_ksplit(int64_t M, int64_t N, int64_t K, int nsm, int *splits,
  * 1: every call on the mma.sync kernel.  The emulated forms with ft = 1 (FP32
  * checksums summed from the staged slices on the CUDA cores) always run on
  * the mma.sync kernel; the plain form with ft = 1 runs on the engine chosen.
+ * 7: the emulated forms with INT8 slices on the mma.sync kernel (m16n8k32 s8
+ *    MMAs; 7 bits per slice, exact INT32 sums over up to 133 120 products;
+ *    ft 0 or 2, ft = 1 returns -15); a row of op(A) or column of op(B) that
+ *    holds Inf or NaN is multiplied in FP64 instead (INT8 cannot carry it);
+ *    the plain form runs as on engine 1.
  * Every CTA loads its own operand tiles (no thread-block clusters, no TMA
  * multicast).  Process-global; returns -1 for another value. */
 int ftgemm_set_split_engine(int engine);

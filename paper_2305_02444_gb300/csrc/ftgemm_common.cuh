@@ -94,6 +94,10 @@ constexpr int SP_STAGES = 4;
 constexpr int SP_A_BYTES = SP_BM * SP_BK * 2, SP_B_BYTES = SP_BN * SP_BK * 2;  // 16 KiB each
 constexpr int SP_STAGE_BYTES = SP_A_BYTES + SP_B_BYTES;
 constexpr int SP_MAX_PAIRS = 128;
+// INT8 slices: the row exponent of a row (column) of op(A) (op(B)) that
+// holds a non-finite entry, whose products the kernel recomputes in FP64
+constexpr int SPLIT_NONFINITE_ROW = -(1 << 20);
+constexpr int SP_BK_I8 = 128;  // INT8 k-slab: 128 bytes per row, like the bf16 slab
 constexpr int SP_RED_DOUBLES = (4 + 2) * 3 * 128 + 8;  // epilogue scratch of the split kernels
 constexpr int SP_SMEM_BYTES = SP_STAGES * SP_STAGE_BYTES + 4 * SP_BK * 4 + 4 * 128 * 8 + 2 * 128 * 4 + 256 +
                               2 * SP_STAGES * 8 + SP_RED_DOUBLES * 8 + 1024;
@@ -138,6 +142,9 @@ struct SplitParams {
   const uint16_t *Ab, *Bb;
   long long ldk;
   long long p1_lo, p2_lo;
+  // INT8 slices (mma.sync s8): rows / columns marked SPLIT_NONFINITE_ROW in
+  // eA / eB are recomputed in FP64
+  int i8;
 };
 
 

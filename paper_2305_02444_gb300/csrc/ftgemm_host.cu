@@ -29,14 +29,15 @@ FTG_DECLARE_LAYOUT(nt)
 FTG_DECLARE_LAYOUT(tn)
 FTG_DECLARE_LAYOUT(tt)
 #undef FTG_DECLARE_LAYOUT
-cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
+cudaError_t launch_split(bool ta, bool tb, int ck, bool i8, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s);
 cudaError_t launch_split_tc(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                             const SplitParams &p, cudaStream_t s);
 cudaError_t launch_split_tcp(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
                              const SplitParams &p, int nctas, cudaStream_t s);
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
-                           int S, int w, int plain, void *out, unsigned long long *mb, int nsm, cudaStream_t s);
+                           int S, int w, int plain, int i8, void *out, unsigned long long *mb, int nsm,
+                           cudaStream_t s);
 long long bf16_checksum_scratch(long long R, long long Kp);
 cudaError_t launch_bf16_checksums(const void *X, long long R, long long Kp, void *pieces, double *rowabs,
                                   double *gmax, float *part, cudaStream_t s);
@@ -221,7 +222,7 @@ bool tma_ok(const void *p, long long ld) {
 int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
 
 // split precision: 0 default (persistent tcgen05), 1 mma.sync, 2 tcgen05 with one CTA per tile,
-// 5 persistent tcgen05
+// 5 persistent tcgen05, 7 mma.sync with INT8 slices
 int g_split_engine = 0;
 int g_correct = 0;  // correction rule of the FP64 kernels (ftgemm_set_correction)
 int g_splitk = 0;  // 0 automatic, 1 never split, n >= 2 force n splits (ftgemm_set_splitk)
@@ -1218,7 +1219,7 @@ int ftgemm_set_panel_check(int kslabs) {
 
 int ftgemm_set_split_engine(int engine) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (engine != 0 && engine != 1 && engine != 2 && engine != 5) return -1;
+  if (engine != 0 && engine != 1 && engine != 2 && engine != 5 && engine != 7) return -1;
   g_split_engine = engine;
   return 0;
 }
@@ -1973,14 +1974,19 @@ int ftgemm_batched(int64_t count, const char *transA, const char *transB, const 
 // Split-precision FT-GEMM (BF16 tensor cores; see ftgemm_split.cuh).
 namespace {
 
-int make_map_slices(CUtensorMap *m, const void *ptr, long long Kp, long long R, long long S, int box_rows) {
+// 3-D map {Kp, R, S} of slices: bf16, or bytes (INT8 slices, i8); the box is
+// one 128-byte row of k by box_rows rows, with the 128-byte swizzle.
+int make_map_slices(CUtensorMap *m, const void *ptr, long long Kp, long long R, long long S, int box_rows,
+                    bool i8 = false) {
   auto fn = encode_fn();
   if (!fn) return FTGEMM_ERR_TENSORMAP;
+  const long long esz = i8 ? 1 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)R, (cuuint64_t)S};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)R * Kp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)SP_BK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * esz), (cuuint64_t)(R * Kp * esz)};
+  cuuint32_t box[3] = {(cuuint32_t)(i8 ? SP_BK_I8 : SP_BK), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+  CUresult r = fn(m, i8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                  const_cast<void *>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : FTGEMM_ERR_TENSORMAP;
@@ -2011,17 +2017,25 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   const bool ta_t = is_t(transA), tb_t = is_t(transB);
   const bool plain = nslices == 0;
   const int S = plain ? 1 : nslices;
-  const long long Kp = (K + SP_BK - 1) / SP_BK * SP_BK;
-  // bits per slice: the FP32 accumulation of a pair stays exact over kchunk products
+  // INT8 slices (engine 7, emulated forms): 7 bits each, exact INT32 sums
+  const bool i8 = g_split_engine == 7 && !plain;
+  if (i8 && ft == 1) return -15;
+  const long long sbk = i8 ? SP_BK_I8 : SP_BK, esz = i8 ? 1 : 2;
+  const long long Kp = (K + sbk - 1) / sbk * sbk;
+  // bits per slice: the FP32 (INT32) accumulation of a pair stays exact over
+  // kchunk products
   int wbits = 0;
   long long kchunk = Kp;
-  if (!plain) {
+  if (i8) {
+    wbits = 7;
+    kchunk = std::min<long long>(Kp, ((1LL << 31) - 1) / (127 * 127) / SP_BK_I8 * SP_BK_I8);
+  } else if (!plain) {
     wbits = K <= 256 ? 8 : K <= 1024 ? 7 : K <= 4096 ? 6 : 5;
     const long long lim = (1LL << 24) / (((1LL << wbits) - 1) * ((1LL << wbits) - 1));
     kchunk = std::max<long long>(SP_BK, lim / SP_BK * SP_BK);
   }
   const long long nI = (M + SP_BM - 1) / SP_BM, nJ = (N + SP_BN - 1) / SP_BN;
-  if (ensure(w.spA, (size_t)S * M * Kp * 2) || ensure(w.spB, (size_t)S * N * Kp * 2) ||
+  if (ensure(w.spA, (size_t)(S * M * Kp * esz)) || ensure(w.spB, (size_t)(S * N * Kp * esz)) ||
       ensure(w.spEA, sizeof(int) * M) || ensure(w.spEB, sizeof(int) * N))
     return FTGEMM_ERR_NOMEM;
   if (plain) {
@@ -2033,7 +2047,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   // tcgen05 kernels (ft 0 / 2, and the plain form with ft 1) or the mma.sync
   // kernel; ck: the kernels' check mode (2: verification against the
   // checksum products P1 / P2 computed before the product)
-  const bool tc = g_split_engine != 1 && (ft != 1 || plain);
+  const bool tc = !i8 && g_split_engine != 1 && g_split_engine != 7 && (ft != 1 || plain);
   const int ck = tc ? (ft ? 2 : 0) : ft;
   // the plain form on tcgen05 with checks: P1 / P2 are plain BF16 products of
   // the two bf16 pieces of the checksum vectors (P1 with 2 nI rows, P2 with
@@ -2058,11 +2072,12 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   }
   // op(A)(i, k): 'T' has k contiguous; op(B)(k, j) seen as row j: 'N' has k contiguous
   const int nsm = device_sms(dev);
-  if (ensure(w.spMB, sizeof(unsigned long long) * (size_t)std::max(M, N))) return FTGEMM_ERR_NOMEM;
+  if (ensure(w.spMB, (sizeof(unsigned long long) + sizeof(unsigned int)) * (size_t)std::max(M, N)))
+    return FTGEMM_ERR_NOMEM;
   unsigned long long *mb = (unsigned long long *)w.spMB.p;
-  if (launch_slicing(A, lda, ta_t ? 1 : 0, M, K, Kp, (int *)w.spEA.p, S, wbits, plain, w.spA.p, mb, nsm, s) !=
+  if (launch_slicing(A, lda, ta_t ? 1 : 0, M, K, Kp, (int *)w.spEA.p, S, wbits, plain, i8, w.spA.p, mb, nsm, s) !=
           cudaSuccess ||
-      launch_slicing(B, ldb, tb_t ? 0 : 1, N, K, Kp, (int *)w.spEB.p, S, wbits, plain, w.spB.p, mb, nsm, s) !=
+      launch_slicing(B, ldb, tb_t ? 0 : 1, N, K, Kp, (int *)w.spEB.p, S, wbits, plain, i8, w.spB.p, mb, nsm, s) !=
           cudaSuccess)
     return FTGEMM_ERR_CUDA;
   g_launches += plain ? 2 : 4;
@@ -2076,7 +2091,8 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     return launch_split_tc(ta, tb, ck, a, b, q, st);
   };
   CUtensorMap mA, mB;
-  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S, SP_BM)) || (rc = make_map_slices(&mB, w.spB.p, Kp, N, S, SP_BN)))
+  if ((rc = make_map_slices(&mA, w.spA.p, Kp, M, S, SP_BM, i8)) ||
+      (rc = make_map_slices(&mB, w.spB.p, Kp, N, S, SP_BN, i8)))
     return rc;
 
   SplitParams p;
@@ -2091,6 +2107,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
   p.eA = (const int *)w.spEA.p; p.eB = (const int *)w.spEB.p;
   p.A = A; p.B = B; p.lda = lda; p.ldb = ldb; p.ta = ta_t; p.tb = tb_t;
   p.C = C; p.ldc = ldc; p.nI = (int)nI; p.nJ = (int)nJ;
+  p.i8 = i8 ? 1 : 0;
   p.rep = (DevReport *)w.rep.p; p.loc = (DevLoc *)w.loc.p; p.loc_cap = LOC_CAP_DEV;
   p.wait_limit_ns = wait_limit_ns();
   p.verify = ft;
@@ -2157,9 +2174,9 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
       if (ensure(w.spPA, (size_t)S * nI * Kp * 2) || ensure(w.spPB, (size_t)S * nJ * Kp * 2) ||
           ensure(w.spEPA, sizeof(int) * nI) || ensure(w.spEPB, sizeof(int) * nJ))
         return FTGEMM_ERR_NOMEM;
-      if (launch_slicing((const double *)w.acs.p, Kq, 1, nI, K, Kp, (int *)w.spEPA.p, S, wbits, 0, w.spPA.p, mb,
+      if (launch_slicing((const double *)w.acs.p, Kq, 1, nI, K, Kp, (int *)w.spEPA.p, S, wbits, 0, 0, w.spPA.p, mb,
                          nsm, s) != cudaSuccess ||
-          launch_slicing((const double *)w.bcs.p, Kq, 1, nJ, K, Kp, (int *)w.spEPB.p, S, wbits, 0, w.spPB.p, mb,
+          launch_slicing((const double *)w.bcs.p, Kq, 1, nJ, K, Kp, (int *)w.spEPB.p, S, wbits, 0, 0, w.spPB.p, mb,
                          nsm, s) != cudaSuccess)
         return FTGEMM_ERR_CUDA;
       g_launches += 4;
@@ -2214,7 +2231,7 @@ extern "C" int ftgemm_d_split(char transA, char transB, int64_t M, int64_t N, in
     timing_record(g_tim.main_ev, &em0, &em1);
     cudaEventRecord(em0, s);
   }
-  if ((tc ? run_tc(ta_t, tb_t, ck, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, mA, mB, p, s)) !=
+  if ((tc ? run_tc(ta_t, tb_t, ck, mA, mB, p, s) : launch_split(ta_t, tb_t, ft, i8, mA, mB, p, s)) !=
       cudaSuccess)
     return FTGEMM_ERR_CUDA;
   if (g_tim.on) cudaEventRecord(em1, s);

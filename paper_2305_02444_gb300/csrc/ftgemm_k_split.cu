@@ -9,27 +9,33 @@
 
 namespace ftg {
 
-template <bool TA, bool TB, int CK>
+template <bool TA, bool TB, int CK, bool I8>
 static cudaError_t launch_split_variant(const CUtensorMap &a, const CUtensorMap &b, const SplitParams &p,
                                         cudaStream_t s) {
-  auto k = ftsplit_kernel<TA, TB, CK>;
+  auto k = ftsplit_kernel<TA, TB, CK, I8>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SP_SMEM_BYTES);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)p.nI * (unsigned)p.nJ, 256, SP_SMEM_BYTES, s>>>(a, b, p);
   return cudaGetLastError();
 }
 
-template <int CK>
+template <int CK, bool I8 = false>
 static cudaError_t launch_split_ck(bool ta, bool tb, const CUtensorMap &a, const CUtensorMap &b,
                                    const SplitParams &p, cudaStream_t s) {
-  if (!ta && !tb) return launch_split_variant<false, false, CK>(a, b, p, s);
-  if (!ta && tb) return launch_split_variant<false, true, CK>(a, b, p, s);
-  if (ta && !tb) return launch_split_variant<true, false, CK>(a, b, p, s);
-  return launch_split_variant<true, true, CK>(a, b, p, s);
+  if (!ta && !tb) return launch_split_variant<false, false, CK, I8>(a, b, p, s);
+  if (!ta && tb) return launch_split_variant<false, true, CK, I8>(a, b, p, s);
+  if (ta && !tb) return launch_split_variant<true, false, CK, I8>(a, b, p, s);
+  return launch_split_variant<true, true, CK, I8>(a, b, p, s);
 }
 
-cudaError_t launch_split(bool ta, bool tb, int ck, const CUtensorMap &a, const CUtensorMap &b,
+// ck: 0 no checks, 1 FP32 checksums in the kernel, 2 FP64 checksums computed
+// before it; i8: INT8 slices (ck 0 or 2)
+cudaError_t launch_split(bool ta, bool tb, int ck, bool i8, const CUtensorMap &a, const CUtensorMap &b,
                          const SplitParams &p, cudaStream_t s) {
+  if (i8) {
+    if (ck == 1) return cudaErrorInvalidValue;
+    return ck == 2 ? launch_split_ck<2, true>(ta, tb, a, b, p, s) : launch_split_ck<0, true>(ta, tb, a, b, p, s);
+  }
   if (ck == 1) return launch_split_ck<1>(ta, tb, a, b, p, s);
   if (ck == 2) return launch_split_ck<2>(ta, tb, a, b, p, s);
   return launch_split_ck<0>(ta, tb, a, b, p, s);
@@ -62,9 +68,11 @@ __device__ __forceinline__ int exponent_above(unsigned long long mb) {
 // flight per thread.
 __global__ void __launch_bounds__(256) split_rowmax_kernel(const double *__restrict__ X, long long ld, int trans,
                                                            long long R, long long K, long long kper,
-                                                           unsigned long long *__restrict__ mb) {
+                                                           unsigned long long *__restrict__ mb,
+                                                           unsigned int *__restrict__ nf) {
   const long long k0 = (long long)blockIdx.y * kper, k1 = min(K, k0 + kper);
   unsigned long long m = 0;
+  bool bad = false;  // a non-finite entry in this part of the row
   long long r;
   if (!trans) {
     r = (long long)blockIdx.x * 256 + threadIdx.x;
@@ -76,9 +84,15 @@ __global__ void __launch_bounds__(256) split_rowmax_kernel(const double *__restr
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = x[(k + u) * ld];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) m = max(m, abs_bits_finite(v[u]));
+      for (int u = 0; u < 8; ++u) {
+        m = max(m, abs_bits_finite(v[u]));
+        bad = bad || !isfinite(v[u]);
+      }
     }
-    for (; k < k1; ++k) m = max(m, abs_bits_finite(x[k * ld]));
+    for (; k < k1; ++k) {
+      m = max(m, abs_bits_finite(x[k * ld]));
+      bad = bad || !isfinite(x[k * ld]);
+    }
   } else {
     r = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -90,14 +104,22 @@ __global__ void __launch_bounds__(256) split_rowmax_kernel(const double *__restr
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = x[k + 32 * u];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) m = max(m, abs_bits_finite(v[u]));
+      for (int u = 0; u < 8; ++u) {
+        m = max(m, abs_bits_finite(v[u]));
+        bad = bad || !isfinite(v[u]);
+      }
     }
-    for (; k < k1; k += 32) m = max(m, abs_bits_finite(x[k]));
+    for (; k < k1; k += 32) {
+      m = max(m, abs_bits_finite(x[k]));
+      bad = bad || !isfinite(x[k]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, m, o));
+    bad = __any_sync(0xffffffffu, bad);
     if (lane != 0) return;
   }
   if (m) atomicMax(mb + r, m);
+  if (bad && nf) atomicOr(nf + r, 1u);
 }
 
 // floor(m 2^t) mod 2^64 for the 53-bit integer m and any t.
@@ -145,6 +167,17 @@ __device__ __forceinline__ uint32_t slice_bits(const SliceIn &q, int w, int S, i
   return q.sg | (__float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | n), 8388608.0f)) >> 16);
 }
 
+// INT8 form of slice s: the w-bit field (w <= 7) with the entry's sign, as a
+// two's-complement byte; a non-finite entry gives 0 (its row is recomputed
+// in FP64 by the product kernel, which INT8 slices cannot carry Inf / NaN to).
+__device__ __forceinline__ uint32_t slice_i8(const SliceIn &q, int w, int S, int S1, int s) {
+  if (q.nfb) return 0u;
+  const unsigned long long f = s < S1 ? q.f1 : q.f2;
+  const int c = s < S1 ? w * (S1 - 1 - s) : w * (S - 1 - s);
+  const int n = (int)((uint32_t)(f >> c) & ((1u << w) - 1u));
+  return (uint32_t)(uint8_t)(int8_t)(q.sg ? -n : n);
+}
+
 // Slices: out[s][r][k] (bf16, row length Kp, zero padded past K); plain: the
 // bf16 rounding of each entry.  The row exponent e(r) (max |op(X)(r, :)| <
 // 2^e(r), 0 for a zero row) comes from the row maxima mb and is written to e
@@ -155,13 +188,17 @@ __device__ __forceinline__ uint32_t slice_bits(const SliceIn &q, int w, int S, i
 //     store per slice), a warp reads 32 consecutive rows per k; the 8 warps
 //     take the 8 8-k groups of a 64-k block.
 // Eight loads in flight per thread.
-template <int trans, int plain>
+// I8: INT8 slices (bytes) instead of bf16, and e[r] = SPLIT_NONFINITE_ROW
+// for a row with a non-finite entry (nf, from the row-maxima pass).
+template <int trans, int plain, bool I8 = false>
 __global__ void __launch_bounds__(256) split_slice_kernel(const double *__restrict__ X, long long ld, long long R,
                                                           long long K, long long Kp,
                                                           const unsigned long long *__restrict__ mb,
+                                                          const unsigned int *__restrict__ nf,
                                                           int *__restrict__ e, int S, int w,
                                                           __nv_bfloat16 *__restrict__ out) {
   uint16_t *o16 = reinterpret_cast<uint16_t *>(out);
+  uint8_t *o8 = reinterpret_cast<uint8_t *>(out);
   const long long RK = R * Kp;
   const int ns = plain ? 1 : S;
   if constexpr (trans != 0) {
@@ -169,7 +206,7 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const double *__restri
     const int lane = threadIdx.x & 31;
     if (r >= R) return;
     const int er = plain ? 0 : exponent_above(mb[r]);
-    if (!plain && blockIdx.x == 0 && lane == 0) e[r] = er;
+    if (!plain && blockIdx.x == 0 && lane == 0) e[r] = (I8 && nf[r]) ? SPLIT_NONFINITE_ROW : er;
     const long long kb = (long long)blockIdx.x * 256 + 2 * lane;  // k of span u: kb + 64 u
     const double *x = X + r * ld;
     double v[8];
@@ -195,7 +232,11 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const double *__restri
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const long long k = kb + 64 * u;
-          if (k < Kp)
+          if (k >= Kp) continue;
+          if constexpr (I8)
+            *reinterpret_cast<uint16_t *>(o8 + s * RK + r * Kp + k) =
+                (uint16_t)(slice_i8(q[2 * u], w, S, S1, s) | (slice_i8(q[2 * u + 1], w, S, S1, s) << 8));
+          else
             *reinterpret_cast<uint32_t *>(o16 + s * RK + r * Kp + k) =
                 slice_bits(q[2 * u], w, S, S1, s) | (slice_bits(q[2 * u + 1], w, S, S1, s) << 16);
         }
@@ -206,7 +247,7 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const double *__restri
     const int g = threadIdx.x >> 5;
     if (r >= R) return;
     const int er = plain ? 0 : exponent_above(mb[r]);
-    if (!plain && blockIdx.x == 0 && g == 0) e[r] = er;
+    if (!plain && blockIdx.x == 0 && g == 0) e[r] = (I8 && nf[r]) ? SPLIT_NONFINITE_ROW : er;
     const long long k0 = (long long)blockIdx.x * 64 + 8 * g;
     const double *x = X + r;
     double v[8];
@@ -224,11 +265,20 @@ __global__ void __launch_bounds__(256) split_slice_kernel(const double *__restri
 #pragma unroll
       for (int u = 0; u < 8; ++u) q[u] = slice_prep(v[u], er, w, S, S1);
       for (int s = 0; s < ns; ++s) {
-        uint32_t h[4];
+        if constexpr (I8) {
+          uint32_t h[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          h[u] = slice_bits(q[2 * u], w, S, S1, s) | (slice_bits(q[2 * u + 1], w, S, S1, s) << 16);
-        dst[s * (RK / 8)] = make_uint4(h[0], h[1], h[2], h[3]);
+          for (int u = 0; u < 2; ++u)
+            h[u] = slice_i8(q[4 * u], w, S, S1, s) | (slice_i8(q[4 * u + 1], w, S, S1, s) << 8) |
+                   (slice_i8(q[4 * u + 2], w, S, S1, s) << 16) | (slice_i8(q[4 * u + 3], w, S, S1, s) << 24);
+          *reinterpret_cast<uint2 *>(o8 + s * RK + r * Kp + k0) = make_uint2(h[0], h[1]);  // 8-byte aligned
+        } else {
+          uint32_t h[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            h[u] = slice_bits(q[2 * u], w, S, S1, s) | (slice_bits(q[2 * u + 1], w, S, S1, s) << 16);
+          dst[s * (RK / 8)] = make_uint4(h[0], h[1], h[2], h[3]);
+        }
       }
     }
   }
@@ -347,30 +397,35 @@ cudaError_t launch_bf16_checksums(const void *X, long long R, long long Kp, void
 }
 
 // Row exponents (unless plain) and slices of op(X) (R x K, padded to Kp);
-// mb: R words of device scratch for the row maxima; nsm: the SM count (sizes
-// the k-split of the maxima pass).
+// i8: INT8 slices (Kp a multiple of 128) with non-finite rows marked in e.
+// mb: device scratch of 12 R bytes (the row maxima, then the rows' non-finite
+// flags); nsm: the SM count (sizes the k-split of the maxima pass).
 cudaError_t launch_slicing(const double *X, long long ld, int trans, long long R, long long K, long long Kp, int *e,
-                           int S, int w, int plain, void *out, unsigned long long *mb, int nsm, cudaStream_t s) {
+                           int S, int w, int plain, int i8, void *out, unsigned long long *mb, int nsm,
+                           cudaStream_t s) {
   if (R <= 0) return cudaSuccess;
+  unsigned int *nf = reinterpret_cast<unsigned int *>(mb + R);
   if (!plain) {
-    cudaError_t err = cudaMemsetAsync(mb, 0, sizeof(unsigned long long) * (size_t)R, s);
+    cudaError_t err = cudaMemsetAsync(mb, 0, (sizeof(unsigned long long) + sizeof(unsigned int)) * (size_t)R, s);
     if (err != cudaSuccess) return err;
     // enough warps to cover every SM several times over, k-ranges of at least 64
     const long long rows_per_block = trans ? 8 : 256, bx = (R + rows_per_block - 1) / rows_per_block;
     const long long want = (long long)nsm * 8, ksplit = std::max(1LL, std::min((K + 63) / 64, (want + bx - 1) / bx));
     const long long kper = (K + ksplit - 1) / ksplit;
     split_rowmax_kernel<<<dim3((unsigned)bx, (unsigned)((K + kper - 1) / kper)), 256, 0, s>>>(X, ld, trans, R, K,
-                                                                                             kper, mb);
+                                                                                             kper, mb, nf);
   }
   __nv_bfloat16 *o = (__nv_bfloat16 *)out;
   if (trans) {
     dim3 grid((unsigned)((Kp + 255) / 256), (unsigned)((R + 7) / 8));
-    if (plain) split_slice_kernel<1, 1><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
-    else split_slice_kernel<1, 0><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
+    if (plain) split_slice_kernel<1, 1><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, nf, e, S, w, o);
+    else if (i8) split_slice_kernel<1, 0, true><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, nf, e, S, w, o);
+    else split_slice_kernel<1, 0><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, nf, e, S, w, o);
   } else {
     dim3 grid((unsigned)(Kp / 64), (unsigned)((R + 31) / 32));
-    if (plain) split_slice_kernel<0, 1><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
-    else split_slice_kernel<0, 0><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, e, S, w, o);
+    if (plain) split_slice_kernel<0, 1><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, nf, e, S, w, o);
+    else if (i8) split_slice_kernel<0, 0, true><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, nf, e, S, w, o);
+    else split_slice_kernel<0, 0><<<grid, 256, 0, s>>>(X, ld, R, K, Kp, mb, nf, e, S, w, o);
   }
   return cudaGetLastError();
 }

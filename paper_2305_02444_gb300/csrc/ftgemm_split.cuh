@@ -31,6 +31,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "ftgemm_common.cuh"
 
 namespace ftg {
@@ -50,6 +52,26 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       "{%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// The INT8 form: m16n8k32 with INT32 accumulators.  Its A and B fragments
+// hold the same bytes of a 128-byte slab row as the bf16 m16n8k16 ones (32 k
+// of int8 where bf16 has 16), so the same ldmatrix addresses load them.
+__device__ __forceinline__ void mma_s8(int (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                       uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void mma_acc(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                        uint32_t b0, uint32_t b1) {
+  mma_bf16(d, a0, a1, a2, a3, b0, b1);
+}
+__device__ __forceinline__ void mma_acc(int (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                        uint32_t b0, uint32_t b1) {
+  mma_s8(d, a0, a1, a2, a3, b0, b1);
 }
 
 // bf16 element (row, k) of a [128][64] slab written by TMA with 128-byte swizzle.
@@ -261,7 +283,13 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
     if (il < mI && jl < nJt) {
       const long long gi = i0 + il, gj = j0 + jl;
       const int eBj = p.eB[gj];
-      const double v = scale_pow2(sC[jl * SP_BM + il], eAi + eBj);
+      double v = scale_pow2(sC[jl * SP_BM + il], eAi + eBj);
+      if (p.i8 && (eAi == SPLIT_NONFINITE_ROW || eBj == SPLIT_NONFINITE_ROW)) {
+        // INT8 slices cannot carry Inf / NaN: a row or column with a
+        // non-finite entry is multiplied in FP64 (IEEE results)
+        v = 0.0;
+        for (long long k = 0; k < p.K; ++k) v = fma(sp_glob_a<TA, TB>(p, gi, k), sp_glob_b<TA, TB>(p, k, gj), v);
+      }
       if (use_c) c = p.C[gi + gj * p.ldc];
       out = use_c ? fma(p.alpha, v, p.beta * c) : p.alpha * v;
       sC[jl * SP_BM + il] = out;
@@ -345,10 +373,14 @@ __device__ __forceinline__ void split_tile_finish(const SplitParams &p, double *
 // CK 0: no checks; 1: FP32 predicted checksums from the staged slices;
 // 2: FP64 predicted checksums from the original operands (two skinny FP64
 // GEMMs before the kernel), verified against the scaled FP64 result.
-template <bool TA, bool TB, int CK>
+// I8: INT8 slices (w = 7; m16n8k32 s8 MMAs with exact INT32 accumulation
+// over k-chunks of up to 133 120 products), 128 k per slab; CK 0 or 2.
+template <bool TA, bool TB, int CK, bool I8 = false>
 __global__ void __launch_bounds__(256, 1)
     ftsplit_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ SplitParams p) {
+  static_assert(!I8 || CK != 1, "INT8 slices: no checks or FP64 checksums");
+  constexpr int SBK = I8 ? SP_BK_I8 : SP_BK;  // k per slab (128 bytes per row either way)
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -385,8 +417,8 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
 
   // work list: (pair q, k-chunk c, slab b) in the order pairs x chunks x slabs
-  const int nslab_total = (int)(p.Kp / SP_BK);
-  const int chunk_slabs = max(1, p.kchunk / SP_BK);
+  const int nslab_total = (int)(p.Kp / SBK);
+  const int chunk_slabs = max(1, p.kchunk / SBK);
   const int nchunks = (nslab_total + chunk_slabs - 1) / chunk_slabs;
   const int nsteps = p.npairs * nslab_total;  // every pair sweeps all slabs once
   auto step_coords = [&](int step, int &pq, int &slab) {
@@ -403,26 +435,27 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb),
-        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(fb), "r"(slab * SP_BK), "r"(i0), "r"(p.pair_s[pq])
+        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(fb), "r"(slab * SBK), "r"(i0), "r"(p.pair_s[pq])
         : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(sb + SP_A_BYTES),
-        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(fb), "r"(slab * SP_BK), "r"(j0), "r"(p.pair_t[pq])
+        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(fb), "r"(slab * SBK), "r"(j0), "r"(p.pair_t[pq])
         : "memory");
   };
   int issued = 0;
   if (tid == 0)
     for (; issued < SP_STAGES && issued < nsteps; ++issued) issue(issued);
 
-  float acc32[4][4][4];
+  using Acc = typename std::conditional<I8, int, float>::type;  // exact pair sums: INT32 or FP32
+  Acc acc32[4][4][4];
   double acc64[4][4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) { acc32[a][b][c] = 0.f; acc64[a][b][c] = 0.0; }
+      for (int c = 0; c < 4; ++c) { acc32[a][b][c] = 0; acc64[a][b][c] = 0.0; }
   float cs32 = 0.f, ca32 = 0.f;     // FT: this pair-chunk's predicted checksum (t < 128: column, else row)
   double cs64 = 0.0, ca64 = 0.0;    // folded predicted checksum and its absolute bound
   int fptr = 0, fend = 0;
@@ -456,7 +489,7 @@ __global__ void __launch_bounds__(256, 1)
         for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt)
-            mma_bf16(acc32[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bf[nt][0], bf[nt][1]);
+            mma_acc(acc32[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], bf[nt][0], bf[nt][1]);
       }
     }  // ok
     if (FT) {
@@ -523,7 +556,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             acc64[a][b][c] = fma(wgt, (double)acc32[a][b][c], acc64[a][b][c]);
-            acc32[a][b][c] = 0.f;
+            acc32[a][b][c] = 0;
           }
       if (FT) {
         cs64 = fma(wgt, (double)cs32, cs64);

@@ -309,7 +309,7 @@ def ftgemm_set_correction(mode: int) -> int:
 
 def ftgemm_set_split_engine(engine: int) -> int:
     """Split precision: 0 default (= 5), 1 mma.sync, 2 tcgen05 one CTA per tile, 5 persistent
-    tcgen05 (ft=1 always runs on mma.sync); other values return -1."""
+    tcgen05, 7 mma.sync with INT8 slices (emulated forms; ft 0 or 2); other values return -1."""
     return lib().ftgemm_set_split_engine(engine)
 
 

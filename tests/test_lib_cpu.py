@@ -88,9 +88,9 @@ def test_host_settings_and_strings(ft):
 
 
 def test_split_engine_knob_codes(ft):
-    for e in (7, 6, 4, 3, -1):   # 3, 4 and 6 (cluster forms) no longer exist
+    for e in (8, 6, 4, 3, -1):   # 3, 4 and 6 (cluster forms) no longer exist
         assert ft.ftgemm_set_split_engine(e) == -1
-    for e in (5, 2):
+    for e in (7, 5, 2):
         assert ft.ftgemm_set_split_engine(e) == 0
     assert ft.ftgemm_set_split_engine(1) == 0
     assert ft.ftgemm_set_split_engine(0) == 0
