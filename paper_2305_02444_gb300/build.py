@@ -11,6 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libftgemm.so")
 SOURCES = ["ftgemm_host.cu", "ftgemm_k_nn.cu", "ftgemm_k_nt.cu", "ftgemm_k_tn.cu", "ftgemm_k_tt.cu",
+           "ftgemm_kb_nn.cu", "ftgemm_kb_nt.cu", "ftgemm_kb_tn.cu", "ftgemm_kb_tt.cu",
            "ftgemm_k_split.cu", "ftgemm_k_split_tc.cu", "ftgemm_k_split_tcp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -25,7 +25,7 @@ constexpr int RING_BYTES = STAGES * STAGE_BYTES;
 constexpr int CTILE_BYTES = BM * BN * 8;  // output tile staged for verify/store
 constexpr int TILE_REGION = RING_BYTES > CTILE_BYTES ? RING_BYTES : CTILE_BYTES;
 // epilogue arrays: 10 x 128 doubles + 4 x 128 ints + counters
-constexpr int EPI_BYTES = 10 * 128 * 8 + 4 * 128 * 4 + 256;
+constexpr int EPI_BYTES = 10 * 128 * 8 + 4 * 128 * 4 + 256 + 264 * 8;
 constexpr int BAR_BYTES = 2 * STAGES * 8 + 8 + 8;
 constexpr int SMEM_BYTES = TILE_REGION + EPI_BYTES + BAR_BYTES + 1024;
 constexpr int MAX_INTERSECT = 64;  // flagged row x column intersections per tile
@@ -306,20 +306,27 @@ __device__ __forceinline__ uint32_t bf16_rn_bits(double x) {
   return (uint32_t)__bfloat16_as_ushort(__double2bfloat16(x));
 }
 
-// |x| rounded upward to FP32 (the result of __double2float_ru(fabs(x))): the
-// fields are rounded with integer operations when the result is a normal
-// FP32 number or overflows, the conversion handles zeros, subnormal results,
-// Inf and NaN.  Used for the absolute sums of the detection thresholds, off
-// the FP64 pipe.
+// |x| rounded upward to FP32 (the result of __double2float_ru(fabs(x)), a NaN
+// for a NaN), with integer operations only: the absolute sums of the
+// detection thresholds run over every element of partly filled tiles (zeros
+// included), and a conversion from FP64 would take the FP64 pipe.
 __device__ __forceinline__ float f32_ru_abs(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  const int ef = (int)(b >> 52) - 1023 + 127;
-  if (ef >= 1 && ef <= 254) {
+  const int E = (int)(b >> 52), ef = E - 1023 + 127;
+  if (ef >= 1 && ef <= 254) {  // a normal FP32 result (or, by the carry, Inf)
     uint32_t v = ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
     v += (b & 0x1FFFFFFFull) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
     return __uint_as_float(v);
   }
-  return __double2float_ru(fabs(x));
+  if (ef > 254) return __uint_as_float(b > 0x7FF0000000000000ull ? 0x7FFFFFFFu : 0x7F800000u);  // NaN; Inf
+  if (b == 0) return 0.0f;
+  // below FP32's normal range: |x| = m 2^(max(E,1) - 1075), that is m 2^-sh in
+  // units of FP32's smallest subnormal 2^-149 (sh >= 30), rounded up; q <= 2^23
+  // (2^23 is the bit pattern of the smallest normal number)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+  const int sh = 926 - (E ? E : 1);
+  const uint32_t q = sh >= 64 ? 1u : (uint32_t)(m >> sh) + ((m & ((1ull << sh) - 1ull)) ? 1u : 0u);
+  return __uint_as_float(q);
 }
 
 // x rounded to FP32, to nearest with ties to even (the result of

@@ -187,9 +187,19 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
   enc_group_finish(cnt, G, nG, (int)gridDim.y, s0, S, part_cabs, part_max, cabs_out, gmax);
 }
 
-// Batched checksum pass: one item per operand of each problem of a batch;
-// every block covers one 128-wide group of one item over the item's whole
-// other dimension, so each result is written once (no partials).
+// Batched checksum pass: one item per operand of each problem of a batch, of
+// the SEG or the STR shape; every block covers one 128-wide group of one item
+// over the item's whole other dimension, so each result is written once (no
+// partials).  The host orders the items by the length of their blocks,
+// longest first, so that the long blocks start in the first wave.
+//
+// The checksum sums are FP64.  The absolute sums, which only bound the
+// rounding in the detection thresholds, run on the FP32 pipe with upward
+// rounding (each partial stays an upper bound of the FP64 sum), which leaves
+// about one FP64 add per operand element.  Where the range makes an FP32
+// absolute sum overflow or leaves it tiny (below 2^-90, where terms under
+// FP32's normal range were rounded up to its smallest numbers), the block
+// takes its absolute sums again in FP64.
 struct EncItem {
   const double *X;       // column-major R x S
   long long R, S, ld;
@@ -198,7 +208,7 @@ struct EncItem {
   double *absv;          // SEG: row abs sums (R); STR: column abs sums (S)
   double *gmax;          // per group: max of the group's abs sums
   int first_block;       // prefix sum of the items' group counts
-  int pad;
+  int seg;               // 1: SEG, 0: STR
 };
 
 __device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b) {
@@ -210,124 +220,259 @@ __device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b
   return lo;
 }
 
-// SEG over groups of 128 rows, all columns of the item in one block; warp w
-// takes batches of 16 columns (16w, 16w + 128, ...), reduced by the
-// transposing butterfly as in enc_seg_kernel.
-__global__ void __launch_bounds__(256) enc_seg_batched_kernel(const EncItem *__restrict__ items, int nitems) {
-  __shared__ double sh[8][128];
-  __shared__ double smx[8];
-  const int it = find_item(items, nitems, blockIdx.x);
-  const EncItem &E = items[it];
-  const int G = blockIdx.x - E.first_block;
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// colsum16 on the FP32 pipe, every addition rounded upward.
+__device__ __forceinline__ float colsum16_ru(float (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
+      v[i] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, o));
+    }
+  }
+  return __fadd_ru(v[0], __shfl_xor_sync(0xffffffffu, v[0], 16));
+}
+
+// The transposing butterfly for 8 columns: lane l's v[c] is its part of
+// column c; the result in lane l is the whole warp's sum of column l mod 8
+// (3 levels exchange half of the columns each, 2 more add across lane bits 3
+// and 4).  RU: FP32 with every addition rounded upward.
+template <typename T, bool RU>
+__device__ __forceinline__ T colsum8(T (&v)[8], int lane) {
+  auto add = [](T x, T y) -> T {
+    if constexpr (RU) return __fadd_ru(x, y);
+    else return x + y;
+  };
+#pragma unroll
+  for (int o = 4; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const T send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
+      v[i] = add(keep, __shfl_xor_sync(0xffffffffu, send, o));
+    }
+  }
+  T t = add(v[0], __shfl_xor_sync(0xffffffffu, v[0], 8));
+  return add(t, __shfl_xor_sync(0xffffffffu, t, 16));
+}
+
+// An FP32 absolute sum that does not stand for the FP64 one (see above).  A
+// NaN (from a NaN operand) stands: the FP64 sum is NaN as well.
+__device__ __forceinline__ bool abs32_loose(float s) { return isinf(s) || (s > 0.0f && s < 0x1p-90f); }
+
+// Elements r and r + 1 (r even) of a column as one 16-byte load (the batched
+// operands are 16-byte aligned with even leading dimensions); an element past
+// the last row reads as zero.
+__device__ __forceinline__ double2 load_pair(const double *col, long long r, long long R) {
+  double2 v = make_double2(0.0, 0.0);
+  if (r < R) {
+    v = __ldg(reinterpret_cast<const double2 *>(col + r));
+    if (r + 1 >= R) v.y = 0.0;
+  }
+  return v;
+}
+
+// SEG over the 128-row group G, all columns of the item: warp w takes batches
+// of 8 columns (8w, 8w + 64, ...), lane l the rows 2l, 2l + 1, 2l + 64 and
+// 2l + 65 of each column (two 16-byte loads; a batch's 16 loads are issued
+// before any is used); a column's sum is the lanes' 4-row partials reduced by
+// the transposing butterfly.
+__device__ __forceinline__ void enc_seg_group(const EncItem &E, int G, float (*s_abs)[128], float *s_mx,
+                                              double *s_md) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long r0 = (long long)G * 128;
-  double rabs[4] = {0.0, 0.0, 0.0, 0.0};
-  double mx = 0.0;
-  for (long long sb = 16 * w; sb < E.S; sb += 128) {
-    double ps[16], pa[16];
+  float rabs[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // rows 2l, 2l + 1, 2l + 64, 2l + 65
+  float mx = 0.0f;
+  for (long long sb = 8 * w; sb < E.S; sb += 64) {
+    double2 v[8][2];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < 8; ++j) {
       const long long s = sb + j;
-      double v[4];
+      const double *col = E.X + min(s, E.S - 1) * E.ld;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long long r = r0 + lane + 32 * q;
-        v[q] = (r < E.R && s < E.S) ? E.X[r + s * E.ld] : 0.0;
-        rabs[q] += fabs(v[q]);
-      }
-      ps[j] = (v[0] + v[1]) + (v[2] + v[3]);
-      pa[j] = (fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3]));
+      for (int h = 0; h < 2; ++h) v[j][h] = load_pair(col, r0 + 64 * h + 2 * lane, s < E.S ? E.R : 0);
     }
-    const double sum = colsum16(ps, lane), ab = colsum16(pa, lane);
-    const long long s = sb + (lane & 15);
-    if (lane < 16 && s < E.S) {
+    double ps[8];
+    float pa[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float a0 = f32_ru_abs(v[j][0].x), a1 = f32_ru_abs(v[j][0].y);
+      const float a2 = f32_ru_abs(v[j][1].x), a3 = f32_ru_abs(v[j][1].y);
+      rabs[0] = __fadd_ru(rabs[0], a0);
+      rabs[1] = __fadd_ru(rabs[1], a1);
+      rabs[2] = __fadd_ru(rabs[2], a2);
+      rabs[3] = __fadd_ru(rabs[3], a3);
+      ps[j] = (v[j][0].x + v[j][0].y) + (v[j][1].x + v[j][1].y);
+      pa[j] = __fadd_ru(__fadd_ru(a0, a1), __fadd_ru(a2, a3));
+    }
+    const double sum = colsum8<double, false>(ps, lane);
+    const float ab = colsum8<float, true>(pa, lane);
+    const long long s = sb + (lane & 7);
+    if (lane < 8 && s < E.S) {
       E.gsum[(long long)G * E.gstride + s] = sum;
-      mx = fmax(mx, ab);
+      mx = fmaxf(mx, ab);
     }
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) sh[w][lane + 32 * q] = rabs[q];
+  s_abs[w][2 * lane] = rabs[0];
+  s_abs[w][2 * lane + 1] = rabs[1];
+  s_abs[w][2 * lane + 64] = rabs[2];
+  s_abs[w][2 * lane + 65] = rabs[3];
   mx = warp_max(mx);
-  if (lane == 0) smx[w] = mx;
+  if (lane == 0) s_mx[w] = mx;
   __syncthreads();
+  float t = 0.0f, m = 0.0f;
+  bool loose = false;
+  const long long r = r0 + threadIdx.x;
   if (threadIdx.x < 128) {
-    double t = 0.0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
-    const long long r = r0 + threadIdx.x;
-    if (r < E.R) E.absv[r] = t;
+    for (int q = 0; q < 8; ++q) t = __fadd_ru(t, s_abs[q][threadIdx.x]);
+    loose = r < E.R && abs32_loose(t);
   }
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int q = 0; q < 8; ++q) m = fmax(m, smx[q]);
-    E.gmax[G] = m;
+    for (int q = 0; q < 8; ++q) m = fmaxf(m, s_mx[q]);
+    loose = loose || abs32_loose(m);
+  }
+  if (!__syncthreads_or(loose)) {
+    if (threadIdx.x < 128 && r < E.R) E.absv[r] = (double)t;
+    if (threadIdx.x == 0) E.gmax[G] = (double)m;
+    return;
+  }
+  // FP64 absolute sums: thread t the row r0 + t; warp w the columns w, w + 8, ...
+  if (threadIdx.x < 128 && r < E.R) {
+    double a = 0.0;
+    for (long long s = 0; s < E.S; ++s) a += fabs(E.X[r + s * E.ld]);
+    E.absv[r] = a;
+  }
+  double md = 0.0;
+  for (long long s = w; s < E.S; s += 8) {
+    double a = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long rr = r0 + lane + 32 * q;
+      if (rr < E.R) a += fabs(E.X[rr + s * E.ld]);
+    }
+    md = fmax(md, warp_sum(a));
+  }
+  if (lane == 0) s_md[w] = md;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double g = 0.0;
+    for (int q = 0; q < 8; ++q) g = fmax(g, s_md[q]);
+    E.gmax[G] = g;
   }
 }
 
-// STR over groups of 128 columns, all rows of the item in one block, in
-// chunks of 64 rows: warp w takes the group's columns 16w..16w+15, lane l the
-// rows l and l + 32 of a chunk; the columns' absolute sums stay per lane in
-// registers and are reduced once at the end (transposing butterfly), the
-// rows' sums go through shared memory once per chunk.
-__global__ void __launch_bounds__(256) enc_str_batched_kernel(const EncItem *__restrict__ items, int nitems) {
-  __shared__ double srs[8][64], sra[8][64];
-  __shared__ double smx[2];
-  const int it = find_item(items, nitems, blockIdx.x);
-  const EncItem &E = items[it];
-  const int G = blockIdx.x - E.first_block;
+// STR over the 128-column group G, all rows of the item: warp w takes the
+// 64-row chunks w, w + 8, ..., lane l the rows 2l and 2l + 1 of a chunk over
+// all of the group's columns (one 16-byte load per column; 16 columns' loads
+// are issued before any is used), so a row's sum over the group stays in one
+// lane (columns in ascending order).  The columns' absolute sums over the
+// chunk are reduced across the warp by the transposing butterfly and kept per
+// lane; the warps' parts are added once at the end.
+__device__ __forceinline__ void enc_str_group(const EncItem &E, int G, float (*s_cab)[128], float *s_mx,
+                                              double *s_md) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long s0 = (long long)G * 128;
   const int ns = (int)min(128LL, E.S - s0);
-  double cab[16];
+  // s_cab[w][c]: column c's absolute sum over warp w's chunks (the warp's own row)
+  if (lane < 16) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) cab[q] = 0.0;
-  double mloc = 0.0;
-  for (long long r0 = 0; r0 < E.R; r0 += 64) {
-    const long long ra = r0 + lane, rb = ra + 32;
-    double rs_a = 0.0, rs_b = 0.0, ab_a = 0.0, ab_b = 0.0;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int sl = w * 16 + q;
-      double va = 0.0, vb = 0.0;
-      if (sl < ns) {
-        const double *col = E.X + (s0 + sl) * E.ld;
-        if (ra < E.R) va = col[ra];
-        if (rb < E.R) vb = col[rb];
-      }
-      rs_a += va;
-      rs_b += vb;
-      ab_a += fabs(va);
-      ab_b += fabs(vb);
-      cab[q] += fabs(va) + fabs(vb);
-    }
-    srs[w][lane] = rs_a;
-    srs[w][lane + 32] = rs_b;
-    sra[w][lane] = ab_a;
-    sra[w][lane + 32] = ab_b;
-    __syncthreads();
-    if (threadIdx.x < 64) {
-      const long long r = r0 + threadIdx.x;
-      double t = 0.0, ta = 0.0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        t += srs[q][threadIdx.x];
-        ta += sra[q][threadIdx.x];
-      }
-      if (r < E.R) {
-        E.gsum[(long long)G * E.gstride + r] = t;
-        mloc = fmax(mloc, ta);
-      }
-    }
-    __syncthreads();
+    for (int b = 0; b < 8; ++b) s_cab[w][16 * b + lane] = 0.0f;
   }
-  const double cs = colsum16(cab, lane);
-  if (lane < 16 && w * 16 + lane < ns) E.absv[s0 + w * 16 + lane] = cs;
-  if (threadIdx.x < 64) {
-    const double m = warp_max(mloc);
-    if (lane == 0) smx[w] = m;
+  __syncwarp();
+  float mloc = 0.0f;
+  for (long long r0 = 64LL * w; r0 < E.R; r0 += 512) {
+    const long long r = r0 + 2 * lane;
+    double rs0 = 0.0, rs1 = 0.0;
+    float ra0 = 0.0f, ra1 = 0.0f;
+#pragma unroll 1
+    for (int b = 0; 16 * b < ns; ++b) {
+      double2 v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int sl = 16 * b + q;
+        v[q] = load_pair(E.X + (s0 + min(sl, ns - 1)) * E.ld, r, sl < ns ? E.R : 0);
+      }
+      float pc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        rs0 += v[q].x;
+        rs1 += v[q].y;
+        const float fa = f32_ru_abs(v[q].x), fb = f32_ru_abs(v[q].y);
+        ra0 = __fadd_ru(ra0, fa);
+        ra1 = __fadd_ru(ra1, fb);
+        pc[q] = __fadd_ru(fa, fb);
+      }
+      const float cs = colsum16_ru(pc, lane);
+      if (lane < 16) s_cab[w][16 * b + lane] = __fadd_ru(s_cab[w][16 * b + lane], cs);
+    }
+    if (r < E.R) {
+      E.gsum[(long long)G * E.gstride + r] = rs0;
+      mloc = fmaxf(mloc, ra0);
+    }
+    if (r + 1 < E.R) {
+      E.gsum[(long long)G * E.gstride + r + 1] = rs1;
+      mloc = fmaxf(mloc, ra1);
+    }
   }
+  mloc = warp_max(mloc);
+  if (lane == 0) s_mx[w] = mloc;
   __syncthreads();
-  if (threadIdx.x == 0) E.gmax[G] = fmax(smx[0], smx[1]);
+  float cs = 0.0f, gm = 0.0f;
+  bool loose = false;
+  if (threadIdx.x < ns) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cs = __fadd_ru(cs, s_cab[q][threadIdx.x]);
+    loose = abs32_loose(cs);
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 8; ++q) gm = fmaxf(gm, s_mx[q]);
+    loose = loose || abs32_loose(gm);
+  }
+  if (!__syncthreads_or(loose)) {
+    if (threadIdx.x < ns) E.absv[s0 + threadIdx.x] = (double)cs;
+    if (threadIdx.x == 0) E.gmax[G] = (double)gm;
+    return;
+  }
+  // FP64 absolute sums: thread t the column s0 + t; rows strided over the block
+  if ((int)threadIdx.x < ns) {
+    const double *col = E.X + (s0 + threadIdx.x) * E.ld;
+    double a = 0.0;
+    for (long long rr = 0; rr < E.R; ++rr) a += fabs(col[rr]);
+    E.absv[s0 + threadIdx.x] = a;
+  }
+  double md = 0.0;
+  for (long long rr = threadIdx.x; rr < E.R; rr += 256) {
+    double a = 0.0;
+    for (int sl = 0; sl < ns; ++sl) a += fabs(E.X[rr + (s0 + sl) * E.ld]);
+    md = fmax(md, a);
+  }
+  md = warp_max(md);
+  if (lane == 0) s_md[w] = md;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double g = 0.0;
+    for (int q = 0; q < 8; ++q) g = fmax(g, s_md[q]);
+    E.gmax[G] = g;
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) enc_batched_kernel(const EncItem *__restrict__ items, int nitems) {
+  __shared__ float s_abs[8][128];
+  __shared__ float s_mx[8];
+  __shared__ double s_md[8];
+  const int it = find_item(items, nitems, blockIdx.x);
+  const EncItem &E = items[it];
+  const int G = blockIdx.x - E.first_block;
+  if (E.seg) enc_seg_group(E, G, s_abs, s_mx, s_md);
+  else enc_str_group(E, G, s_abs, s_mx, s_md);
 }
 
 // One pass over C that takes, per 128x128 tile, the column sums over the

@@ -1775,28 +1775,35 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
   PLAN_TRY(plan_alloc(P, &dprobs, hp.size()));
   cudaMemcpy(dprobs, hp.data(), sizeof(BatchProblem) * hp.size(), cudaMemcpyHostToDevice);
 
-  // checksum-pass items: op(A) 'N' and op(B) 'T' are SEG, the others STR
-  std::vector<EncItem> seg, str;
-  int seg_blocks = 0, str_blocks = 0;
+  // checksum-pass items: op(A) 'N' and op(B) 'T' are SEG, the others STR; one
+  // block per 128-wide group, the items ordered by the length of their blocks
+  // (the other dimension), longest first
+  std::vector<EncItem> items;
+  int enc_blocks = 0;
   for (long long q = 0; q < count && P->ft; ++q) {
     if (!work[q]) continue;
     EncItem a{}, b{};
-    if (!is_t(transA[q])) { a.X = A[q]; a.R = M[q]; a.S = K[q]; }
-    else { a.X = A[q]; a.R = K[q]; a.S = M[q]; }
+    if (!is_t(transA[q])) { a.X = A[q]; a.R = M[q]; a.S = K[q]; a.seg = 1; }
+    else { a.X = A[q]; a.R = K[q]; a.S = M[q]; a.seg = 0; }
     a.ld = lda[q]; a.gsum = enc + off_acs[q]; a.gstride = Kp[q]; a.absv = enc + off_ar[q]; a.gmax = enc + off_am[q];
-    if (!is_t(transB[q])) { b.X = B[q]; b.R = K[q]; b.S = N[q]; }
-    else { b.X = B[q]; b.R = N[q]; b.S = K[q]; }
+    if (!is_t(transB[q])) { b.X = B[q]; b.R = K[q]; b.S = N[q]; b.seg = 0; }
+    else { b.X = B[q]; b.R = N[q]; b.S = K[q]; b.seg = 1; }
     b.ld = ldb[q]; b.gsum = enc + off_bcs[q]; b.gstride = Kp[q]; b.absv = enc + off_bc[q]; b.gmax = enc + off_bm[q];
-    if (!is_t(transA[q])) { a.first_block = seg_blocks; seg_blocks += (int)nI[q]; seg.push_back(a); }
-    else { a.first_block = str_blocks; str_blocks += (int)nI[q]; str.push_back(a); }
-    if (is_t(transB[q])) { b.first_block = seg_blocks; seg_blocks += (int)nJ[q]; seg.push_back(b); }
-    else { b.first_block = str_blocks; str_blocks += (int)nJ[q]; str.push_back(b); }
+    a.first_block = (int)nI[q];   // group counts until the prefix sums below
+    b.first_block = (int)nJ[q];
+    items.push_back(a);
+    items.push_back(b);
   }
-  EncItem *dseg = nullptr, *dstr = nullptr;
-  PLAN_TRY(plan_alloc(P, &dseg, std::max<size_t>(1, seg.size())));
-  PLAN_TRY(plan_alloc(P, &dstr, std::max<size_t>(1, str.size())));
-  if (!seg.empty()) cudaMemcpy(dseg, seg.data(), sizeof(EncItem) * seg.size(), cudaMemcpyHostToDevice);
-  if (!str.empty()) cudaMemcpy(dstr, str.data(), sizeof(EncItem) * str.size(), cudaMemcpyHostToDevice);
+  auto blen = [](const EncItem &e) { return e.seg ? e.S : e.R; };
+  std::stable_sort(items.begin(), items.end(), [&](const EncItem &x, const EncItem &y) { return blen(x) > blen(y); });
+  for (EncItem &e : items) {
+    const int groups = e.first_block;
+    e.first_block = enc_blocks;
+    enc_blocks += groups;
+  }
+  EncItem *ditems = nullptr;
+  PLAN_TRY(plan_alloc(P, &ditems, std::max<size_t>(1, items.size())));
+  if (!items.empty()) cudaMemcpy(ditems, items.data(), sizeof(EncItem) * items.size(), cudaMemcpyHostToDevice);
 
   // work lists per operand layout, in the scheduled order
   struct Group { std::vector<int> prob, local, order; };
@@ -1846,8 +1853,7 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
     cudaMemsetAsync(P->reps, 0, sizeof(DevReport) * std::max<long long>(1, count), cs);
     if (P->ft && enc_total) {
       cudaMemsetAsync(enc, 0, sizeof(double) * enc_total, cs);
-      if (seg_blocks) { enc_seg_batched_kernel<<<seg_blocks, 256, 0, cs>>>(dseg, (int)seg.size()); P->kernels++; }
-      if (str_blocks) { enc_str_batched_kernel<<<str_blocks, 256, 0, cs>>>(dstr, (int)str.size()); P->kernels++; }
+      if (enc_blocks) { enc_batched_kernel<<<enc_blocks, 256, 0, cs>>>(ditems, (int)items.size()); P->kernels++; }
     }
     for (long long q = 0; q < count; ++q)
       if (!work[q] && M[q] > 0 && N[q] > 0 && beta[q] != 1.0) {

@@ -1,4 +1,4 @@
-// FP64 kernels for op(A) = t, op(B) = n (one translation unit per layout).
+// Single-problem FP64 kernels for op(A) = t, op(B) = n (one translation unit per layout).
 #include "ftgemm_launch.cuh"
 
 FTG_LAYOUT_LAUNCHERS(tn, true, false)

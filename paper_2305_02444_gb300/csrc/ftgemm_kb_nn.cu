@@ -1,0 +1,4 @@
+// Batched FP64 kernel for op(A) = n, op(B) = n (one translation unit per layout).
+#include "ftgemm_launch.cuh"
+
+FTG_LAYOUT_BATCHED_LAUNCHERS(nn, false, false)

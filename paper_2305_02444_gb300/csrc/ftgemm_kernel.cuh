@@ -114,21 +114,62 @@ __device__ __forceinline__ void slab_fma(double (&acc)[8][8], const unsigned cha
   }
 }
 
-// slab_fma for rblk x cblk accumulator blocks (each 2, 4 or 8; 6 as well
-// with FINE).
-template <bool TA, bool TB, int PP>
-__device__ __forceinline__ void slab_fma_cols(int cblk, double (&acc)[8][8], const unsigned char *sA,
-                                              const unsigned char *sB, int tx, int ty) {
-  if (cblk == 8) slab_fma<TA, TB, PP, 8>(acc, sA, sB, tx, ty);
-  else if (cblk == 6) slab_fma<TA, TB, PP, 6>(acc, sA, sB, tx, ty);
-  else if (cblk == 4) slab_fma<TA, TB, PP, 4>(acc, sA, sB, tx, ty);
-  else slab_fma<TA, TB, PP, 2>(acc, sA, sB, tx, ty);
+// One k-slab for the accumulator blocks P0 .. P0+PP-1 (rows) x Q0 .. Q0+QQ-1
+// (columns) of this thread: the same FMAs, in the same k order, as those
+// blocks get in slab_fma.
+template <bool TA, bool TB, int P0, int PP, int Q0, int QQ>
+__device__ __forceinline__ void slab_fma_part(double (&acc)[8][8], const unsigned char *sA, const unsigned char *sB,
+                                              int tx, int ty) {
+#pragma unroll
+  for (int k = 0; k < BK; ++k) {
+    double a[PP], b[QQ];
+#pragma unroll
+    for (int pp = 0; pp < PP; ++pp) a[pp] = stage_a<TA>(sA, tx + 16 * (P0 + pp), k);
+#pragma unroll
+    for (int qq = 0; qq < QQ; ++qq) b[qq] = stage_b<TB>(sB, k, ty + 16 * (Q0 + qq));
+#pragma unroll
+    for (int pp = 0; pp < PP; ++pp)
+#pragma unroll
+      for (int qq = 0; qq < QQ; ++qq) acc[P0 + pp][Q0 + qq] = fma(a[pp], b[qq], acc[P0 + pp][Q0 + qq]);
+  }
 }
 
+// The column blocks 0 .. cblk-1 (cblk in 1..8) for the row blocks P0 ..
+// P0+PP-1: all 8 in one pass, else in binary pieces (4, 2, 1), one pass each.
+template <bool TA, bool TB, int P0, int PP>
+__device__ __forceinline__ void slab_fma_rowpiece(int cblk, double (&acc)[8][8], const unsigned char *sA,
+                                                  const unsigned char *sB, int tx, int ty) {
+  if (cblk == 8) {
+    slab_fma_part<TA, TB, P0, PP, 0, 8>(acc, sA, sB, tx, ty);
+    return;
+  }
+  if (cblk & 4) slab_fma_part<TA, TB, P0, PP, 0, 4>(acc, sA, sB, tx, ty);
+  if (cblk & 2) {
+    if (cblk & 4) slab_fma_part<TA, TB, P0, PP, 4, 2>(acc, sA, sB, tx, ty);
+    else slab_fma_part<TA, TB, P0, PP, 0, 2>(acc, sA, sB, tx, ty);
+  }
+  if (cblk & 1) {
+    switch (cblk & 6) {
+      case 0: slab_fma_part<TA, TB, P0, PP, 0, 1>(acc, sA, sB, tx, ty); break;
+      case 2: slab_fma_part<TA, TB, P0, PP, 2, 1>(acc, sA, sB, tx, ty); break;
+      case 4: slab_fma_part<TA, TB, P0, PP, 4, 1>(acc, sA, sB, tx, ty); break;
+      default: slab_fma_part<TA, TB, P0, PP, 6, 1>(acc, sA, sB, tx, ty); break;
+    }
+  }
+}
+
+// slab_fma for rblk x cblk accumulator blocks.  Without FINE each count is 2,
+// 4 or 8 and the blocks take one fused pass.  With FINE (the batched kernel,
+// whose small problems often end in partly filled tiles) each count is any of
+// 1..8, so a tile computes its valid rows and columns rounded up to 16 only:
+// the row and column blocks split into binary pieces and each pair of pieces
+// takes one pass over the slab.  Every accumulator gets the same FMAs in the
+// same order either way (the same bits); the extra passes re-read operands
+// from shared memory, which is cheap beside the FP64 pipe.
 template <bool TA, bool TB, bool FINE>
 __device__ __forceinline__ void slab_fma_blocks(int rblk, int cblk, double (&acc)[8][8], const unsigned char *sA,
                                                 const unsigned char *sB, int tx, int ty) {
-  if constexpr (!FINE) {  // 2, 4 or 8 blocks each way
+  if constexpr (!FINE) {
     if (rblk == 8 && cblk == 8) slab_fma<TA, TB, 8, 8>(acc, sA, sB, tx, ty);
     else if (rblk == 8 && cblk == 4) slab_fma<TA, TB, 8, 4>(acc, sA, sB, tx, ty);
     else if (rblk == 8) slab_fma<TA, TB, 8, 2>(acc, sA, sB, tx, ty);
@@ -139,10 +180,23 @@ __device__ __forceinline__ void slab_fma_blocks(int rblk, int cblk, double (&acc
     else if (cblk == 4) slab_fma<TA, TB, 2, 4>(acc, sA, sB, tx, ty);
     else slab_fma<TA, TB, 2, 2>(acc, sA, sB, tx, ty);
   } else {
-    if (rblk == 8) slab_fma_cols<TA, TB, 8>(cblk, acc, sA, sB, tx, ty);
-    else if (rblk == 6) slab_fma_cols<TA, TB, 6>(cblk, acc, sA, sB, tx, ty);
-    else if (rblk == 4) slab_fma_cols<TA, TB, 4>(cblk, acc, sA, sB, tx, ty);
-    else slab_fma_cols<TA, TB, 2>(cblk, acc, sA, sB, tx, ty);
+    if (rblk == 8) {
+      slab_fma_rowpiece<TA, TB, 0, 8>(cblk, acc, sA, sB, tx, ty);
+      return;
+    }
+    if (rblk & 4) slab_fma_rowpiece<TA, TB, 0, 4>(cblk, acc, sA, sB, tx, ty);
+    if (rblk & 2) {
+      if (rblk & 4) slab_fma_rowpiece<TA, TB, 4, 2>(cblk, acc, sA, sB, tx, ty);
+      else slab_fma_rowpiece<TA, TB, 0, 2>(cblk, acc, sA, sB, tx, ty);
+    }
+    if (rblk & 1) {
+      switch (rblk & 6) {
+        case 0: slab_fma_rowpiece<TA, TB, 0, 1>(cblk, acc, sA, sB, tx, ty); break;
+        case 2: slab_fma_rowpiece<TA, TB, 2, 1>(cblk, acc, sA, sB, tx, ty); break;
+        case 4: slab_fma_rowpiece<TA, TB, 4, 1>(cblk, acc, sA, sB, tx, ty); break;
+        default: slab_fma_rowpiece<TA, TB, 6, 1>(cblk, acc, sA, sB, tx, ty); break;
+      }
+    }
   }
 }
 
@@ -164,6 +218,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   int *s_fr = reinterpret_cast<int *>(epi + 1280);
   int *s_fc = s_fr + 128, *s_rfail = s_fc + 128, *s_cfail = s_rfail + 128;
   int *cnt = s_cfail + 128;
+  double *s_abv = epi + 1568;  // the verify's absolute sums: columns, rows, then the two maxima
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + TILE_REGION + EPI_BYTES);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), cbar = smem_u32(bars + 2 * STAGES);
 
@@ -224,12 +279,19 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   if (tid == 0) {
     for (; issued < STAGES && issued < nks; ++issued) issue(issued);
   }
+  if (FT && MODE != 1) {  // fetched while the first slabs are in flight
+    if (tid < 128) s_abv[tid] = tid < nJt ? p.bcolabs[j0 + tid] : 0.0;
+    else s_abv[tid] = tid - 128 < mI ? p.arowabs[i0 + tid - 128] : 0.0;
+    if (tid == 32) {
+      s_abv[256] = p.aabsmax[I];
+      s_abv[257] = p.babsmax[J];
+    }
+  }
 
   const int tx = tid & 15, ty = tid >> 4;  // rows tx + 16*pp, columns ty + 16*qq
   // accumulator blocks (16 rows / columns each) that hold valid rows / columns:
-  // 2, 4 or 8, and also 6 in the batched kernel (FINE), whose small problems
-  // often end in partly filled tiles
-  auto blocks = [](int v) { return v <= 32 ? 2 : v <= 64 ? 4 : (FINE && v <= 96) ? 6 : 8; };
+  // 2, 4 or 8, and any of 1..8 in the batched kernel (FINE)
+  auto blocks = [](int v) { return FINE ? (v + 15) >> 4 : v <= 32 ? 2 : v <= 64 ? 4 : 8; };
   const int rblk = blocks(mI), cblk = blocks(nJt);
   double acc[8][8];
 #pragma unroll
@@ -255,8 +317,8 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     const unsigned char *sA = smem + st * STAGE_BYTES;
     const unsigned char *sB = sA + A_BYTES;
     // rows tx + 16 pp >= mI and columns ty + 16 qq >= nJt hold zeros (TMA
-    // zero fill): a tile with at most 96 / 64 / 32 valid rows or columns
-    // skips those blocks' FMAs, leaving the same bits
+    // zero fill): a tile whose valid rows or columns end before the last
+    // blocks skips those blocks' FMAs, leaving the same bits
     slab_fma_blocks<TA, TB, FINE>(rblk, cblk, acc, sA, sB, tx, ty);
     if (FT) {
       const double *scs = reinterpret_cast<const double *>(sA + A_BYTES + B_BYTES);
@@ -530,14 +592,37 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   } else if (FT && use_c) {
     double rs = 0.0, cs = 0.0;
     float ra = 0.0f, ca = 0.0f;
+    if constexpr (FINE) {
+      // the batched kernel sums the valid rows and columns only: half h of
+      // row r has xc valid columns, half h of column r xr valid rows (visited
+      // in the rotated order modulo xr)
+      const int xc = min(max(nJt - 64 * h, 0), 64), xr = min(max(mI - 64 * h, 0), 64);
+      if (r < mI) {
+        for (int q = 0; q < xc; ++q) {
+          const double v = sC[(64 * h + q) * BM + r];
+          rs += v;
+          ra = __fadd_ru(ra, f32_ru_abs(v));
+        }
+      }
+      if (r < nJt && xr > 0) {
+        int x = r % xr;
+        for (int q = 0; q < xr; ++q) {
+          const double v = sC[r * BM + 64 * h + x];
+          cs += v;
+          ca = __fadd_ru(ca, f32_ru_abs(v));
+          x = (x + 1 == xr) ? 0 : x + 1;
+        }
+      }
+    } else {
 #pragma unroll 8
-    for (int q = 0; q < 64; ++q) {
-      const double vr = sC[(64 * h + q) * BM + r];
-      const double vc = sC[r * BM + 64 * h + ((q + r) & 63)];
-      rs += vr;
-      cs += vc;
-      ra = __fadd_ru(ra, f32_ru_abs(vr));
-      ca = __fadd_ru(ca, f32_ru_abs(vc));
+      for (int q = 0; q < 64; ++q) {
+        const double vr = sC[(64 * h + q) * BM + r];
+        const double vc = sC[r * BM + 64 * h + ((q + r) & 63)];
+        rs += vr;
+        cs += vc;
+        ra = __fadd_ru(ra, f32_ru_abs(vr));
+        ca = __fadd_ru(ca, f32_ru_abs(vc));
+      }
     }
     if (h) { s_ro[r] = rs; s_co[r] = cs; s_pr[r] = (double)ra; s_pc[r] = (double)ca; }
     compute_sync();
@@ -550,12 +635,15 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   }
   if (FT) compute_sync();
 
-  // out = alpha*acc + beta*C, written over the staged C tile
+  // out = alpha*acc + beta*C, written over the staged C tile (the batched
+  // kernel writes the computed blocks only; the rest of the tile lies outside
+  // C, and no later step reads it)
   if (MODE != 3) {
 #pragma unroll
     for (int pp = 0; pp < 8; ++pp)
 #pragma unroll
       for (int qq = 0; qq < 8; ++qq) {
+        if (FINE && (pp >= rblk || qq >= cblk)) continue;
         const int idx = (ty + 16 * qq) * BM + tx + 16 * pp;
         sC[idx] = use_c ? fma(p.alpha, acc[pp][qq], p.beta * sC[idx]) : p.alpha * acc[pp][qq];
       }
@@ -563,13 +651,27 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
   }
 
   if (FT) {
-    // reference checksums of the computed tile
+    // reference checksums of the computed tile (the batched kernel: over the
+    // valid rows and columns, as the C sums above)
     {
       double rs = 0.0, cs = 0.0;
+      if constexpr (FINE) {
+        const int xc = min(max(nJt - 64 * h, 0), 64), xr = min(max(mI - 64 * h, 0), 64);
+        if (r < mI)
+          for (int q = 0; q < xc; ++q) rs += sC[(64 * h + q) * BM + r];
+        if (r < nJt && xr > 0) {
+          int x = r % xr;
+          for (int q = 0; q < xr; ++q) {
+            cs += sC[r * BM + 64 * h + x];
+            x = (x + 1 == xr) ? 0 : x + 1;
+          }
+        }
+      } else {
 #pragma unroll 8
-      for (int q = 0; q < 64; ++q) {
-        rs += sC[(64 * h + q) * BM + r];
-        cs += sC[r * BM + 64 * h + ((q + r) & 63)];
+        for (int q = 0; q < 64; ++q) {
+          rs += sC[(64 * h + q) * BM + r];
+          cs += sC[r * BM + 64 * h + ((q + r) & 63)];
+        }
       }
       if (h) { s_pr[r] = rs; s_pc[r] = cs; }
       compute_sync();
@@ -583,7 +685,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
         const int j = tid;
         if (j < nJt) {
           const double pc = use_c ? fma(p.alpha, csacc, p.beta * s_cc[j]) : p.alpha * csacc;
-          const double S = fabs(p.alpha) * p.bcolabs[j0 + j] * p.aabsmax[I] + (use_c ? fabs(p.beta) * s_cca[j] : 0.0);
+          const double S = fabs(p.alpha) * s_abv[j] * s_abv[256] + (use_c ? fabs(p.beta) * s_cca[j] : 0.0);
           const double n = (double)(p.K + mI + nextra);
           const double tau = 2.01 * n * u * S + n * 0x1p-1021;
           s_pc[j] = pc;
@@ -595,7 +697,7 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
         const int i = tid - 128;
         if (i < mI) {
           const double pr = use_c ? fma(p.alpha, csacc, p.beta * s_rc[i]) : p.alpha * csacc;
-          const double S = fabs(p.alpha) * p.arowabs[i0 + i] * p.babsmax[J] + (use_c ? fabs(p.beta) * s_rca[i] : 0.0);
+          const double S = fabs(p.alpha) * s_abv[128 + i] * s_abv[257] + (use_c ? fabs(p.beta) * s_rca[i] : 0.0);
           const double n = (double)(p.K + nJt + nextra);
           const double tau = 2.01 * n * u * S + n * 0x1p-1021;
           s_pr[i] = pr;
@@ -646,12 +748,12 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
         double s = 0.0;
         if (e < nr) {
           const int i = s_fr[e];
-          for (int j = lane; j < BN; j += 32) s += sC[j * BM + i];
+          for (int j = lane; j < nJt; j += 32) s += sC[j * BM + i];
           s = warp_sum(s);
           if (lane == 0 && !(fabs(s - s_pr[i]) <= s_tr[i])) { s_rfail[i] = 1; atomicAdd(&cnt[C_FAIL], 1); }
         } else {
           const int j = s_fc[e - nr];
-          for (int i = lane; i < BM; i += 32) s += sC[j * BM + i];
+          for (int i = lane; i < mI; i += 32) s += sC[j * BM + i];
           s = warp_sum(s);
           if (lane == 0 && !(fabs(s - s_pc[j]) <= s_tc[j])) { s_cfail[j] = 1; atomicAdd(&cnt[C_FAIL], 1); }
         }
@@ -668,13 +770,13 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
           double s = 0.0;
           if (e < BM) {
             if (!s_rfail[e]) continue;
-            for (int j = lane; j < BN; j += 32) s += sC[j * BM + e];
+            for (int j = lane; j < nJt; j += 32) s += sC[j * BM + e];
             s = warp_sum(s);
             if (lane == 0 && !(fabs(s - s_pr[e]) <= s_tr[e])) atomicAdd(&cnt[C_CSONLY], 1);
           } else {
             const int j = e - BM;
             if (!s_cfail[j]) continue;
-            for (int i = lane; i < BM; i += 32) s += sC[j * BM + i];
+            for (int i = lane; i < mI; i += 32) s += sC[j * BM + i];
             s = warp_sum(s);
             if (lane == 0 && !(fabs(s - s_pc[j]) <= s_tc[j])) atomicAdd(&cnt[C_CSONLY], 1);
           }

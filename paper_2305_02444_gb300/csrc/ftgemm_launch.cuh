@@ -3,9 +3,9 @@
 // the fault-tolerant kernel with the injector, for whole tiles (mode 0),
 // split-K partials (mode 1) and reductions (mode 2), each of the first two
 // with or without the per-k-panel verification; the verify-only pass (mode
-// 3); and the persistent batched kernel.  Each ftgemm_k_<layout>.cu
-// instantiates them for its layout, so that the four layouts compile in
-// parallel.
+// 3); and the persistent batched kernel.  Each ftgemm_k_<layout>.cu and
+// ftgemm_kb_<layout>.cu instantiates them for its layout, so that the layouts
+// compile in parallel.
 #pragma once
 
 #include "ftgemm_kernel.cuh"
@@ -67,13 +67,20 @@ struct LayoutLaunch {
 
 }  // namespace ftg
 
-// The entry points of one layout XX (nn, nt, tn, tt) for the host code.
+// The entry points of one layout XX (nn, nt, tn, tt) for the host code: the
+// single-problem kernels (ftgemm_k_<layout>.cu) and the batched kernel
+// (ftgemm_kb_<layout>.cu), in separate translation units so that they
+// compile in parallel.
 #define FTG_LAYOUT_LAUNCHERS(XX, TA, TB)                                                                          \
   namespace ftg {                                                                                                 \
   cudaError_t launch_gemm_##XX(bool ft, bool inj, int mode, bool panel, const CUtensorMap &a, const CUtensorMap &b, \
                                const CUtensorMap &c, const CUtensorMap &w, const Params &p, cudaStream_t s) {     \
     return LayoutLaunch<TA, TB>::gemm(ft, inj, mode, panel, a, b, c, w, p, s);                                    \
   }                                                                                                               \
+  }
+
+#define FTG_LAYOUT_BATCHED_LAUNCHERS(XX, TA, TB)                                                                  \
+  namespace ftg {                                                                                                 \
   cudaError_t launch_batched_##XX(bool ft, bool inj, const BatchProblem *probs, const int *order,                 \
                                   const int *tile_prob, const int *tile_local, int total, int chunk, int *counter, \
                                   int *gerr, int grid, cudaStream_t s) {                                          \

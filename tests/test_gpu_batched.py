@@ -161,3 +161,101 @@ def test_batched_argument_codes(ft):
     probs = [("N", "N", 4, 4, 4, 1.0, 0, 4, 0, 4, 0.0, 0, 4), ("N", "N", 4, 4, 4, 1.0, 0, 3, 0, 4, 0.0, 0, 4)]
     rc, _ = ft.ftgemm_batched(probs)
     assert rc == -(100 * 1 + 8)
+
+
+def test_batched_every_block_count_equals_single_calls(ft, orc):
+    """The batched kernel computes a tile's valid rows and columns rounded up
+    to 16 (any of 1..8 accumulator blocks each way, in binary pieces); every
+    accumulator still gets the same FMAs in the same order as in ftgemm_d's
+    whole-tile kernel, so each problem's output equals one ftgemm_d call (K
+    not split) bit for bit.  Row and column extents 16r - 3 and 16c - 7 cover
+    every block count; two problems span several tiles with ragged edges."""
+    shapes = []
+    for q in range(8):
+        r, c = q + 1, 8 - q
+        shapes.append(("N", "N", 16 * r - 3, 16 * c - 7, (1, 15, 17, 100)[q % 4], 1.5, (0.0, 0.5)[q % 2]))
+        shapes.append(("T", "N", 16 * c - 3, 16 * r - 7, (33, 64, 5, 250)[q % 4], -0.75, (1.0, 0.0)[q % 2]))
+    shapes += [("N", "T", 200, 333, 129, 1.0, 1.0), ("T", "T", 257, 144, 48, 2.0, 0.5)]
+    host, dev, probs = make_batch(shapes, seed=4242)
+    rc, reps = ft.ftgemm_batched(probs)
+    torch.cuda.synchronize()
+    assert rc == 0, ft.ftgemm_strerror(rc)
+    assert ft.ftgemm_set_splitk(1) == 0
+    try:
+        for q, (ta, tb, m, n, k, alpha, beta) in enumerate(shapes):
+            A, B, C, ar, br = host[q]
+            dC = C.cuda()
+            rc1, rep1 = ft.ftgemm_d(ta, tb, m, n, k, alpha, A.cuda(), A.shape[1], B.cuda(), B.shape[1], beta, dC,
+                                    C.shape[1])
+            torch.cuda.synchronize()
+            assert rc1 == 0
+            assert torch.equal(dev[q][2].cpu()[:, :m], dC.cpu()[:, :m]), shapes[q]
+            check_problem(orc, shapes[q], host[q], dev[q][2])
+            assert reps[q]["detected"] == 0 and reps[q]["unverifiable"] == 0
+    finally:
+        ft.ftgemm_set_splitk(0)
+
+
+@pytest.mark.parametrize("layout", ["NN", "TT"])
+def test_batched_checks_at_the_edges_of_the_fp32_range(ft, orc, layout):
+    """The batched checksum pass keeps the operands' absolute sums in FP32
+    (rounded upward) and takes them again in FP64 where FP32's range would
+    overflow them or leave them loose.  Operands scaled by 2^140 / 2^-140
+    (FP32 overflow) and by 2^-400 each (every |x| under FP32's smallest
+    number, products near 2^-800) stay verifiable: no unverifiable count, no
+    false positive, each problem's one exponent flip detected at its element
+    and corrected, every output within the parity bound (in both layouts, so
+    both shapes of the pass see both scales)."""
+    ta, tb = layout
+    shapes = [(ta, tb, 150, 170, 90, 1.0, 1.0), (ta, tb, 140, 60, 200, 1.0, 0.0), (ta, tb, 100, 100, 100, 1.5, 0.5)]
+    scales = [(2.0 ** 140, 2.0 ** -140), (2.0 ** -400, 2.0 ** -400), (1.0, 1.0)]
+    host, dev, probs = make_batch(shapes, seed=77)
+    for q, (sa, sb) in enumerate(scales):
+        A, B, C, ar, br = host[q]
+        A.mul_(sa)
+        B.mul_(sb)
+        C.mul_(sa * sb)
+        dev[q][0].copy_(A)
+        dev[q][1].copy_(B)
+        dev[q][2].copy_(C)
+    flips = [(7, 11, 2, 60, 0), (100, 33, 5, 61, 1), (50, 50, 3, 60, 2)]
+    assert ft.ftgemm_set_injection(mode=2, flips=flips) == 0
+    try:
+        plan = ft.BatchedPlan(probs)
+    finally:
+        ft.ftgemm_set_injection(mode=0)
+    plan.launch()
+    rc, reps = plan.report()
+    plan.destroy()
+    assert rc == 0
+    for q, sh in enumerate(shapes):
+        assert reps[q]["unverifiable"] == 0, (q, reps[q])
+        assert reps[q]["detected"] == 1 and reps[q]["corrected"] == 1, (q, reps[q])
+        assert reps[q]["locs"][0][:2] == flips[q][:2]
+        check_problem(orc, sh, host[q], dev[q][2])
+
+
+def test_tune_batched_picks_a_plan_that_matches_the_oracle(ft, orc, tmp_path):
+    """The autotuner on a small mixed batch (every layout, ragged sizes): it
+    times every candidate schedule, caches the choice (a second call returns
+    it untimed), and a plan built with the chosen schedule matches the oracle
+    problem by problem, with no check raised."""
+    from paper_2305_02444_gb300 import autotune
+    rng = np.random.default_rng(5)
+    shapes = random_shapes(rng, 20, 8, 260)
+    cache = str(tmp_path / "sched.json")
+    tune_shapes = [(ta, tb, m, n, k) for (ta, tb, m, n, k, _, _) in shapes]
+    best, times = autotune.tune_batched(tune_shapes, reps=2, cache_path=cache)
+    assert set(times) == set(autotune.CANDIDATES) and best in autotune.CANDIDATES
+    assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+    again, cached = autotune.tune_batched(tune_shapes, reps=2, cache_path=cache)
+    assert again == best and {int(k) for k in cached} == set(times)
+    host, dev, probs = make_batch(shapes, seed=600)
+    plan = ft.BatchedPlan(probs, schedule=best)
+    plan.launch()
+    rc, reps = plan.report()
+    plan.destroy()
+    assert rc == 0
+    for q, sh in enumerate(shapes):
+        check_problem(orc, sh, host[q], dev[q][2])
+        assert reps[q]["detected"] == 0 and reps[q]["flagged_rows"] == 0 and reps[q]["flagged_cols"] == 0
