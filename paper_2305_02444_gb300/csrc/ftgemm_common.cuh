@@ -219,6 +219,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return false;
 }
 
+// Byte offset of element (row, k) of a [rows][16] fp64 tile written by TMA with
+// 128-byte swizzle: the 16-byte chunk index is XORed with row % 8.
+__device__ __forceinline__ int swz_off(int row, int k) {
+  return row * 128 + ((((k >> 1) ^ (row & 7)) << 4) | ((k & 1) << 3));
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int c0, int c1) {
   asm volatile(

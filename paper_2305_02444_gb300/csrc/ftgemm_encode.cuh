@@ -187,28 +187,40 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
   enc_group_finish(cnt, G, nG, (int)gridDim.y, s0, S, part_cabs, part_max, cabs_out, gmax);
 }
 
-// Batched checksum pass: one item per operand of each problem of a batch, of
-// the SEG or the STR shape; every block covers one 128-wide group of one item
-// over the item's whole other dimension, so each result is written once (no
-// partials).  The host orders the items by the length of their blocks,
-// longest first, so that the long blocks start in the first wave.
-//
+// Batched checksum pass: one item per operand of each problem of a batch;
+// one block per 128-wide group of an item (the x dimension: rows i of op(A),
+// columns j of op(B)), over the item's whole k dimension.  Each item comes
+// in through the problem's own TMA map as the GEMM's 128 x 16 slabs, into a
+// ring of ENC_STAGES slabs with bounded waits, so the loads of later slabs
+// overlap the sums of the current one.  Per group G:
+//   gsum[G][k] = sum over the group's x of X(x, k)        (FP64)
+//   absv[x]    = sum over k of |X(x, k)|                   (per x)
+//   gmax[G]    = max over k of sum over the group's x of |X(x, k)|
 // The checksum sums are FP64.  The absolute sums, which only bound the
 // rounding in the detection thresholds, run on the FP32 pipe with upward
-// rounding (each partial stays an upper bound of the FP64 sum), which leaves
-// about one FP64 add per operand element.  Where the range makes an FP32
-// absolute sum overflow or leaves it tiny (below 2^-90, where terms under
+// rounding (each partial stays an upper bound of the FP64 sum); where FP32's
+// range makes one overflow or leaves it tiny (below 2^-90, where terms under
 // FP32's normal range were rounded up to its smallest numbers), the block
-// takes its absolute sums again in FP64.
+// takes its absolute sums again in FP64 from global memory.  The host orders
+// the items by their k extent, longest first, so the long blocks start in
+// the first wave.
+constexpr int ENC_STAGES = 4;
+constexpr int ENC_SLAB = BM * BK * 8;  // one 128 x 16 slab, 16 KiB
+constexpr int ENC_SMEM_BYTES = ENC_STAGES * ENC_SLAB + 1024;
+
 struct EncItem {
-  const double *X;       // column-major R x S
-  long long R, S, ld;
-  double *gsum;          // group sums, gsum[G * gstride + (s or r)]
+  const CUtensorMap *map;  // the operand's TMA map (128 x 16 boxes), in global memory
+  const double *X;         // the operand, column-major (for the FP64 absolute sums)
+  long long ld;
+  long long W, L;          // extents of x and k
+  double *gsum;            // gsum[G * gstride + k], k < 16 * ceil(L / 16)
   long long gstride;
-  double *absv;          // SEG: row abs sums (R); STR: column abs sums (S)
-  double *gmax;          // per group: max of the group's abs sums
-  int first_block;       // prefix sum of the items' group counts
-  int seg;               // 1: SEG, 0: STR
+  double *absv;            // absv[x]
+  double *gmax;            // gmax[G]
+  int *err;                // the problem's report flag (a wait that timed out)
+  int first_block;         // prefix sum of the items' group counts
+  int kfirst;              // 1: X(x, k) = X[k + x ld], slab [128 x][16 k] 128-byte swizzled
+                           // 0: X(x, k) = X[x + k ld], slab [16 k][128 x]
 };
 
 __device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b) {
@@ -224,20 +236,6 @@ __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
-}
-
-// colsum16 on the FP32 pipe, every addition rounded upward.
-__device__ __forceinline__ float colsum16_ru(float (&v)[16], int lane) {
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const float send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
-      v[i] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, o));
-    }
-  }
-  return __fadd_ru(v[0], __shfl_xor_sync(0xffffffffu, v[0], 16));
 }
 
 // The transposing butterfly for 8 columns: lane l's v[c] is its part of
@@ -267,212 +265,140 @@ __device__ __forceinline__ T colsum8(T (&v)[8], int lane) {
 // NaN (from a NaN operand) stands: the FP64 sum is NaN as well.
 __device__ __forceinline__ bool abs32_loose(float s) { return isinf(s) || (s > 0.0f && s < 0x1p-90f); }
 
-// Elements r and r + 1 (r even) of a column as one 16-byte load (the batched
-// operands are 16-byte aligned with even leading dimensions); an element past
-// the last row reads as zero.
-__device__ __forceinline__ double2 load_pair(const double *col, long long r, long long R) {
-  double2 v = make_double2(0.0, 0.0);
-  if (r < R) {
-    v = __ldg(reinterpret_cast<const double2 *>(col + r));
-    if (r + 1 >= R) v.y = 0.0;
-  }
-  return v;
+__device__ __forceinline__ double enc_global(const EncItem &E, long long x, long long k) {
+  return E.kfirst ? E.X[k + x * E.ld] : E.X[x + k * E.ld];
 }
 
-// SEG over the 128-row group G, all columns of the item: warp w takes batches
-// of 8 columns (8w, 8w + 64, ...), lane l the rows 2l, 2l + 1, 2l + 64 and
-// 2l + 65 of each column (two 16-byte loads; a batch's 16 loads are issued
-// before any is used); a column's sum is the lanes' 4-row partials reduced by
-// the transposing butterfly.
-__device__ __forceinline__ void enc_seg_group(const EncItem &E, int G, float (*s_abs)[128], float *s_mx,
-                                              double *s_md) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long r0 = (long long)G * 128;
-  float rabs[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // rows 2l, 2l + 1, 2l + 64, 2l + 65
-  float mx = 0.0f;
-  for (long long sb = 8 * w; sb < E.S; sb += 64) {
-    double2 v[8][2];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const long long s = sb + j;
-      const double *col = E.X + min(s, E.S - 1) * E.ld;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) v[j][h] = load_pair(col, r0 + 64 * h + 2 * lane, s < E.S ? E.R : 0);
-    }
+// 256 threads: thread t takes x = t mod 128 and the 8 k's 8h..8h+7 of every
+// slab (h = t / 128).  A warp's 32 x's reduce each k by the transposing
+// butterfly; the 4 warps of a half add their parts through shared memory in
+// a fixed order.  A warp whose x's all lie past the group's last valid x
+// skips its loads and sums.
+__global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restrict__ items, int nitems, int *gerr,
+                                                         unsigned long long limit_ns) {
+  extern __shared__ unsigned char enc_smem_raw[];
+  unsigned char *ring =
+      reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(enc_smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ double s_part[2][4][8];
+  __shared__ float s_apart[2][4][8];
+  __shared__ float s_xabs[128];
+  __shared__ double s_md[8];
+  __shared__ __align__(8) uint64_t s_full[ENC_STAGES];
+  __shared__ int s_stop;
+  const int it = find_item(items, nitems, blockIdx.x);
+  const EncItem E = items[it];
+  const int G = blockIdx.x - E.first_block;
+  const long long x0 = (long long)G * 128;
+  const int xv = (int)min(128LL, E.W - x0);
+  const int nsl = (int)((E.L + BK - 1) / BK);
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, x = tid & 127, h = tid >> 7;
+  const bool wact = 32 * (w & 3) < xv;
+  const uint32_t full0 = smem_u32(s_full);
+  if (tid == 0) {
+    s_stop = *reinterpret_cast<volatile int *>(gerr) != 0;
+    for (int s = 0; s < ENC_STAGES; ++s) mbar_init(full0 + 8 * s, 1);
+    fence_mbar_init();
+    prefetch_tmap(E.map);
+  }
+  __syncthreads();
+  if (s_stop) return;
+  auto issue = [&](int s) {
+    const int st = s % ENC_STAGES;
+    const uint32_t fb = full0 + 8 * st, sb = smem_u32(ring + st * ENC_SLAB);
+    mbar_arrive_expect_tx(fb, ENC_SLAB);
+    if (E.kfirst) tma_load_2d(sb, E.map, fb, BK * s, (int)x0);
+    else tma_load_2d(sb, E.map, fb, (int)x0, BK * s);
+  };
+  int issued = 0;
+  if (tid == 0)
+    for (; issued < ENC_STAGES && issued < nsl; ++issued) issue(issued);
+  float xa = 0.0f;    // this thread's x: |X(x, k)| over its k's, rounded upward
+  float kmax = 0.0f;  // threads < 16: the largest group absolute sum of the k's they finished
+  bool ok = true;
+  int s = 0;
+  for (; s < nsl; ++s) {
+    const int st = s % ENC_STAGES;
+    if (!mbar_wait_bounded(full0 + 8 * st, (s / ENC_STAGES) & 1, limit_ns, E.err)) ok = false;
     double ps[8];
     float pa[8];
+    if (ok && wact) {
+      const unsigned char *sl = ring + st * ENC_SLAB;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float a0 = f32_ru_abs(v[j][0].x), a1 = f32_ru_abs(v[j][0].y);
-      const float a2 = f32_ru_abs(v[j][1].x), a3 = f32_ru_abs(v[j][1].y);
-      rabs[0] = __fadd_ru(rabs[0], a0);
-      rabs[1] = __fadd_ru(rabs[1], a1);
-      rabs[2] = __fadd_ru(rabs[2], a2);
-      rabs[3] = __fadd_ru(rabs[3], a3);
-      ps[j] = (v[j][0].x + v[j][0].y) + (v[j][1].x + v[j][1].y);
-      pa[j] = __fadd_ru(__fadd_ru(a0, a1), __fadd_ru(a2, a3));
+      for (int c = 0; c < 8; ++c) {
+        const int k = 8 * h + c;
+        const double v = E.kfirst ? *reinterpret_cast<const double *>(sl + swz_off(x, k))
+                                  : reinterpret_cast<const double *>(sl)[k * BM + x];
+        ps[c] = v;
+        pa[c] = f32_ru_abs(v);
+        xa = __fadd_ru(xa, pa[c]);
+      }
+      const double cs = colsum8<double, false>(ps, lane);
+      const float ca = colsum8<float, true>(pa, lane);
+      if (lane < 8) {
+        s_part[h][w & 3][lane] = cs;
+        s_apart[h][w & 3][lane] = ca;
+      }
+    } else if (lane < 8) {
+      s_part[h][w & 3][lane] = 0.0;
+      s_apart[h][w & 3][lane] = 0.0f;
     }
-    const double sum = colsum8<double, false>(ps, lane);
-    const float ab = colsum8<float, true>(pa, lane);
-    const long long s = sb + (lane & 7);
-    if (lane < 8 && s < E.S) {
-      E.gsum[(long long)G * E.gstride + s] = sum;
-      mx = fmaxf(mx, ab);
+    if (__syncthreads_or(!ok)) break;  // stage st is read; the partials are in
+    if (tid == 0 && issued < nsl) issue(issued++);
+    if (tid < 16) {
+      const int hh = tid >> 3, c = tid & 7;
+      const double g = ((s_part[hh][0][c] + s_part[hh][1][c]) + s_part[hh][2][c]) + s_part[hh][3][c];
+      const float ga = __fadd_ru(__fadd_ru(s_apart[hh][0][c], s_apart[hh][1][c]),
+                                 __fadd_ru(s_apart[hh][2][c], s_apart[hh][3][c]));
+      E.gsum[(long long)G * E.gstride + BK * s + tid] = g;
+      kmax = fmaxf(kmax, ga);
     }
+    __syncthreads();  // the partials are read before the next slab's are written
   }
-  s_abs[w][2 * lane] = rabs[0];
-  s_abs[w][2 * lane + 1] = rabs[1];
-  s_abs[w][2 * lane + 64] = rabs[2];
-  s_abs[w][2 * lane + 65] = rabs[3];
-  mx = warp_max(mx);
-  if (lane == 0) s_mx[w] = mx;
-  __syncthreads();
-  float t = 0.0f, m = 0.0f;
-  bool loose = false;
-  const long long r = r0 + threadIdx.x;
-  if (threadIdx.x < 128) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) t = __fadd_ru(t, s_abs[q][threadIdx.x]);
-    loose = r < E.R && abs32_loose(t);
-  }
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 8; ++q) m = fmaxf(m, s_mx[q]);
-    loose = loose || abs32_loose(m);
-  }
-  if (!__syncthreads_or(loose)) {
-    if (threadIdx.x < 128 && r < E.R) E.absv[r] = (double)t;
-    if (threadIdx.x == 0) E.gmax[G] = (double)m;
+  if (s < nsl) {  // a wait timed out: stop the batch; the copies in flight get a bounded chance to land
+    if (tid == 0) {
+      atomicExch(gerr, ERR_TIMEOUT);
+      for (int q = s; q < issued; ++q)
+        mbar_wait_bounded(full0 + 8 * (q % ENC_STAGES), (q / ENC_STAGES) & 1, limit_ns, E.err);
+    }
     return;
   }
-  // FP64 absolute sums: thread t the row r0 + t; warp w the columns w, w + 8, ...
-  if (threadIdx.x < 128 && r < E.R) {
-    double a = 0.0;
-    for (long long s = 0; s < E.S; ++s) a += fabs(E.X[r + s * E.ld]);
-    E.absv[r] = a;
-  }
-  double md = 0.0;
-  for (long long s = w; s < E.S; s += 8) {
-    double a = 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long rr = r0 + lane + 32 * q;
-      if (rr < E.R) a += fabs(E.X[rr + s * E.ld]);
-    }
-    md = fmax(md, warp_sum(a));
-  }
-  if (lane == 0) s_md[w] = md;
+  if (h) s_xabs[x] = xa;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double g = 0.0;
-    for (int q = 0; q < 8; ++q) g = fmax(g, s_md[q]);
-    E.gmax[G] = g;
-  }
-}
-
-// STR over the 128-column group G, all rows of the item: warp w takes the
-// 64-row chunks w, w + 8, ..., lane l the rows 2l and 2l + 1 of a chunk over
-// all of the group's columns (one 16-byte load per column; 16 columns' loads
-// are issued before any is used), so a row's sum over the group stays in one
-// lane (columns in ascending order).  The columns' absolute sums over the
-// chunk are reduced across the warp by the transposing butterfly and kept per
-// lane; the warps' parts are added once at the end.
-__device__ __forceinline__ void enc_str_group(const EncItem &E, int G, float (*s_cab)[128], float *s_mx,
-                                              double *s_md) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long s0 = (long long)G * 128;
-  const int ns = (int)min(128LL, E.S - s0);
-  // s_cab[w][c]: column c's absolute sum over warp w's chunks (the warp's own row)
-  if (lane < 16) {
-#pragma unroll
-    for (int b = 0; b < 8; ++b) s_cab[w][16 * b + lane] = 0.0f;
-  }
-  __syncwarp();
-  float mloc = 0.0f;
-  for (long long r0 = 64LL * w; r0 < E.R; r0 += 512) {
-    const long long r = r0 + 2 * lane;
-    double rs0 = 0.0, rs1 = 0.0;
-    float ra0 = 0.0f, ra1 = 0.0f;
-#pragma unroll 1
-    for (int b = 0; 16 * b < ns; ++b) {
-      double2 v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int sl = 16 * b + q;
-        v[q] = load_pair(E.X + (s0 + min(sl, ns - 1)) * E.ld, r, sl < ns ? E.R : 0);
-      }
-      float pc[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        rs0 += v[q].x;
-        rs1 += v[q].y;
-        const float fa = f32_ru_abs(v[q].x), fb = f32_ru_abs(v[q].y);
-        ra0 = __fadd_ru(ra0, fa);
-        ra1 = __fadd_ru(ra1, fb);
-        pc[q] = __fadd_ru(fa, fb);
-      }
-      const float cs = colsum16_ru(pc, lane);
-      if (lane < 16) s_cab[w][16 * b + lane] = __fadd_ru(s_cab[w][16 * b + lane], cs);
-    }
-    if (r < E.R) {
-      E.gsum[(long long)G * E.gstride + r] = rs0;
-      mloc = fmaxf(mloc, ra0);
-    }
-    if (r + 1 < E.R) {
-      E.gsum[(long long)G * E.gstride + r + 1] = rs1;
-      mloc = fmaxf(mloc, ra1);
-    }
-  }
-  mloc = warp_max(mloc);
-  if (lane == 0) s_mx[w] = mloc;
-  __syncthreads();
-  float cs = 0.0f, gm = 0.0f;
+  float xs = 0.0f, gm = 0.0f;
   bool loose = false;
-  if (threadIdx.x < ns) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cs = __fadd_ru(cs, s_cab[q][threadIdx.x]);
-    loose = abs32_loose(cs);
+  if (!h) {
+    xs = __fadd_ru(xa, s_xabs[x]);
+    loose = x < xv && abs32_loose(xs);
   }
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 8; ++q) gm = fmaxf(gm, s_mx[q]);
-    loose = loose || abs32_loose(gm);
+  if (w == 0) {
+    gm = warp_max(kmax);
+    loose = loose || (lane == 0 && abs32_loose(gm));
   }
   if (!__syncthreads_or(loose)) {
-    if (threadIdx.x < ns) E.absv[s0 + threadIdx.x] = (double)cs;
-    if (threadIdx.x == 0) E.gmax[G] = (double)gm;
+    if (!h && x < xv) E.absv[x0 + x] = (double)xs;
+    if (tid == 0) E.gmax[G] = (double)gm;
     return;
   }
-  // FP64 absolute sums: thread t the column s0 + t; rows strided over the block
-  if ((int)threadIdx.x < ns) {
-    const double *col = E.X + (s0 + threadIdx.x) * E.ld;
+  // FP64 absolute sums: thread t the x's absolute sum; the k's strided over the block
+  if (tid < xv) {
     double a = 0.0;
-    for (long long rr = 0; rr < E.R; ++rr) a += fabs(col[rr]);
-    E.absv[s0 + threadIdx.x] = a;
+    for (long long k = 0; k < E.L; ++k) a += fabs(enc_global(E, x0 + tid, k));
+    E.absv[x0 + tid] = a;
   }
   double md = 0.0;
-  for (long long rr = threadIdx.x; rr < E.R; rr += 256) {
+  for (long long k = tid; k < E.L; k += 256) {
     double a = 0.0;
-    for (int sl = 0; sl < ns; ++sl) a += fabs(E.X[rr + (s0 + sl) * E.ld]);
+    for (int xx = 0; xx < xv; ++xx) a += fabs(enc_global(E, x0 + xx, k));
     md = fmax(md, a);
   }
   md = warp_max(md);
   if (lane == 0) s_md[w] = md;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double g = 0.0;
     for (int q = 0; q < 8; ++q) g = fmax(g, s_md[q]);
     E.gmax[G] = g;
   }
-}
-
-__global__ void __launch_bounds__(256, 2) enc_batched_kernel(const EncItem *__restrict__ items, int nitems) {
-  __shared__ float s_abs[8][128];
-  __shared__ float s_mx[8];
-  __shared__ double s_md[8];
-  const int it = find_item(items, nitems, blockIdx.x);
-  const EncItem &E = items[it];
-  const int G = blockIdx.x - E.first_block;
-  if (E.seg) enc_seg_group(E, G, s_abs, s_mx, s_md);
-  else enc_str_group(E, G, s_abs, s_mx, s_md);
 }
 
 // One pass over C that takes, per 128x128 tile, the column sums over the

@@ -1775,27 +1775,25 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
   PLAN_TRY(plan_alloc(P, &dprobs, hp.size()));
   cudaMemcpy(dprobs, hp.data(), sizeof(BatchProblem) * hp.size(), cudaMemcpyHostToDevice);
 
-  // checksum-pass items: op(A) 'N' and op(B) 'T' are SEG, the others STR; one
-  // block per 128-wide group, the items ordered by the length of their blocks
-  // (the other dimension), longest first
+  // checksum-pass items, one per operand, read through the problem's own TMA
+  // maps (in dprobs); one block per 128-wide group, the items ordered by their
+  // k extent, longest first
   std::vector<EncItem> items;
   int enc_blocks = 0;
   for (long long q = 0; q < count && P->ft; ++q) {
     if (!work[q]) continue;
     EncItem a{}, b{};
-    if (!is_t(transA[q])) { a.X = A[q]; a.R = M[q]; a.S = K[q]; a.seg = 1; }
-    else { a.X = A[q]; a.R = K[q]; a.S = M[q]; a.seg = 0; }
-    a.ld = lda[q]; a.gsum = enc + off_acs[q]; a.gstride = Kp[q]; a.absv = enc + off_ar[q]; a.gmax = enc + off_am[q];
-    if (!is_t(transB[q])) { b.X = B[q]; b.R = K[q]; b.S = N[q]; b.seg = 0; }
-    else { b.X = B[q]; b.R = N[q]; b.S = K[q]; b.seg = 1; }
-    b.ld = ldb[q]; b.gsum = enc + off_bcs[q]; b.gstride = Kp[q]; b.absv = enc + off_bc[q]; b.gmax = enc + off_bm[q];
+    a.map = &dprobs[q].tmA; a.X = A[q]; a.ld = lda[q]; a.W = M[q]; a.L = K[q]; a.kfirst = is_t(transA[q]) ? 1 : 0;
+    a.gsum = enc + off_acs[q]; a.gstride = Kp[q]; a.absv = enc + off_ar[q]; a.gmax = enc + off_am[q];
+    b.map = &dprobs[q].tmB; b.X = B[q]; b.ld = ldb[q]; b.W = N[q]; b.L = K[q]; b.kfirst = is_t(transB[q]) ? 0 : 1;
+    b.gsum = enc + off_bcs[q]; b.gstride = Kp[q]; b.absv = enc + off_bc[q]; b.gmax = enc + off_bm[q];
+    a.err = b.err = &P->reps[q].err;
     a.first_block = (int)nI[q];   // group counts until the prefix sums below
     b.first_block = (int)nJ[q];
     items.push_back(a);
     items.push_back(b);
   }
-  auto blen = [](const EncItem &e) { return e.seg ? e.S : e.R; };
-  std::stable_sort(items.begin(), items.end(), [&](const EncItem &x, const EncItem &y) { return blen(x) > blen(y); });
+  std::stable_sort(items.begin(), items.end(), [](const EncItem &x, const EncItem &y) { return x.L > y.L; });
   for (EncItem &e : items) {
     const int groups = e.first_block;
     e.first_block = enc_blocks;
@@ -1804,6 +1802,12 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
   EncItem *ditems = nullptr;
   PLAN_TRY(plan_alloc(P, &ditems, std::max<size_t>(1, items.size())));
   if (!items.empty()) cudaMemcpy(ditems, items.data(), sizeof(EncItem) * items.size(), cudaMemcpyHostToDevice);
+  if (enc_blocks && cudaFuncSetAttribute(enc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ENC_SMEM_BYTES) != cudaSuccess) {
+    cudaGetLastError();
+    plan_free(P);
+    return FTGEMM_ERR_CUDA;
+  }
 
   // work lists per operand layout, in the scheduled order
   struct Group { std::vector<int> prob, local, order; };
@@ -1853,7 +1857,10 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
     cudaMemsetAsync(P->reps, 0, sizeof(DevReport) * std::max<long long>(1, count), cs);
     if (P->ft && enc_total) {
       cudaMemsetAsync(enc, 0, sizeof(double) * enc_total, cs);
-      if (enc_blocks) { enc_batched_kernel<<<enc_blocks, 256, 0, cs>>>(ditems, (int)items.size()); P->kernels++; }
+      if (enc_blocks) {
+        enc_batched_kernel<<<enc_blocks, 256, ENC_SMEM_BYTES, cs>>>(ditems, (int)items.size(), gerr, wait_limit_ns());
+        P->kernels++;
+      }
     }
     for (long long q = 0; q < count; ++q)
       if (!work[q] && M[q] > 0 && N[q] > 0 && beta[q] != 1.0) {

@@ -26,12 +26,6 @@
 
 namespace ftg {
 
-// Byte offset of element (row, k) of a [rows][16] fp64 tile written by TMA with
-// 128-byte swizzle: the 16-byte chunk index is XORed with row % 8.
-__device__ __forceinline__ int swz_off(int row, int k) {
-  return row * 128 + ((((k >> 1) ^ (row & 7)) << 4) | ((k & 1) << 3));
-}
-
 // op(A)(i,k) of the staged slab: 'N' slabs are [BK][BM] (i contiguous),
 // 'T' slabs are [BM][BK] swizzled.
 template <bool TA>
