@@ -313,23 +313,26 @@ __device__ __forceinline__ uint32_t bf16_rn_bits(double x) {
 }
 
 // |x| rounded upward to FP32 (the result of __double2float_ru(fabs(x)), a NaN
-// for a NaN), with integer operations only: the absolute sums of the
-// detection thresholds run over every element of partly filled tiles (zeros
-// included), and a conversion from FP64 would take the FP64 pipe.
+// for a NaN), with integer operations only, on the two 32-bit halves of x (a
+// mask of the 64-bit pattern reads as fabs and would take the FP64 pipe): the
+// absolute sums of the detection thresholds run over every element of the
+// operands and of partly filled tiles (zeros included), and the FP64 pipe is
+// this GPU's scarcest unit.
 __device__ __forceinline__ float f32_ru_abs(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  const int E = (int)(b >> 52), ef = E - 1023 + 127;
+  const uint32_t hi = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu, lo = (uint32_t)__double2loint(x);
+  const int E = (int)(hi >> 20), ef = E - 1023 + 127;
   if (ef >= 1 && ef <= 254) {  // a normal FP32 result (or, by the carry, Inf)
-    uint32_t v = ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu);
-    v += (b & 0x1FFFFFFFull) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
+    uint32_t v = ((uint32_t)ef << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    v += (lo & 0x1FFFFFFFu) ? 1u : 0u;  // a carry moves into the exponent (or to Inf)
     return __uint_as_float(v);
   }
-  if (ef > 254) return __uint_as_float(b > 0x7FF0000000000000ull ? 0x7FFFFFFFu : 0x7F800000u);  // NaN; Inf
-  if (b == 0) return 0.0f;
+  if (ef > 254)  // NaN; Inf
+    return __uint_as_float((hi > 0x7FF00000u || (hi == 0x7FF00000u && lo != 0u)) ? 0x7FFFFFFFu : 0x7F800000u);
+  if ((hi | lo) == 0u) return 0.0f;
   // below FP32's normal range: |x| = m 2^(max(E,1) - 1075), that is m 2^-sh in
   // units of FP32's smallest subnormal 2^-149 (sh >= 30), rounded up; q <= 2^23
   // (2^23 is the bit pattern of the smallest normal number)
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (E ? (1ull << 52) : 0ull);
+  const unsigned long long m = ((unsigned long long)(hi & 0xFFFFFu) << 32 | lo) | (E ? (1ull << 52) : 0ull);
   const int sh = 926 - (E ? E : 1);
   const uint32_t q = sh >= 64 ? 1u : (uint32_t)(m >> sh) + ((m & ((1ull << sh) - 1ull)) ? 1u : 0u);
   return __uint_as_float(q);

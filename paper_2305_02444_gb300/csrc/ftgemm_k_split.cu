@@ -46,10 +46,12 @@ cudaError_t launch_split(bool ta, bool tb, int ck, bool i8, const CUtensorMap &a
 // pipe is the scarce unit of this GPU.
 
 // |x| as ordered bits (the order of non-negative doubles is that of their bit
-// patterns); non-finite entries count as 0 for the row exponent.
+// patterns); non-finite entries count as 0 for the row exponent.  Built from
+// the two 32-bit halves: a mask of the 64-bit pattern reads as fabs and would
+// take the FP64 pipe.
 __device__ __forceinline__ unsigned long long abs_bits_finite(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  return b < 0x7FF0000000000000ull ? b : 0ull;
+  const uint32_t hi = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu, lo = (uint32_t)__double2loint(x);
+  return hi < 0x7FF00000u ? ((unsigned long long)hi << 32 | lo) : 0ull;
 }
 
 // e with |x| < 2^e for the largest |x| given by its bits (0 for zero).
