@@ -528,7 +528,8 @@ def split(args):
     """Split precision at M = N = K = 8192 (or --size), entries sign-random with
     |x| log-uniform in [1e-3, 1e3]: FP64 emulated with S BF16 slices and the
     plain BF16 form, FP32 checksums / FP64 verify, one flip per 64 tiles (top
-    exponent bit of the FP64 accumulator after a random slice pair); against
+    exponent bit of the FP64 accumulator after a random slice pair; exponent
+    bit 9 of the plain form's accumulator); against
     the DFMA FP64 path on the same inputs; max error vs the FP64 oracle on
     sampled rows."""
     import numpy as np
@@ -608,7 +609,13 @@ def split(args):
         if S is None:
             ftgemm.ftgemm_set_injection(mode=1, seed=SEED, count=nflip)
         else:
-            flips = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(npairs)), 62) for _ in range(nflip)]
+            # emulated forms: the top exponent bit of the FP64 accumulator after a
+            # random slice pair; plain form: exponent bit 9 (the value times 2^512
+            # for accumulators in [2, 2^513)), since clearing the top bit only
+            # zeroes an element, which at K = 8192 lies below the FP32-carried
+            # threshold (about 2^-8 of the column's absolute checksum)
+            bit = 61 if S == 0 else 62
+            flips = [(int(rng.integers(n)), int(rng.integers(n)), int(rng.integers(npairs)), bit) for _ in range(nflip)]
             ftgemm.ftgemm_set_injection(mode=2, flips=flips)
         C.copy_(C0)
         if S is None:

@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restr
   extern __shared__ unsigned char enc_smem_raw[];
   unsigned char *ring =
       reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(enc_smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ double s_part[2][4][8];
-  __shared__ float s_apart[2][4][8];
+  __shared__ double s_part[2][2][4][8];  // [slab parity][half][warp of the half][k]
+  __shared__ float s_apart[2][2][4][8];
   __shared__ float s_xabs[128];
   __shared__ double s_md[8];
   __shared__ __align__(8) uint64_t s_full[ENC_STAGES];
@@ -335,24 +335,29 @@ __global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restr
       const double cs = colsum8<double, false>(ps, lane);
       const float ca = colsum8<float, true>(pa, lane);
       if (lane < 8) {
-        s_part[h][w & 3][lane] = cs;
-        s_apart[h][w & 3][lane] = ca;
+        s_part[s & 1][h][w & 3][lane] = cs;
+        s_apart[s & 1][h][w & 3][lane] = ca;
       }
     } else if (lane < 8) {
-      s_part[h][w & 3][lane] = 0.0;
-      s_apart[h][w & 3][lane] = 0.0f;
+      s_part[s & 1][h][w & 3][lane] = 0.0;
+      s_apart[s & 1][h][w & 3][lane] = 0.0f;
     }
-    if (__syncthreads_or(!ok)) break;  // stage st is read; the partials are in
+    // one barrier per slab: stage st is read and the partials are in; the
+    // partials alternate between two buffers, so the next slab's cannot
+    // overwrite these before they are read (a thread writes slab s + 2's
+    // only after passing slab s + 1's barrier, which the readers of slab s
+    // reach after reading)
+    if (__syncthreads_or(!ok)) break;
     if (tid == 0 && issued < nsl) issue(issued++);
     if (tid < 16) {
       const int hh = tid >> 3, c = tid & 7;
-      const double g = ((s_part[hh][0][c] + s_part[hh][1][c]) + s_part[hh][2][c]) + s_part[hh][3][c];
-      const float ga = __fadd_ru(__fadd_ru(s_apart[hh][0][c], s_apart[hh][1][c]),
-                                 __fadd_ru(s_apart[hh][2][c], s_apart[hh][3][c]));
+      const double(*pp)[8] = s_part[s & 1][hh];
+      const float(*pa2)[8] = s_apart[s & 1][hh];
+      const double g = ((pp[0][c] + pp[1][c]) + pp[2][c]) + pp[3][c];
+      const float ga = __fadd_ru(__fadd_ru(pa2[0][c], pa2[1][c]), __fadd_ru(pa2[2][c], pa2[3][c]));
       E.gsum[(long long)G * E.gstride + BK * s + tid] = g;
       kmax = fmaxf(kmax, ga);
     }
-    __syncthreads();  // the partials are read before the next slab's are written
   }
   if (s < nsl) {  // a wait timed out: stop the batch; the copies in flight get a bounded chance to land
     if (tid == 0) {
