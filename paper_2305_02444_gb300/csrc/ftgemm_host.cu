@@ -84,6 +84,7 @@ struct Workspace {
   cudaStream_t up = nullptr, down = nullptr;
   std::vector<cudaEvent_t> pev;
   Buf prep, ploc, pfl;
+  Buf ppin;  // pinned staging of the panels' fault tables, one region per panel
   // the last injected call, for ftgemm_injection_log: one segment per fault
   // table (a call of panels has one per panel)
   struct LogSeg {
@@ -487,10 +488,41 @@ struct InjPanel {
   const std::vector<long long> *orig;
   void *table;
   long long col_off;
+  const std::vector<long long> *perm;  // set: the table is on the device already, in this order
 };
 
+// The fault table of list L for a grid of ntiles tiles (nI tile rows), in
+// host memory at `stage`: the faults sorted by tile, then k-step, then the
+// per-tile offsets at a 256-byte aligned position (one copy moves both).
+// perm[q] is the list position of table entry q.  Returns the table's bytes
+// before the offsets.
+size_t stage_injection_table(const std::vector<ftgemm_flip> &L, long long nI, long long ntiles, void *stage,
+                             std::vector<long long> &perm) {
+  const long long nf = (long long)L.size();
+  perm.resize((size_t)nf);
+  for (long long q = 0; q < nf; ++q) perm[q] = q;
+  auto tile_of = [&](const ftgemm_flip &f) { return (f.row / BM) + (f.col / BN) * nI; };
+  std::stable_sort(perm.begin(), perm.end(), [&](long long a, long long b) {
+    const long long ta = tile_of(L[a]), tb = tile_of(L[b]);
+    return ta != tb ? ta < tb : L[a].kstep < L[b].kstep;
+  });
+  const size_t fbytes = (sizeof(DevFlip) * (size_t)std::max(1LL, nf) + 255) & ~(size_t)255;
+  DevFlip *hf = (DevFlip *)stage;
+  int *ho = (int *)((char *)stage + fbytes);
+  std::fill(ho, ho + ntiles + 1, 0);
+  for (long long q = 0; q < nf; ++q) {
+    const ftgemm_flip &f = L[perm[q]];
+    hf[q].row = f.row; hf[q].col = f.col; hf[q].kstep = f.kstep; hf[q].bit = f.bit;
+    hf[q].applied = 0; hf[q].before = 0.0; hf[q].after = 0.0; hf[q].kfirst = 0;
+    ho[tile_of(f) + 1]++;
+  }
+  for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
+  return fbytes;
+}
+
 // Build and upload the injection table for this call (FT path only); with
-// `pan`, the panel's list into its own table, appended to the call's log.
+// `pan`, the panel's table, appended to the call's log (already on the
+// device when pan->perm is set).
 int upload_injection(long long M, long long N, long long nks, long long nI, long long ntiles, Workspace &w,
                      cudaStream_t s, Params &p, bool *inj, const InjPanel *pan = nullptr) {
   *inj = false;
@@ -502,40 +534,28 @@ int upload_injection(long long M, long long N, long long nks, long long nI, long
     return rc;
   }
   const long long nf = (long long)L.size();
-  std::vector<long long> perm(nf);
-  for (long long q = 0; q < nf; ++q) perm[q] = q;
-  auto tile_of = [&](const ftgemm_flip &f) { return (f.row / BM) + (f.col / BN) * nI; };
-  std::stable_sort(perm.begin(), perm.end(), [&](long long a, long long b) {
-    const long long ta = tile_of(L[a]), tb = tile_of(L[b]);
-    return ta != tb ? ta < tb : L[a].kstep < L[b].kstep;
-  });
-  // the flip table and the per-tile offsets travel in one copy: one staging
-  // buffer, one device buffer (offsets at a 256-byte aligned position)
   const size_t fbytes = (sizeof(DevFlip) * (size_t)std::max(1LL, nf) + 255) & ~(size_t)255;
   const size_t obytes = sizeof(int) * (size_t)(ntiles + 1);
-  // two pinned staging buffers in turn: the one taken now may still be read
-  // by the copies of the call before the previous one, so wait for its event
-  // (recorded after those copies; long complete when calls follow each other)
-  const int k = w.ipin_next;
-  w.ipin_next ^= 1;
-  if (!w.ipin_ev[k] && cudaEventCreateWithFlags(&w.ipin_ev[k], cudaEventDisableTiming) != cudaSuccess)
-    return FTGEMM_ERR_CUDA;
-  if (cudaEventSynchronize(w.ipin_ev[k]) != cudaSuccess) return FTGEMM_ERR_CUDA;
-  if ((!pan && ensure(w.flips, fbytes + obytes)) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096))
-    return FTGEMM_ERR_NOMEM;
   void *table = pan ? pan->table : w.flips.p;
-  DevFlip *hf = (DevFlip *)w.ipin[k].p;
-  int *ho = (int *)((char *)w.ipin[k].p + fbytes);
-  std::fill(ho, ho + ntiles + 1, 0);
-  for (long long q = 0; q < nf; ++q) {
-    const ftgemm_flip &f = L[perm[q]];
-    hf[q].row = f.row; hf[q].col = f.col; hf[q].kstep = f.kstep; hf[q].bit = f.bit;
-    hf[q].applied = 0; hf[q].before = 0.0; hf[q].after = 0.0; hf[q].kfirst = 0;
-    ho[tile_of(f) + 1]++;
+  std::vector<long long> perm;
+  if (pan && pan->perm) {
+    perm = *pan->perm;
+  } else {
+    // two pinned staging buffers in turn: the one taken now may still be read
+    // by the copies of the call before the previous one, so wait for its event
+    // (recorded after those copies; long complete when calls follow each other)
+    const int k = w.ipin_next;
+    w.ipin_next ^= 1;
+    if (!w.ipin_ev[k] && cudaEventCreateWithFlags(&w.ipin_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return FTGEMM_ERR_CUDA;
+    if (cudaEventSynchronize(w.ipin_ev[k]) != cudaSuccess) return FTGEMM_ERR_CUDA;
+    if ((!pan && ensure(w.flips, fbytes + obytes)) || ensure_pinned(w.ipin[k], fbytes + obytes + 4096))
+      return FTGEMM_ERR_NOMEM;
+    table = pan ? pan->table : w.flips.p;
+    stage_injection_table(L, nI, ntiles, w.ipin[k].p, perm);
+    cudaMemcpyAsync(table, w.ipin[k].p, fbytes + obytes, cudaMemcpyHostToDevice, s);
+    cudaEventRecord(w.ipin_ev[k], s);
   }
-  for (long long t = 0; t < ntiles; ++t) ho[t + 1] += ho[t];
-  cudaMemcpyAsync(table, hf, fbytes + obytes, cudaMemcpyHostToDevice, s);
-  cudaEventRecord(w.ipin_ev[k], s);
   Workspace::LogSeg seg;
   seg.dev = (const DevFlip *)table;
   seg.orig.resize((size_t)nf);
@@ -858,7 +878,7 @@ int host_panels(char transA, char transB, long long M, long long N, long long K,
     toff[pp + 1] = toff[pp] + injection_table_bytes((long long)pl[pp].size(), nI * ((nc + BN - 1) / BN));
   }
   if (ensure(w.prep, sizeof(DevReport) * (size_t)P) || ensure(w.ploc, sizeof(DevLoc) * (size_t)(capp * P)) ||
-      ensure(w.pfl, toff[P]))
+      ensure(w.pfl, toff[P]) || (!all.empty() && ensure_pinned(w.ppin, toff[P])))
     return FTGEMM_ERR_NOMEM;
   if (int rc = ensure_side(w)) return rc;
   if (int rc = ensure_copy_streams(w, (size_t)(2 * P + 2))) return rc;
@@ -869,6 +889,18 @@ int host_panels(char transA, char transB, long long M, long long N, long long K,
   cudaStreamWaitEvent(w.up, ev[0], 0);
   cudaStreamWaitEvent(w.down, ev[0], 0);
   double *hA = (double *)w.hA.p, *hB = (double *)w.hB.p, *hC = (double *)w.hC.p;
+  // the panels' fault tables travel first, in one copy on the upload stream:
+  // a small copy queued on the compute stream would wait in the copy engine
+  // behind the panels' uploads, and the first panel with it
+  std::vector<std::vector<long long>> perms((size_t)P);
+  if (!all.empty()) {
+    for (long long pp = 0; pp < P; ++pp) {
+      const long long nc = std::min(N, (pp + 1) * NB) - pp * NB;
+      if (!pl[pp].empty())
+        stage_injection_table(pl[pp], nI, nI * ((nc + BN - 1) / BN), (char *)w.ppin.p + toff[pp], perms[pp]);
+    }
+    cudaMemcpyAsync(w.pfl.p, w.ppin.p, toff[P], cudaMemcpyHostToDevice, w.up);
+  }
   cudaMemcpyAsync(hA, A, abytes, cudaMemcpyHostToDevice, w.up);
   for (long long pp = 0; pp < P; ++pp) {
     const long long j0 = pp * NB, nc = std::min(N, j0 + NB) - j0;
@@ -891,7 +923,7 @@ int host_panels(char transA, char transB, long long M, long long N, long long K,
   for (long long pp = 0; pp < P && !rc; ++pp) {
     const long long j0 = pp * NB, nc = std::min(N, j0 + NB) - j0;
     cudaStreamWaitEvent(s, ev[1 + pp], 0);
-    InjPanel ip{&pl[pp], &po[pp], (char *)w.pfl.p + toff[pp], j0};
+    InjPanel ip{&pl[pp], &po[pp], (char *)w.pfl.p + toff[pp], j0, &perms[pp]};
     GemmPanel gp{(DevReport *)w.prep.p + pp, (DevLoc *)w.ploc.p + pp * capp, capp,
                  (g_inj.mode && !pl[pp].empty()) ? &ip : nullptr};
     rc = gemm_impl(transA, transB, M, nc, K, alpha, hA, lda, hB + (tb_n ? j0 * ldb : j0), ldb, beta, hC + j0 * ldc,
@@ -1337,6 +1369,9 @@ int ftgemm_finalize(void) {
   }
   if (w.pin.p) cudaFreeHost(w.pin.p);
   w.pin.p = nullptr;
+  if (w.ppin.p) cudaFreeHost(w.ppin.p);
+  w.ppin.p = nullptr;
+  w.ppin.cap = 0;
   for (int k = 0; k < 2; ++k) {
     if (w.ipin[k].p) cudaFreeHost(w.ipin[k].p);
     w.ipin[k].p = nullptr;
