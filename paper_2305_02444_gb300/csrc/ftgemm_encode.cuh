@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
 // takes its absolute sums again in FP64 from global memory.  The host orders
 // the items by their k extent, longest first, so the long blocks start in
 // the first wave.
-constexpr int ENC_STAGES = 4;
+constexpr int ENC_STAGES = 3;
 constexpr int ENC_SLAB = BM * BK * 8;  // one 128 x 16 slab, 16 KiB
 constexpr int ENC_SMEM_BYTES = ENC_STAGES * ENC_SLAB + 1024;
 
@@ -222,15 +222,6 @@ struct EncItem {
   int kfirst;              // 1: X(x, k) = X[k + x ld], slab [128 x][16 k] 128-byte swizzled
                            // 0: X(x, k) = X[x + k ld], slab [16 k][128 x]
 };
-
-__device__ __forceinline__ int find_item(const EncItem *items, int nitems, int b) {
-  int lo = 0, hi = nitems - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (items[mid].first_block <= b) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
@@ -274,7 +265,10 @@ __device__ __forceinline__ double enc_global(const EncItem &E, long long x, long
 // butterfly; the 4 warps of a half add their parts through shared memory in
 // a fixed order.  A warp whose x's all lie past the group's last valid x
 // skips its loads and sums.
-__global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restrict__ items, int nitems, int *gerr,
+// block_item[b]: the item of block b (a host-built map: one load instead of a
+// search at the start of every block).
+__global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restrict__ items,
+                                                         const int *__restrict__ block_item, int *gerr,
                                                          unsigned long long limit_ns) {
   extern __shared__ unsigned char enc_smem_raw[];
   unsigned char *ring =
@@ -285,8 +279,7 @@ __global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restr
   __shared__ double s_md[8];
   __shared__ __align__(8) uint64_t s_full[ENC_STAGES];
   __shared__ int s_stop;
-  const int it = find_item(items, nitems, blockIdx.x);
-  const EncItem E = items[it];
+  const EncItem E = items[block_item[blockIdx.x]];
   const int G = blockIdx.x - E.first_block;
   const long long x0 = (long long)G * 128;
   const int xv = (int)min(128LL, E.W - x0);

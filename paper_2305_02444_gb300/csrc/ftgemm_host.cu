@@ -1829,14 +1829,21 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
     items.push_back(b);
   }
   std::stable_sort(items.begin(), items.end(), [](const EncItem &x, const EncItem &y) { return x.L > y.L; });
-  for (EncItem &e : items) {
+  std::vector<int> block_item;
+  for (size_t q = 0; q < items.size(); ++q) {
+    EncItem &e = items[q];
     const int groups = e.first_block;
     e.first_block = enc_blocks;
     enc_blocks += groups;
+    block_item.insert(block_item.end(), (size_t)groups, (int)q);
   }
   EncItem *ditems = nullptr;
+  int *dblock_item = nullptr;
   PLAN_TRY(plan_alloc(P, &ditems, std::max<size_t>(1, items.size())));
+  PLAN_TRY(plan_alloc(P, &dblock_item, std::max<size_t>(1, block_item.size())));
   if (!items.empty()) cudaMemcpy(ditems, items.data(), sizeof(EncItem) * items.size(), cudaMemcpyHostToDevice);
+  if (!block_item.empty())
+    cudaMemcpy(dblock_item, block_item.data(), sizeof(int) * block_item.size(), cudaMemcpyHostToDevice);
   if (enc_blocks && cudaFuncSetAttribute(enc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          ENC_SMEM_BYTES) != cudaSuccess) {
     cudaGetLastError();
@@ -1893,7 +1900,7 @@ int ftgemm_batched_plan_create(ftgemm_batched_plan *plan_out, int64_t count, con
     if (P->ft && enc_total) {
       cudaMemsetAsync(enc, 0, sizeof(double) * enc_total, cs);
       if (enc_blocks) {
-        enc_batched_kernel<<<enc_blocks, 256, ENC_SMEM_BYTES, cs>>>(ditems, (int)items.size(), gerr, wait_limit_ns());
+        enc_batched_kernel<<<enc_blocks, 256, ENC_SMEM_BYTES, cs>>>(ditems, dblock_item, gerr, wait_limit_ns());
         P->kernels++;
       }
     }
