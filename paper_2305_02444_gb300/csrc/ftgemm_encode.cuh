@@ -25,75 +25,205 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// The absolute sums, which only bound the rounding in the detection
+// thresholds, in FP64 (ABS32 = false: the exact sums ftgemm_encode_operands
+// returns) or on the FP32 pipe with every operation rounded upward (each
+// partial stays an upper bound of the FP64 sum; the FP64 pipe is this GPU's
+// scarcest unit).  Where FP32's range makes an absolute sum overflow or
+// leaves it tiny (below 2^-90, where terms under FP32's normal range were
+// rounded up to its smallest numbers), it is taken again in FP64.
+template <bool ABS32> struct AbsAcc;
+template <> struct AbsAcc<false> {
+  using T = double;
+  static __device__ __forceinline__ double of(double v) { return fabs(v); }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double mx(double a, double b) { return fmax(a, b); }
+};
+template <> struct AbsAcc<true> {
+  using T = float;
+  static __device__ __forceinline__ float of(double v) { return f32_ru_abs(v); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_ru(a, b); }
+  static __device__ __forceinline__ float mx(float a, float b) { return fmaxf(a, b); }
+};
+
+// An FP32 absolute sum that does not stand for the FP64 one (see above).  A
+// NaN (from a NaN operand) stands: the FP64 sum is NaN as well.
+__device__ __forceinline__ bool abs32_loose(float s) { return isinf(s) || (s > 0.0f && s < 0x1p-90f); }
+
+// colsum16 for the absolute sums: FP64, or FP32 with every addition rounded
+// upward.
+__device__ __forceinline__ double colsum16_abs(double (&v)[16], int lane) { return colsum16(v, lane); }
+__device__ __forceinline__ float colsum16_abs(float (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
+      v[i] = __fadd_ru(keep, __shfl_xor_sync(0xffffffffu, send, o));
+    }
+  }
+  return __fadd_ru(v[0], __shfl_xor_sync(0xffffffffu, v[0], 16));
+}
+
+// The transposing butterfly for 8 columns: lane l's v[c] is its part of
+// column c; the result in lane l is the whole warp's sum of column l mod 8
+// (3 levels exchange half of the columns each, 2 more add across lane bits 3
+// and 4).  RU: FP32 with every addition rounded upward.
+template <typename T, bool RU>
+__device__ __forceinline__ T colsum8(T (&v)[8], int lane) {
+  auto add = [](T x, T y) -> T {
+    if constexpr (RU) return __fadd_ru(x, y);
+    else return x + y;
+  };
+#pragma unroll
+  for (int o = 4; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const T send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
+      v[i] = add(keep, __shfl_xor_sync(0xffffffffu, send, o));
+    }
+  }
+  T t = add(v[0], __shfl_xor_sync(0xffffffffu, v[0], 8));
+  return add(t, __shfl_xor_sync(0xffffffffu, t, 16));
+}
+
+// The FP64 absolute sums of one 128-wide group, from global memory (the rare
+// path behind the FP32 ones), by the whole block: X(x, k) = X[k + x ld] when
+// kfirst, else X[x + k ld]; x0 .. x0 + xv - 1 the group's x, L the k extent;
+// absv[x] = sum over k of |X(x, k)|, *gmax = max over k of sum over the
+// group's x of |X(x, k)|.  s_md: 8 doubles of shared memory.
+__device__ __forceinline__ void enc_abs64_group(const double *X, long long ld, bool kfirst, long long x0, int xv,
+                                                long long L, double *absv, double *gmax, double *s_md) {
+  auto at = [&](long long x, long long k) { return kfirst ? X[k + x * ld] : X[x + k * ld]; };
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  if (tid < xv) {
+    double a = 0.0;
+    for (long long k = 0; k < L; ++k) a += fabs(at(x0 + tid, k));
+    absv[x0 + tid] = a;
+  }
+  double md = 0.0;
+  for (long long k = tid; k < L; k += blockDim.x) {
+    double a = 0.0;
+    for (int xx = 0; xx < xv; ++xx) a += fabs(at(x0 + xx, k));
+    md = fmax(md, a);
+  }
+  md = warp_max(md);
+  if (lane == 0) s_md[w] = md;
+  __syncthreads();
+  if (tid == 0) {
+    double g = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) g = fmax(g, s_md[q]);
+    *gmax = g;
+  }
+}
+
 // The finish of a group of the pass, run by the block that completes the
 // group last (the others' partials are visible: each block fences its
 // partials before counting itself done): abs_out[x] = sum over the chunks c
 // of part_abs[c * L + x] for the group's 128 entries x0 .. (ascending c: a
-// fixed order), gmax[G] = max over c of part_max[c * nG + G].  The counter
-// goes back to zero for the next pass.
+// fixed order), gmax[G] = max over c of part_max[c * nG + G].  With ABS32 the
+// partials are FP32 upper bounds (summed rounded upward), and a group with a
+// loose one takes its absolute sums again in FP64 (X, ld, kfirst, Lk: the
+// operand, as enc_abs64_group takes it).  The counter goes back to zero for
+// the next pass.
+template <bool ABS32>
 __device__ __forceinline__ void enc_group_finish(unsigned int *cnt, int G, int nG, int nch, long long x0,
                                                  long long L, const double *part_abs, const double *part_max,
-                                                 double *abs_out, double *gmax) {
+                                                 double *abs_out, double *gmax, const double *X, long long ld,
+                                                 bool kfirst, long long Lk) {
+  using A = AbsAcc<ABS32>;
+  using T = typename A::T;
   __shared__ int s_last;
+  __shared__ double s_md[8];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = atomicAdd(&cnt[G], 1u) == (unsigned)(nch - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x < 128 && x0 + threadIdx.x < L) {
-    const long long x = x0 + threadIdx.x;
-    double t = 0.0;
-    for (int c = 0; c < nch; ++c) t += __ldcg(part_abs + (long long)c * L + x);
-    abs_out[x] = t;
+  T t = (T)0, m = (T)0;
+  bool loose = false;
+  const long long x = x0 + threadIdx.x;
+  const bool mine = threadIdx.x < 128 && x < L;
+  if (mine) {
+    for (int c = 0; c < nch; ++c) t = A::add(t, (T)__ldcg(part_abs + (long long)c * L + x));
+    if constexpr (ABS32) loose = abs32_loose(t);
   }
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int c = 0; c < nch; ++c) m = fmax(m, __ldcg(part_max + (long long)c * nG + G));
-    gmax[G] = m;
-    cnt[G] = 0u;
+    for (int c = 0; c < nch; ++c) m = A::mx(m, (T)__ldcg(part_max + (long long)c * nG + G));
+    if constexpr (ABS32) loose = loose || abs32_loose(m);
   }
+  bool redo = false;
+  if constexpr (ABS32) redo = __syncthreads_or(loose) != 0;
+  if (!redo) {
+    if (mine) abs_out[x] = (double)t;
+    if (threadIdx.x == 0) gmax[G] = (double)m;
+  } else {
+    enc_abs64_group(X, ld, kfirst, x0, (int)min(128LL, L - x0), Lk, abs_out, gmax + G, s_md);
+  }
+  if (threadIdx.x == 0) cnt[G] = 0u;
 }
 
 // grid (nG, ceil(S / cw)), 256 threads; block (G, c) covers columns c*cw ..
-// c*cw + cw - 1 of the 128-row group G.  Warp w takes batches of 16 columns
-// (16w, 16w + 128, ...), lane l the rows l + 32q (q < 4) of each column; a
+// c*cw + cw - 1 of the 128-row group G.  Warp w takes batches of 8 columns
+// (8w, 8w + 64, ...), lane l the rows l + 32q (q < 4) of each column; a
 // column's sum and absolute sum are the lanes' 4-row partials reduced by the
-// transposing butterfly (16 shuffled adds per 16 columns, not 5 per column:
-// this pass runs on the FP64 pipe, GB300's scarcest unit).
+// transposing butterfly (9 shuffled adds per 8 columns, not 5 per column: the
+// FP64 pipe is GB300's scarcest unit).
+template <bool ABS32>
 __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
                                                       double *__restrict__ part_rabs, double *__restrict__ part_max,
                                                       int cw, unsigned int *__restrict__ cnt,
                                                       double *__restrict__ rabs_out, double *__restrict__ gmax) {
-  __shared__ double sh[8][128];
-  __shared__ double smx[8];
+  using A = AbsAcc<ABS32>;
+  using T = typename A::T;
+  __shared__ T sh[8][128];
+  __shared__ T smx[8];
   const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long r0 = (long long)G * 128;
-  double rabs[4] = {0.0, 0.0, 0.0, 0.0};
-  double mx = 0.0;
+  T rabs[4] = {(T)0, (T)0, (T)0, (T)0};
+  T mx = (T)0;
   const long long c0 = (long long)c * cw, s1 = min(S, c0 + cw);
-  for (long long sb = c0 + 16 * w; sb < s1; sb += 128) {
-    double ps[16], pa[16];
+  for (long long sb = c0 + 8 * w; sb < s1; sb += 64) {
+    // the batch's 32 loads first: the absolute values' branches would
+    // otherwise hold each load back until the previous value was used
+    double v[8][4];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const long long s = sb + j;
-      double v[4];
+    for (int j = 0; j < 8; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const long long r = r0 + lane + 32 * q;
-        v[q] = (s < s1 && r < R) ? X[r + s * ld] : 0.0;
-        rabs[q] += fabs(v[q]);
+        const long long s = sb + j, r = r0 + lane + 32 * q;
+        v[j][q] = (s < s1 && r < R) ? X[r + s * ld] : 0.0;
       }
-      ps[j] = (v[0] + v[1]) + (v[2] + v[3]);
-      pa[j] = (fabs(v[0]) + fabs(v[1])) + (fabs(v[2]) + fabs(v[3]));
+    double ps[8];
+    T pa[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      T a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = A::of(v[j][q]);
+        rabs[q] = A::add(rabs[q], a[q]);
+      }
+      ps[j] = (v[j][0] + v[j][1]) + (v[j][2] + v[j][3]);
+      pa[j] = A::add(A::add(a[0], a[1]), A::add(a[2], a[3]));
     }
-    const double sum = colsum16(ps, lane), ab = colsum16(pa, lane);
-    const long long s = sb + (lane & 15);
-    if (lane < 16 && s < s1) {
+    const double sum = colsum8<double, false>(ps, lane);
+    const T ab = colsum8<T, ABS32>(pa, lane);
+    const long long s = sb + (lane & 7);
+    if (lane < 8 && s < s1) {
       gsum[(long long)G * gstride + s] = sum;
-      mx = fmax(mx, ab);
+      mx = A::mx(mx, ab);
     }
   }
 #pragma unroll
@@ -102,18 +232,18 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
   if (lane == 0) smx[w] = mx;
   __syncthreads();
   if (threadIdx.x < 128) {
-    double t = 0.0;
+    T t = (T)0;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+    for (int q = 0; q < 8; ++q) t = A::add(t, sh[q][threadIdx.x]);
     const long long r = r0 + threadIdx.x;
-    if (r < R) part_rabs[(long long)c * R + r] = t;
+    if (r < R) part_rabs[(long long)c * R + r] = (double)t;
   }
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int q = 0; q < 8; ++q) m = fmax(m, smx[q]);
-    part_max[(long long)c * nG + G] = m;
+    T m = (T)0;
+    for (int q = 0; q < 8; ++q) m = A::mx(m, smx[q]);
+    part_max[(long long)c * nG + G] = (double)m;
   }
-  enc_group_finish(cnt, G, nG, (int)gridDim.y, r0, R, part_rabs, part_max, rabs_out, gmax);
+  enc_group_finish<ABS32>(cnt, G, nG, (int)gridDim.y, r0, R, part_rabs, part_max, rabs_out, gmax, X, ld, false, S);
 }
 
 // grid (nG, ceil(R / (64 nsub))), 256 threads: a block covers nsub chunks of
@@ -121,40 +251,49 @@ __global__ void __launch_bounds__(256) enc_seg_kernel(const double *__restrict__
 // 16w..16w+15, lane l the rows l and l + 32 of a chunk.  A column's absolute
 // sum is kept per lane over the block's rows and reduced once at the end (the
 // transposing butterfly over the warp's 16 columns).
+template <bool ABS32>
 __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__ X, long long R, long long S,
                                                       long long ld, double *__restrict__ gsum, long long gstride,
                                                       double *__restrict__ part_cabs, double *__restrict__ part_max,
                                                       int nsub, unsigned int *__restrict__ cnt,
                                                       double *__restrict__ cabs_out, double *__restrict__ gmax) {
   static_assert(ENC_CHUNK == 64, "two rows per lane");
-  __shared__ double srs[8][64], sra[8][64];
-  __shared__ double smx[2];
+  using A = AbsAcc<ABS32>;
+  using T = typename A::T;
+  __shared__ double srs[8][64];
+  __shared__ T sra[8][64];
+  __shared__ T smx[2];
   const int G = blockIdx.x, c = blockIdx.y, nG = gridDim.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long s0 = (long long)G * 128;
   const int ns = (int)min(128LL, S - s0);
-  double cab[16];
+  T cab[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) cab[q] = 0.0;
-  double mloc = 0.0;  // largest row absolute sum seen by this thread (threads < 64)
+  for (int q = 0; q < 16; ++q) cab[q] = (T)0;
+  T mloc = (T)0;  // largest row absolute sum seen by this thread (threads < 64)
   for (int sub = 0; sub < nsub; ++sub) {
     const long long r0 = ((long long)c * nsub + sub) * 64, ra = r0 + lane, rb = ra + 32;
     if (r0 >= R) break;
-    double rs_a = 0.0, rs_b = 0.0, ab_a = 0.0, ab_b = 0.0;
+    double rs_a = 0.0, rs_b = 0.0;
+    T ab_a = (T)0, ab_b = (T)0;
+    // the chunk's 32 loads first (see enc_seg_kernel)
+    double vs[16][2];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int sl = w * 16 + q;
-      double va = 0.0, vb = 0.0;
-      if (sl < ns) {
-        const double *col = X + (s0 + sl) * ld;
-        if (ra < R) va = col[ra];
-        if (rb < R) vb = col[rb];
-      }
+      const double *col = X + (s0 + min(sl, ns - 1)) * ld;
+      vs[q][0] = (sl < ns && ra < R) ? col[ra] : 0.0;
+      vs[q][1] = (sl < ns && rb < R) ? col[rb] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const double va = vs[q][0], vb = vs[q][1];
       rs_a += va;
       rs_b += vb;
-      ab_a += fabs(va);
-      ab_b += fabs(vb);
-      cab[q] += fabs(va) + fabs(vb);
+      const T fa = A::of(va), fb = A::of(vb);
+      ab_a = A::add(ab_a, fa);
+      ab_b = A::add(ab_b, fb);
+      cab[q] = A::add(cab[q], A::add(fa, fb));
     }
     srs[w][lane] = rs_a;
     srs[w][lane + 32] = rs_b;
@@ -163,28 +302,29 @@ __global__ void __launch_bounds__(256) enc_str_kernel(const double *__restrict__
     __syncthreads();
     if (threadIdx.x < 64) {
       const long long r = r0 + threadIdx.x;
-      double t = 0.0, ta = 0.0;
+      double t = 0.0;
+      T ta = (T)0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         t += srs[q][threadIdx.x];
-        ta += sra[q][threadIdx.x];
+        ta = A::add(ta, sra[q][threadIdx.x]);
       }
       if (r < R) {
         gsum[(long long)G * gstride + r] = t;
-        mloc = fmax(mloc, ta);
+        mloc = A::mx(mloc, ta);
       }
     }
     __syncthreads();
   }
-  const double cs = colsum16(cab, lane);
-  if (lane < 16 && w * 16 + lane < ns) part_cabs[(long long)c * S + s0 + w * 16 + lane] = cs;
+  const T cs = colsum16_abs(cab, lane);
+  if (lane < 16 && w * 16 + lane < ns) part_cabs[(long long)c * S + s0 + w * 16 + lane] = (double)cs;
   if (threadIdx.x < 64) {
-    const double m = warp_max(mloc);
+    const T m = warp_max(mloc);
     if (lane == 0) smx[w] = m;
   }
   __syncthreads();
-  if (threadIdx.x == 0) part_max[(long long)c * nG + G] = fmax(smx[0], smx[1]);
-  enc_group_finish(cnt, G, nG, (int)gridDim.y, s0, S, part_cabs, part_max, cabs_out, gmax);
+  if (threadIdx.x == 0) part_max[(long long)c * nG + G] = (double)A::mx(smx[0], smx[1]);
+  enc_group_finish<ABS32>(cnt, G, nG, (int)gridDim.y, s0, S, part_cabs, part_max, cabs_out, gmax, X, ld, true, R);
 }
 
 // Batched checksum pass: one item per operand of each problem of a batch;
@@ -222,43 +362,6 @@ struct EncItem {
   int kfirst;              // 1: X(x, k) = X[k + x ld], slab [128 x][16 k] 128-byte swizzled
                            // 0: X(x, k) = X[x + k ld], slab [16 k][128 x]
 };
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// The transposing butterfly for 8 columns: lane l's v[c] is its part of
-// column c; the result in lane l is the whole warp's sum of column l mod 8
-// (3 levels exchange half of the columns each, 2 more add across lane bits 3
-// and 4).  RU: FP32 with every addition rounded upward.
-template <typename T, bool RU>
-__device__ __forceinline__ T colsum8(T (&v)[8], int lane) {
-  auto add = [](T x, T y) -> T {
-    if constexpr (RU) return __fadd_ru(x, y);
-    else return x + y;
-  };
-#pragma unroll
-  for (int o = 4; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const T send = up ? v[i] : v[i + o], keep = up ? v[i + o] : v[i];
-      v[i] = add(keep, __shfl_xor_sync(0xffffffffu, send, o));
-    }
-  }
-  T t = add(v[0], __shfl_xor_sync(0xffffffffu, v[0], 8));
-  return add(t, __shfl_xor_sync(0xffffffffu, t, 16));
-}
-
-// An FP32 absolute sum that does not stand for the FP64 one (see above).  A
-// NaN (from a NaN operand) stands: the FP64 sum is NaN as well.
-__device__ __forceinline__ bool abs32_loose(float s) { return isinf(s) || (s > 0.0f && s < 0x1p-90f); }
-
-__device__ __forceinline__ double enc_global(const EncItem &E, long long x, long long k) {
-  return E.kfirst ? E.X[k + x * E.ld] : E.X[x + k * E.ld];
-}
 
 // 256 threads: thread t takes x = t mod 128 and the 8 k's 8h..8h+7 of every
 // slab (h = t / 128).  A warp's 32 x's reduce each k by the transposing
@@ -377,26 +480,7 @@ __global__ void __launch_bounds__(256) enc_batched_kernel(const EncItem *__restr
     if (tid == 0) E.gmax[G] = (double)gm;
     return;
   }
-  // FP64 absolute sums: thread t the x's absolute sum; the k's strided over the block
-  if (tid < xv) {
-    double a = 0.0;
-    for (long long k = 0; k < E.L; ++k) a += fabs(enc_global(E, x0 + tid, k));
-    E.absv[x0 + tid] = a;
-  }
-  double md = 0.0;
-  for (long long k = tid; k < E.L; k += 256) {
-    double a = 0.0;
-    for (int xx = 0; xx < xv; ++xx) a += fabs(enc_global(E, x0 + xx, k));
-    md = fmax(md, a);
-  }
-  md = warp_max(md);
-  if (lane == 0) s_md[w] = md;
-  __syncthreads();
-  if (tid == 0) {
-    double g = 0.0;
-    for (int q = 0; q < 8; ++q) g = fmax(g, s_md[q]);
-    E.gmax[G] = g;
-  }
+  enc_abs64_group(E.X, E.ld, E.kfirst != 0, x0, xv, E.L, E.absv, E.gmax + G, s_md);
 }
 
 // One pass over C that takes, per 128x128 tile, the column sums over the

@@ -368,15 +368,22 @@ void enc_ops(bool ta_t, bool tb_t, long long M, long long N, long long K, int ns
 // One operand's pass: gsum = group sums (stride gstride), absv = row (SEG) /
 // column (STR) absolute sums, gmax = per group maximum; part_abs / part_max
 // hold the chunks' partials, cnt (o.nG counters, zero between passes) counts
-// each group's finished chunks.
+// each group's finished chunks.  abs32: the absolute sums as FP32 upper
+// bounds (the thresholds' use), else exact FP64 sums.
 void launch_enc(const EncOp &o, const double *X, long long ld, double *gsum, long long gstride, double *part_abs,
-                double *part_max, unsigned int *cnt, double *absv, double *gmax, cudaStream_t s) {
+                double *part_max, unsigned int *cnt, double *absv, double *gmax, cudaStream_t s, bool abs32 = false) {
   const dim3 grid((unsigned)o.nG, (unsigned)o.nch);
-  if (o.seg)
-    enc_seg_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, ENC_CHUNK * o.sub, cnt,
-                                        absv, gmax);
+  const int cw = ENC_CHUNK * o.sub;
+  if (o.seg && abs32)
+    enc_seg_kernel<true><<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, cw, cnt, absv, gmax);
+  else if (o.seg)
+    enc_seg_kernel<false><<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, cw, cnt, absv, gmax);
+  else if (abs32)
+    enc_str_kernel<true><<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, o.sub, cnt, absv,
+                                              gmax);
   else
-    enc_str_kernel<<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, o.sub, cnt, absv, gmax);
+    enc_str_kernel<false><<<grid, 256, 0, s>>>(X, o.R, o.S, ld, gsum, gstride, part_abs, part_max, o.sub, cnt, absv,
+                                               gmax);
 }
 
 // The second stream of a call (independent work inside one call runs on it
@@ -405,11 +412,13 @@ int device_sms(int dev) {
 }
 
 // Encode the operand checksum vectors (see ftgemm_encode.cuh).  Writes
-// acs (nI x Kp), aabsmax, arowabs, bcs (nJ x Kp), babsmax, bcolabs.
+// acs (nI x Kp), aabsmax, arowabs, bcs (nJ x Kp), babsmax, bcolabs; the
+// absolute sums as FP32 upper bounds (abs32: what the thresholds need) or as
+// exact FP64 sums (ftgemm_encode_operands).
 int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, const double *A, long long lda,
                const double *B, long long ldb, long long Kp, double *acs, double *aabsmax, double *arowabs,
                double *bcs, double *babsmax, double *bcolabs, Workspace &w, cudaStream_t s,
-               bool concurrent = true) {
+               bool concurrent = true, bool abs32 = true) {
   const long long nI = (M + BM - 1) / BM, nJ = (N + BN - 1) / BN;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -438,9 +447,10 @@ int run_encode(bool ta_t, bool tb_t, long long M, long long N, long long K, cons
     cudaEventRecord(w.fork_ev, s);
     cudaStreamWaitEvent(w.side, w.fork_ev, 0);
   }
-  launch_enc(oa, A, lda, acs, Kp, (double *)w.part_abs.p, (double *)w.part_max.p, cnt, arowabs, aabsmax, s);
+  launch_enc(oa, A, lda, acs, Kp, (double *)w.part_abs.p, (double *)w.part_max.p, cnt, arowabs, aabsmax, s,
+             abs32);
   launch_enc(ob, B, ldb, bcs, Kp, (double *)w.part_abs2.p, (double *)w.part_max2.p, cnt + oa.nG, bcolabs, babsmax,
-             sb);
+             sb, abs32);
   if (concurrent) {
     cudaEventRecord(w.join_ev, w.side);
     cudaStreamWaitEvent(s, w.join_ev, 0);
@@ -1164,7 +1174,7 @@ int ftgemm_encode_operands(char transA, char transB, int64_t M, int64_t N, int64
   Workspace *wp = workspace(&dev);
   if (!wp) return FTGEMM_ERR_NODEVICE;
   return run_encode(is_t(transA), is_t(transB), M, N, K, A, lda, B, ldb, K, acs, aabsmax, arowabs, bcs, babsmax,
-                    bcolabs, *wp, (cudaStream_t)stream);
+                    bcolabs, *wp, (cudaStream_t)stream, true, false);
 }
 
 int ftgemm_set_injection(const ftgemm_inject *cfg) {

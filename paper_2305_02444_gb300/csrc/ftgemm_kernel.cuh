@@ -513,6 +513,27 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     // With p.presummed, slot 0 already holds that sum (splitk_sum_kernel, the
     // same additions in the same order): one load, the checksum partials of
     // every split still added here.
+    if (FT) {
+      // the predicted-checksum partials of every split, added in ascending
+      // split order; their loads do not depend on one another, so they go out
+      // four at a time, ahead of the partial tiles' loads
+      const bool col = tid < 128;
+      const int idx = col ? tid : tid - 128;
+      if (col ? idx < nJt : idx < mI) {
+        const double *base = col ? p.wpc + (long long)I * p.N + j0 + idx : p.wpr + (long long)J * p.M + i0 + idx;
+        const long long stride = col ? (long long)p.nI * p.N : (long long)p.nJ * p.M;
+        int sp = 0;
+        for (; sp + 4 <= p.nsplit; sp += 4) {
+          const double v0 = base[sp * stride], v1 = base[(sp + 1) * stride];
+          const double v2 = base[(sp + 2) * stride], v3 = base[(sp + 3) * stride];
+          csacc += v0;
+          csacc += v1;
+          csacc += v2;
+          csacc += v3;
+        }
+        for (; sp < p.nsplit; ++sp) csacc += base[sp * stride];
+      }
+    }
     for (int sp = 0; sp < p.nsplit; ++sp) {
       if (!p.presummed || sp == 0) {
       if (tid == 0) {
@@ -528,13 +549,6 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
         for (int qq = 0; qq < 8; ++qq) acc[pp][qq] += sC[(ty + 16 * qq) * BM + tx + 16 * pp];
       fence_proxy_async_smem();  // these generic reads precede the next async write (next partial or C)
       compute_sync();
-      }
-      if (FT) {
-        if (tid < 128) {
-          if (tid < nJt) csacc += p.wpc[((long long)sp * p.nI + I) * p.N + j0 + tid];
-        } else if (tid - 128 < mI) {
-          csacc += p.wpr[((long long)sp * p.nJ + J) * p.M + i0 + tid - 128];
-        }
       }
     }
   }

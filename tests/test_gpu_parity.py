@@ -226,6 +226,32 @@ def test_encode_operands_vs_oracle(ft, orc, ta, tb, M, N, K):
         np.testing.assert_allclose(outs[k].cpu().numpy(), getattr(e, k), rtol=rel, atol=0)
 
 
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
+@pytest.mark.parametrize("sa,sb", [(2.0 ** 140, 2.0 ** -140), (2.0 ** -400, 2.0 ** -400)])
+def test_thresholds_at_the_edges_of_the_fp32_range(ft, orc, ta, tb, sa, sb):
+    """The checksum pass of a call keeps the thresholds' absolute sums as FP32
+    upper bounds and takes a group's again in FP64 where FP32's range would
+    overflow them (operands near 2^140) or leave them loose (every |x| near
+    2^-400, products near 2^-800).  With beta = 0 (C's own absolute sums are
+    the epilogue's) the call stays verifiable, raises no check without
+    faults, and detects, locates and corrects an exponent flip; K = 700 gives
+    every group several chunks, both layouts both shapes of the pass."""
+    P = make_problem(ta, tb, 300, 260, 700, seed=31)
+    P["A"].mul_(sa)
+    P["B"].mul_(sb)
+    ref, E = oracle_ref(orc, P, 1.0, 0.0)
+    with splitk(ft, 1):
+        rc, rep, out = run_gpu(ft, P, 1.0, 0.0)
+    assert rc == 0
+    assert rep["unverifiable"] == 0 and rep["detected"] == 0 and rep["flagged_rows"] == 0, rep
+    assert_parity(orc, P, out, ref, E)
+    rc, rep, out, log = run_injected(ft, P, 1.0, 0.0, [(100, 50, 3, 61)])
+    assert rc == 0 and log[0]["applied"] == 1
+    assert rep["unverifiable"] == 0 and rep["detected"] == 1 and rep["corrected"] == 1, rep
+    assert tuple(rep["locs"][0][:2]) == (100, 50)
+    assert_parity(orc, P, out, ref, E)
+
+
 # ------------------------------------------------------------------------------ injection
 
 def flip_value(x: float, bit: int) -> float:
