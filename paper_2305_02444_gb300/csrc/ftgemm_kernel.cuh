@@ -110,12 +110,15 @@ __device__ __forceinline__ void slab_fma(double (&acc)[8][8], const unsigned cha
 
 // One k-slab for the accumulator blocks P0 .. P0+PP-1 (rows) x Q0 .. Q0+QQ-1
 // (columns) of this thread: the same FMAs, in the same k order, as those
-// blocks get in slab_fma.
-template <bool TA, bool TB, int P0, int PP, int Q0, int QQ>
+// blocks get in slab_fma.  KT: only the first kv k's of the slab (the last
+// slab of a problem whose K is not a multiple of BK; the rest are TMA zero
+// fill, whose FMAs would leave the accumulators as they are), in a loop that
+// is not unrolled.
+template <bool TA, bool TB, int P0, int PP, int Q0, int QQ, bool KT = false>
 __device__ __forceinline__ void slab_fma_part(double (&acc)[8][8], const unsigned char *sA, const unsigned char *sB,
-                                              int tx, int ty) {
-#pragma unroll
-  for (int k = 0; k < BK; ++k) {
+                                              int tx, int ty, int kv = BK) {
+#pragma unroll(KT ? 1 : BK)
+  for (int k = 0; k < (KT ? kv : BK); ++k) {
     double a[PP], b[QQ];
 #pragma unroll
     for (int pp = 0; pp < PP; ++pp) a[pp] = stage_a<TA>(sA, tx + 16 * (P0 + pp), k);
@@ -130,24 +133,24 @@ __device__ __forceinline__ void slab_fma_part(double (&acc)[8][8], const unsigne
 
 // The column blocks 0 .. cblk-1 (cblk in 1..8) for the row blocks P0 ..
 // P0+PP-1: all 8 in one pass, else in binary pieces (4, 2, 1), one pass each.
-template <bool TA, bool TB, int P0, int PP>
+template <bool TA, bool TB, int P0, int PP, bool KT>
 __device__ __forceinline__ void slab_fma_rowpiece(int cblk, double (&acc)[8][8], const unsigned char *sA,
-                                                  const unsigned char *sB, int tx, int ty) {
+                                                  const unsigned char *sB, int tx, int ty, int kv) {
   if (cblk == 8) {
-    slab_fma_part<TA, TB, P0, PP, 0, 8>(acc, sA, sB, tx, ty);
+    slab_fma_part<TA, TB, P0, PP, 0, 8, KT>(acc, sA, sB, tx, ty, kv);
     return;
   }
-  if (cblk & 4) slab_fma_part<TA, TB, P0, PP, 0, 4>(acc, sA, sB, tx, ty);
+  if (cblk & 4) slab_fma_part<TA, TB, P0, PP, 0, 4, KT>(acc, sA, sB, tx, ty, kv);
   if (cblk & 2) {
-    if (cblk & 4) slab_fma_part<TA, TB, P0, PP, 4, 2>(acc, sA, sB, tx, ty);
-    else slab_fma_part<TA, TB, P0, PP, 0, 2>(acc, sA, sB, tx, ty);
+    if (cblk & 4) slab_fma_part<TA, TB, P0, PP, 4, 2, KT>(acc, sA, sB, tx, ty, kv);
+    else slab_fma_part<TA, TB, P0, PP, 0, 2, KT>(acc, sA, sB, tx, ty, kv);
   }
   if (cblk & 1) {
     switch (cblk & 6) {
-      case 0: slab_fma_part<TA, TB, P0, PP, 0, 1>(acc, sA, sB, tx, ty); break;
-      case 2: slab_fma_part<TA, TB, P0, PP, 2, 1>(acc, sA, sB, tx, ty); break;
-      case 4: slab_fma_part<TA, TB, P0, PP, 4, 1>(acc, sA, sB, tx, ty); break;
-      default: slab_fma_part<TA, TB, P0, PP, 6, 1>(acc, sA, sB, tx, ty); break;
+      case 0: slab_fma_part<TA, TB, P0, PP, 0, 1, KT>(acc, sA, sB, tx, ty, kv); break;
+      case 2: slab_fma_part<TA, TB, P0, PP, 2, 1, KT>(acc, sA, sB, tx, ty, kv); break;
+      case 4: slab_fma_part<TA, TB, P0, PP, 4, 1, KT>(acc, sA, sB, tx, ty, kv); break;
+      default: slab_fma_part<TA, TB, P0, PP, 6, 1, KT>(acc, sA, sB, tx, ty, kv); break;
     }
   }
 }
@@ -160,9 +163,9 @@ __device__ __forceinline__ void slab_fma_rowpiece(int cblk, double (&acc)[8][8],
 // takes one pass over the slab.  Every accumulator gets the same FMAs in the
 // same order either way (the same bits); the extra passes re-read operands
 // from shared memory, which is cheap beside the FP64 pipe.
-template <bool TA, bool TB, bool FINE>
+template <bool TA, bool TB, bool FINE, bool KT = false>
 __device__ __forceinline__ void slab_fma_blocks(int rblk, int cblk, double (&acc)[8][8], const unsigned char *sA,
-                                                const unsigned char *sB, int tx, int ty) {
+                                                const unsigned char *sB, int tx, int ty, int kv = BK) {
   if constexpr (!FINE) {
     if (rblk == 8 && cblk == 8) slab_fma<TA, TB, 8, 8>(acc, sA, sB, tx, ty);
     else if (rblk == 8 && cblk == 4) slab_fma<TA, TB, 8, 4>(acc, sA, sB, tx, ty);
@@ -175,20 +178,20 @@ __device__ __forceinline__ void slab_fma_blocks(int rblk, int cblk, double (&acc
     else slab_fma<TA, TB, 2, 2>(acc, sA, sB, tx, ty);
   } else {
     if (rblk == 8) {
-      slab_fma_rowpiece<TA, TB, 0, 8>(cblk, acc, sA, sB, tx, ty);
+      slab_fma_rowpiece<TA, TB, 0, 8, KT>(cblk, acc, sA, sB, tx, ty, kv);
       return;
     }
-    if (rblk & 4) slab_fma_rowpiece<TA, TB, 0, 4>(cblk, acc, sA, sB, tx, ty);
+    if (rblk & 4) slab_fma_rowpiece<TA, TB, 0, 4, KT>(cblk, acc, sA, sB, tx, ty, kv);
     if (rblk & 2) {
-      if (rblk & 4) slab_fma_rowpiece<TA, TB, 4, 2>(cblk, acc, sA, sB, tx, ty);
-      else slab_fma_rowpiece<TA, TB, 0, 2>(cblk, acc, sA, sB, tx, ty);
+      if (rblk & 4) slab_fma_rowpiece<TA, TB, 4, 2, KT>(cblk, acc, sA, sB, tx, ty, kv);
+      else slab_fma_rowpiece<TA, TB, 0, 2, KT>(cblk, acc, sA, sB, tx, ty, kv);
     }
     if (rblk & 1) {
       switch (rblk & 6) {
-        case 0: slab_fma_rowpiece<TA, TB, 0, 1>(cblk, acc, sA, sB, tx, ty); break;
-        case 2: slab_fma_rowpiece<TA, TB, 2, 1>(cblk, acc, sA, sB, tx, ty); break;
-        case 4: slab_fma_rowpiece<TA, TB, 4, 1>(cblk, acc, sA, sB, tx, ty); break;
-        default: slab_fma_rowpiece<TA, TB, 6, 1>(cblk, acc, sA, sB, tx, ty); break;
+        case 0: slab_fma_rowpiece<TA, TB, 0, 1, KT>(cblk, acc, sA, sB, tx, ty, kv); break;
+        case 2: slab_fma_rowpiece<TA, TB, 2, 1, KT>(cblk, acc, sA, sB, tx, ty, kv); break;
+        case 4: slab_fma_rowpiece<TA, TB, 4, 1, KT>(cblk, acc, sA, sB, tx, ty, kv); break;
+        default: slab_fma_rowpiece<TA, TB, 6, 1, KT>(cblk, acc, sA, sB, tx, ty, kv); break;
       }
     }
   }
@@ -313,7 +316,10 @@ __device__ __forceinline__ void ftd_tile(const CUtensorMap *tmA, const CUtensorM
     // rows tx + 16 pp >= mI and columns ty + 16 qq >= nJt hold zeros (TMA
     // zero fill): a tile whose valid rows or columns end before the last
     // blocks skips those blocks' FMAs, leaving the same bits
-    slab_fma_blocks<TA, TB, FINE>(rblk, cblk, acc, sA, sB, tx, ty);
+    if (FINE && s_begin + s == p.nks - 1 && p.K < (long long)p.nks * BK)
+      slab_fma_blocks<TA, TB, FINE, true>(rblk, cblk, acc, sA, sB, tx, ty, (int)(p.K - (long long)(p.nks - 1) * BK));
+    else
+      slab_fma_blocks<TA, TB, FINE>(rblk, cblk, acc, sA, sB, tx, ty);
     if (FT) {
       const double *scs = reinterpret_cast<const double *>(sA + A_BYTES + B_BYTES);
       if (tid < 128) {
